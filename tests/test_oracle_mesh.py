@@ -1,0 +1,167 @@
+"""Pins of the oracle's detector surfaces (CPU only).
+
+Closed forms: the exact volume of a faceted solid of revolution (sum of
+similar-N-gon frusta over the profile), convergence to the smooth volume at
+O(N^-2), Euler characteristic 2 per closed genus-0 solid, every directed edge
+matched by exactly one opposite edge (closed and consistently oriented),
+positive signed volume (outward normals), the vertex equations of Sec. 2.2.2,
+and the parity rule at points whose region is known by construction.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2605_25963_gb300 import workloads as W
+
+
+def det(orc, d: W.Detector):
+    return orc.Mesh.build(orc.Det(**d.as_dict()))
+
+
+def faceted_volume(profile, N):
+    """Volume of a closed (rho, z) profile revolved with N-gon cross sections.
+
+    Each profile segment sweeps a frustum of similar N-gons:
+    (z_a - z_b) * (N/2) sin(2 pi / N) * (ra^2 + ra rb + rb^2) / 3, signed.
+    """
+    c = 0.5 * N * math.sin(2 * math.pi / N)
+    v = 0.0
+    for (ra, za), (rb, zb) in zip(profile[:-1], profile[1:]):
+        v += (za - zb) * c * (ra * ra + ra * rb + rb * rb) / 3.0
+    return v
+
+
+def rounded_profile(R, rch, zf, zb, n_phi):
+    pts = []
+    if rch > 0:
+        hemi = rch == R
+        if not hemi:
+            pts.append((0.0, zf))
+        for j in range(n_phi, -1, -1):
+            phi = 0.5 * math.pi * j / n_phi
+            r = 0.0 if (hemi and j == n_phi) else (R - rch) + rch * math.cos(phi)
+            pts.append((r, zf - rch * (1 - math.sin(phi))))
+    else:
+        pts += [(0.0, zf), (R, zf)]
+    pts += [(R, zb), (0.0, zb)]
+    return pts
+
+
+def test_bare_cylinder_counts_volume_topology(orc):
+    m = det(orc, W.BARE_CYLINDER)
+    assert (m.n_vert, m.n_tri, m.n_solid) == (98, 192, 1)
+    N, R, H = 48, 30.0, 60.0
+    assert m.volume(0) == pytest.approx(N / 2 * R * R * math.sin(2 * math.pi / N) * H, rel=1e-12)
+    assert m.volume(0) == pytest.approx(169161.9, abs=0.1)
+    deficit = 1 - m.volume(0) / (math.pi * R * R * H)
+    assert deficit == pytest.approx((2 * math.pi / N) ** 2 / 6, rel=0.01)
+    assert m.euler(0) == 2 and m.open_edges(0) == 0
+    xyz, tri, ts, solids = m.arrays()
+    # vertex equations: x = R cos(2 pi i / N), y = R sin(2 pi i / N) on the rings
+    ring = xyz[np.isclose(np.hypot(xyz[:, 0], xyz[:, 1]), R)]
+    ang = np.sort(np.mod(np.arctan2(ring[:, 1], ring[:, 0]), 2 * math.pi))
+    i = np.round(ang / (2 * math.pi / N))
+    assert np.allclose(ang, 2 * math.pi * i / N, atol=1e-14)
+    assert solids["active"][0] == 1 and solids["material"][0] == W.MAT_GE
+
+
+def test_volume_converges_second_order(orc):
+    R, H = 30.0, 60.0
+    errs = []
+    for N in (16, 32, 64, 128):
+        d = W.Detector(kind=W.DET_BARE_CYLINDER, D=(H, R, 0, 0, 0, 0, 0), n_theta=N)
+        errs.append(abs(det(orc, d).volume(0) - math.pi * R * R * H))
+    for a, b in zip(errs[:-1], errs[1:]):
+        assert a / b == pytest.approx(4.0, rel=0.02)
+
+
+def test_coax_solids(orc):
+    d = W.COAX_P
+    m = det(orc, d)
+    assert m.n_solid == 7
+    N, nphi = d.n_theta, d.n_phi
+    ext, D = d.d, d.D
+    zf = -(ext[1] + ext[4])
+    zb = zf - D[0]
+    sep = d.sep_delta
+    profiles = {
+        0: [(0, 0.0), (ext[0], 0.0), (ext[0], -ext[6]), (0, -ext[6])],
+        1: [(0, -ext[1]), (ext[0] - ext[2], -ext[1]), (ext[0] - ext[2], -ext[6] + ext[8]),
+            (0, -ext[6] + ext[8])],
+        2: [(0, -ext[7] + ext[9]), (D[1] + ext[5], -ext[7] + ext[9]), (D[1] + ext[5], zf - 10.0),
+            (D[1] + ext[5] + ext[3], zf - 10.0), (D[1] + ext[5] + ext[3], -ext[7]), (0, -ext[7])],
+        3: rounded_profile(D[1], D[2], zf, zb, nphi),
+        4: rounded_profile(D[1] - D[3], D[2] - D[3], zf - D[3], zb + sep, nphi),
+        5: rounded_profile(D[5] + D[6], D[5] + D[6], zb + D[4] + D[6], zb + 2 * sep, nphi),
+        6: rounded_profile(D[5], D[5], zb + D[4], zb + 3 * sep, nphi),
+    }
+    for s, prof in profiles.items():
+        assert m.euler(s) == 2, s
+        assert m.open_edges(s) == 0, s
+        v = m.volume(s)
+        assert v > 0, s
+        assert v == pytest.approx(faceted_volume(prof, N), rel=1e-10), s
+    # smooth-body limits: crystal volume vs the Pappus volume of the rounded profile
+    R, rch, L = D[1], D[2], D[0]
+    smooth = math.pi * R * R * L - (1 - math.pi / 4) * rch * rch * 2 * math.pi * (R - rch * (
+        (10 - 3 * math.pi) / (12 - 3 * math.pi)))
+    assert m.volume(3) == pytest.approx(smooth, rel=2e-3)
+    # triangle budget: 2N(Nphi+2) per rounded crystal solid, 2N(Nphi+1) per bore solid
+    assert m.n_tri == 2 * 4 * N + 8 * N + 2 * 2 * N * (nphi + 2) + 2 * 2 * N * (nphi + 1)
+    xyz, tri, ts, solids = m.arrays()
+    assert list(solids["parent"]) == [-1, 0, 1, 1, 3, 4, 5]
+    assert list(solids["material"]) == [W.MAT_AL, W.MAT_VACUUM, W.MAT_CU, W.MAT_GE, W.MAT_GE,
+                                        W.MAT_GE, W.MAT_VACUUM]
+    assert list(solids["active"]) == [0, 0, 0, 0, 1, 0, 0]
+    # rounding vertices obey rho_j, z_j of Sec. 2.2.2 (crystal solid, j = 0..Nphi)
+    cx = xyz[np.unique(tri[ts == 3])]
+    for j in range(nphi + 1):
+        phi = 0.5 * math.pi * j / nphi
+        rho = (R - rch) + rch * math.cos(phi)
+        z = zf - rch * (1 - math.sin(phi))
+        sel = np.isclose(cx[:, 2], z, atol=1e-12) & (np.hypot(cx[:, 0], cx[:, 1]) > 0)
+        assert sel.sum() == N
+        assert np.allclose(np.hypot(cx[sel, 0], cx[sel, 1]), rho, atol=1e-12)
+
+
+def test_parity_rule_locates_known_points(orc):
+    m = det(orc, W.COAX_P)
+    D = W.COAX_D_INT
+    zf = -6.0
+    zb = zf - D[0]
+    cases = [
+        ((0, 0, 10.0), -1),                 # above the endcap
+        ((0, 0, -0.5), 0),                  # in the Al window
+        ((0, 0, -3.0), 1),                  # vacuum gap
+        ((0, 0, zf - 0.3), 3),              # front dead layer
+        ((10.0, 0, -30.0), 4),              # active Ge
+        ((0, 0, zb + 10.0), 6),             # bore vacuum
+        ((5.00015, 0, zb + 20.0), 5),       # inside the 0.3 um bore contact
+        ((31.4, 0, -50.0), 2),              # Cu holder wall
+        ((37.5, 0, -60.0), 0),              # endcap side wall
+        ((50.0, 0, -60.0), -1),
+    ]
+    dirs = [(0, 0, 1), (0.3, -0.5, 0.81), (-1, 0, 0), (0.1, 0.99, -0.05)]
+    for p, want in cases:
+        for dd in dirs:
+            n = np.array(dd, dtype=float)
+            n /= np.linalg.norm(n)
+            assert m.locate(p, n) == want, (p, dd)
+
+
+def test_bare_with_source_prism(orc):
+    m = det(orc, W.BATCH_DET)
+    assert m.n_solid == 2
+    N = W.BATCH_DET.src_n_sides
+    assert m.volume(1) == pytest.approx(N / 2 * 35.0 ** 2 * math.sin(2 * math.pi / N) * 40.0, rel=1e-12)
+    assert m.euler(1) == 2 and m.open_edges(1) == 0
+    assert m.locate((0, 0, 25.0), (0, 0, 1)) == 1
+    assert m.locate((0, 0, -5.0), (1, 0, 0)) == 0
+
+
+def test_box_mesh_input_generator(orc):
+    xyz, tri, ts = W.box_mesh([(-1, -2, -3, 1, 2, 3)])
+    m = orc.Mesh.from_arrays(xyz, tri, ts, [1], [1], [0], [-1])
+    assert m.volume(0) == pytest.approx(48.0, rel=1e-14)
+    assert m.euler(0) == 2 and m.open_edges(0) == 0

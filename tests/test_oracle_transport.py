@@ -1,0 +1,215 @@
+"""Pins of the oracle's transport against closed forms (CPU only).
+
+  * narrow-beam slab transmission: P(E_dep > 0) = 1 - exp(-mu_tot x);
+  * black absorber: FEPE = (solid angle of the meshed top face) / 4 pi, from
+    the Van Oosterom-Strackee formula summed over the fan triangles;
+  * Kahn sampler: chi-square against bin integrals of the Klein-Nishina
+    angular distribution;
+  * first-interaction process frequencies = mu_i / mu_tot;
+  * pair production: deposit E - 2 mc^2 and two 511 keV photons;
+  * energy conservation per history, parity rule == nesting-tree rule;
+  * density-perturbation gradient: the slab identity dFEPE/ds = -mu x FEPE
+    and central finite differences with common random numbers;
+  * source sampling moments.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, stats
+
+from paper_2605_25963_gb300 import workloads as W
+
+MEC2 = 510.99895
+
+
+def zsig(a, b, sa, sb):
+    return abs(a - b) / math.sqrt(sa * sa + sb * sb)
+
+
+def slab_mesh(orc, boxes, materials, active, groups=None):
+    xyz, tri, ts = W.box_mesh(boxes)
+    n = len(boxes)
+    groups = groups if groups is not None else [-1] * n
+    return orc.Mesh.from_arrays(xyz, tri, ts, materials, active, groups, [-1] * n)
+
+
+def test_slab_transmission(orc):
+    x = 5.0
+    m = slab_mesh(orc, [(-1e3, -1e3, -x, 1e3, 1e3, 0.0)], [W.MAT_GE], [1])
+    t = orc.Tables.build(W.MATERIAL_CODES)
+    src = orc.Source(kind=W.SRC_PENCIL, pos=(0, 0, 10.0), dir=(0, 0, -1.0))
+    for E in (59.5, 662.0):
+        N = 200_000
+        r = orc.transport(m, t, src, E, N)
+        p_int = 1 - r.tally["n_zero"] / N
+        mu = sum(t.eval(W.MAT_GE, E))
+        expect = 1 - math.exp(-mu * x)
+        sig = math.sqrt(expect * (1 - expect) / N)
+        assert abs(p_int - expect) < 4 * sig, (E, p_int, expect)
+        assert r.tally["n_err"] == 0
+
+
+def vos_solid_angle(obs, tri_pts):
+    """Van Oosterom & Strackee (1983): solid angle of a triangle seen from obs."""
+    a, b, c = (np.asarray(p, float) - obs for p in tri_pts)
+    la, lb, lc = (np.linalg.norm(v) for v in (a, b, c))
+    num = abs(np.dot(a, np.cross(b, c)))
+    den = la * lb * lc + np.dot(a, b) * lc + np.dot(a, c) * lb + np.dot(b, c) * la
+    return 2 * math.atan2(num, den)
+
+
+def test_black_absorber_solid_angle(orc):
+    m = orc.Mesh.build(orc.Det(**W.BARE_CYLINDER.as_dict()))
+    mu = np.zeros((2, 3, 1000), np.float32)
+    mu[1, 0, :] = 1e6                      # photoabsorption only, mean free path 1 nm
+    t = orc.Tables.from_array(mu)
+    src = orc.Source(kind=W.SRC_POINT, pos=(0, 0, 100.0))
+    N = 400_000
+    r = orc.transport(m, t, src, 662.0, N)
+    xyz, tri, ts, _ = m.arrays()
+    top = [f for f in tri if np.allclose(xyz[f][:, 2], 0.0)]
+    assert len(top) == 48
+    omega = sum(vos_solid_angle(np.array([0, 0, 100.0]), xyz[f]) for f in top)
+    expect = omega / (4 * math.pi)
+    disk = (1 - 100 / math.hypot(100, 30)) / 2
+    assert expect == pytest.approx(disk, rel=3e-3)       # polygon -> disk at O(N^-2)
+    sig = math.sqrt(expect * (1 - expect) / N)
+    assert abs(r.fepe - expect) < 4 * sig
+    assert r.tally["n_fep"] + r.tally["n_zero"] == N
+
+
+@pytest.mark.parametrize("E", [59.5, 662.0, 1332.0, 2900.0])
+def test_kahn_sampler_klein_nishina(orc, E):
+    k = E / MEC2
+    n = 200_000
+    x = orc.kahn_samples(k, n, seed=5)
+    assert np.all(x >= 1.0) and np.all(x <= 1 + 2 * k + 1e-12)
+    c = 1 - (x - 1) / k
+    edges = np.linspace(-1, 1, 41)
+    obs, _ = np.histogram(c, bins=edges)
+    tot = orc.sigma_kn(k)
+    p = np.array([integrate.quad(lambda cc: orc.dsigma_kn_dcos(k, cc), a, b)[0] / tot
+                  for a, b in zip(edges[:-1], edges[1:])])
+    assert p.sum() == pytest.approx(1.0, rel=1e-9)
+    chi = stats.chisquare(obs, p * n)
+    assert chi.pvalue > 0.001, chi
+
+
+def test_first_interaction_frequencies(orc):
+    E = 1332.0
+    m = slab_mesh(orc, [(-1e4, -1e4, -1e4, 1e4, 1e4, 0.0)], [W.MAT_GE], [1])
+    t = orc.Tables.build(W.MATERIAL_CODES)
+    src = orc.Source(kind=W.SRC_PENCIL, pos=(0, 0, 1.0), dir=(0, 0, -1.0))
+    N = 300_000
+    r = orc.transport(m, t, src, E, N)
+    mu = np.array(t.eval(W.MAT_GE, E))
+    obs = [r.tally["n_first_pe"], r.tally["n_first_compton"], r.tally["n_first_pair"]]
+    assert sum(obs) == N
+    chi = stats.chisquare(obs, mu / mu.sum() * N)
+    assert chi.pvalue > 0.001, (obs, mu / mu.sum() * N)
+
+
+def test_pair_production_deposits(orc):
+    """Pair-only above threshold, black absorber below 600 keV: every interacting
+    1332 keV photon deposits E - 2 mc^2 and both 511 keV photons are absorbed."""
+    m = slab_mesh(orc, [(-1e3, -1e3, -1e3, 1e3, 1e3, 0.0)], [W.MAT_GE], [1])
+    mu = np.zeros((2, 3, 1000), np.float32)
+    lnE = np.linspace(math.log(10), math.log(3000), 1000)
+    E = np.exp(lnE)
+    mu[1, 2, E > 1100] = 0.5
+    mu[1, 0, E < 600] = 1e3
+    t = orc.Tables.from_array(mu)
+    src = orc.Source(kind=W.SRC_PENCIL, pos=(0, 0, 1.0), dir=(0, 0, -1.0))
+    r = orc.transport(m, t, src, 1332.0, 20_000, want_edep=True)
+    assert r.tally["n_first_pair"] == 20_000
+    # a 511 keV photon escapes only from pair events within ~1 um of the surface
+    assert r.fepe > 0.999
+    allowed = np.array([1332.0, 1332.0 - MEC2, 1332.0 - 2 * MEC2])
+    assert np.all(np.min(np.abs(r.edep[:, None] - allowed[None, :]), axis=1) < 1e-9)
+    assert r.tally["max_rel_energy_err"] < 1e-12
+    # thin active layer: annihilation photons leave, deposit is exactly E - 2 mc^2
+    m2 = slab_mesh(orc, [(-1e3, -1e3, -1e3, 1e3, 1e3, 0.0)], [W.MAT_GE], [1])
+    mu2 = np.zeros((2, 3, 1000), np.float32)
+    mu2[1, 2, E > 1100] = 0.5
+    t2 = orc.Tables.from_array(mu2)
+    r2 = orc.transport(m2, t2, src, 1332.0, 5_000, want_edep=True)
+    assert np.allclose(r2.edep, 1332.0 - 2 * MEC2, rtol=0, atol=1e-9)
+    assert r2.tally["sum_esc"] == pytest.approx(5_000 * 2 * MEC2, rel=1e-12)
+
+
+@pytest.mark.parametrize("E", [59.5, 1332.0])
+def test_coax_energy_conservation_and_parity(orc, E):
+    m = orc.Mesh.build(orc.Det(**W.GRAD_DET.as_dict()))
+    t = orc.Tables.build(W.MATERIAL_CODES)
+    for src in (orc.Source(kind=W.SRC_POINT, pos=(0, 0, 25.0)),
+                orc.Source(kind=W.SRC_PRISM, pos=(0, 0, 0.01), radius=35.0, height=40.0, n_sides=128)):
+        r = orc.transport(m, t, src, E, 3000)
+        T = r.tally
+        assert T["n_err"] == 0
+        assert T["n_parity_mismatch"] == 0
+        assert T["max_rel_energy_err"] < 1e-12
+        assert T["n_crossings"] > 0 and T["n_interactions"] > 0
+
+
+def test_source_moments(orc):
+    N = 20000
+    disk = orc.Source(kind=W.SRC_DISK, pos=(1.0, -2.0, 10.0), radius=30.0)
+    P = np.array([orc.sample_birth(disk, 9, h)[0] for h in range(N)])
+    r2 = (P[:, 0] - 1) ** 2 + (P[:, 1] + 2) ** 2
+    assert r2.max() <= 900.0 and np.all(P[:, 2] == 10.0)
+    assert r2.mean() == pytest.approx(450.0, rel=0.02)           # E[r^2] = R^2 / 2
+    prism = orc.Source(kind=W.SRC_PRISM, pos=(0, 0, 1.0), radius=35.0, height=40.0, n_sides=8)
+    P = np.array([orc.sample_birth(prism, 9, h)[0] for h in range(N)])
+    assert P[:, 2].min() >= 1.0 and P[:, 2].max() <= 41.0
+    assert P[:, 2].mean() == pytest.approx(21.0, abs=0.3)
+    # inside the octagon: |(x,y) . n_k| <= apothem for every edge normal
+    apo = 35.0 * math.cos(math.pi / 8)
+    for kk in range(8):
+        a = 2 * math.pi * (kk + 0.5) / 8
+        assert np.all(P[:, 0] * math.cos(a) + P[:, 1] * math.sin(a) <= apo + 1e-9)
+    # uniform in area: the fraction inside radius apo/2 equals its area fraction
+    inner = np.mean(np.hypot(P[:, 0], P[:, 1]) < apo / 2)
+    area_oct = 8 / 2 * 35.0 ** 2 * math.sin(2 * math.pi / 8)
+    assert inner == pytest.approx(math.pi * (apo / 2) ** 2 / area_oct, abs=0.015)
+    dirs = np.array([orc.sample_birth(disk, 9, h)[1] for h in range(N)])
+    assert np.allclose(np.linalg.norm(dirs, axis=1), 1.0)
+    assert abs(dirs[:, 2].mean()) < 0.02 and dirs[:, 2].var() == pytest.approx(1 / 3, rel=0.03)
+
+
+def test_dos_gradient_slab_identity(orc):
+    """Al slab (group 0) in front of a Ge slab: FEPE(s) = exp(-s mu x) K,
+    so dFEPE/ds = -mu x FEPE exactly."""
+    x = 2.0
+    m = slab_mesh(orc, [(-50, -50, -x, 50, 50, 0.0), (-50, -50, -40, 50, 50, -x - 1.0)],
+                  [W.MAT_AL, W.MAT_GE], [0, 1], groups=[0, 1])
+    t = orc.Tables.build(W.MATERIAL_CODES)
+    src = orc.Source(kind=W.SRC_PENCIL, pos=(0, 0, 5.0), dir=(0, 0, -1.0))
+    E, N = 122.0, 200_000
+    r = orc.transport(m, t, src, E, N, group_scale=(1.0, 1.0))
+    mu = sum(t.eval(W.MAT_AL, E))
+    expect = -mu * x * r.fepe
+    g, sg = r.dfepe(0), r.dfepe_sigma(0)
+    assert abs(g - expect) < 4 * sg, (g, expect, sg)
+    # central finite differences with common random numbers
+    h = 0.01
+    fp = orc.transport(m, t, src, E, N, group_scale=(1 + h, 1.0)).fepe
+    fm = orc.transport(m, t, src, E, N, group_scale=(1 - h, 1.0)).fepe
+    fd = (fp - fm) / (2 * h)
+    # with common random numbers the difference counts histories whose FEP status
+    # flips between the two scales: Poisson noise sqrt(n_flip) / (N 2h)
+    s_fd = math.sqrt(abs(fp - fm) * N) / (N * 2 * h)
+    assert abs(fd - g) < 4 * math.hypot(s_fd, sg)
+
+
+def test_history_offset_partitions_exactly(orc):
+    """Counter-based streams: two halves with history offsets add up to one run."""
+    m = orc.Mesh.build(orc.Det(**W.BARE_CYLINDER.as_dict()))
+    t = orc.Tables.build(W.MATERIAL_CODES)
+    src = orc.Source(kind=W.SRC_POINT, pos=(0, 0, 100.0))
+    full = orc.transport(m, t, src, 662.0, 20000)
+    a = orc.transport(m, t, src, 662.0, 12000)
+    b = orc.transport(m, t, src, 662.0, 8000, history_offset=12000)
+    for k in ("n_fep", "n_zero", "n_over", "n_crossings", "n_interactions"):
+        assert full.tally[k] == a.tally[k] + b.tally[k]
+    assert np.array_equal(full.spectrum, a.spectrum + b.spectrum)
