@@ -1,0 +1,340 @@
+"""Benchmark: photon histories/s on one GB300 (and N GPUs, one process each).
+
+Workload (default "coax"): p-type coaxial HPGe in an Al endcap with a Cu holder,
+128 segments per circle (~1.4e4 triangles), isotropic point source 25 mm above
+the endcap, energies 59.5 / 122 / 662 / 1332 keV, 1e8 histories each, pair
+production on, closed-form synthetic cross sections, Philox seed 1.  One step =
+the four transport launches (one per energy) with the tally reduction; the mesh,
+BVH and plans are built once before timing (like model weights).  Between timed
+steps a 512 MB buffer is written to flush L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gadep|reference]
+
+With N > 1 (torchrun), every rank transports its own history-id range (weak
+scaling); the time is the max over ranks.  --impl reference times the FP64 CPU
+oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2605_25963_gb300 import workloads as W  # noqa: E402
+
+METRIC = "photon histories/s on 1 GB300, FEPE within 3σ of oracle; batched/grad vs plain"
+UNIT = "histories/s"
+# FP32 operations per traversal unit (counted from the kernel's arithmetic):
+# node visit = 12 slab FMAs (2 FLOP) + 12 min/max -> 36; triangle test = 9 vertex
+# translations + 6 shear FMAs (12) + 6 mul + 3 sub (edge functions) + 2 add (det)
+# + 3 mul + 2 FMA (T, 5) + 1 div + 2 compares -> ~45.
+FLOP_PER_NODE = 36.0
+FLOP_PER_TRI = 45.0
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 512 << 20
+
+
+def workload_config(name, n_hist):
+    if name == "coax":
+        return dict(det=W.COAX_P, src=W.COAX_POINT_25, energies=W.COAX_ENERGIES, n_hist=n_hist or W.COAX_HISTORIES,
+                    desc="coax_p: p-type coaxial HPGe (R 30.5 L 62, bore 5x48, 0.7 mm dead layer, 0.3 um contact, "
+                         "Al endcap, Cu holder), 128 segments (13824 triangles), point source 25 mm, "
+                         "59.5/122/662/1332 keV")
+    if name == "bare":
+        return dict(det=W.BARE_CYLINDER, src=W.BARE_POINT_100, energies=(662.0,), n_hist=n_hist or 1_000_000,
+                    desc="bare Ge cylinder R 30 L 60, 48 segments (192 triangles), point source 100 mm, 662 keV")
+    raise SystemExit("unknown workload %r" % name)
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("transport.cu", "device_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2605_25963_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    e = d.get(workload)
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+class ClockSampler:
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        loaded = [s for s, _, _ in rows if s > 0.5 * rows[0][1]] or [s for s, _, _ in rows]
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": max(m for _, m, _ in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(cfg, budget_s=15.0, threads=None):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample."""
+    from oracle import oracle as O
+    threads = threads or os.cpu_count() or 1
+    om = O.Mesh.build(O.Det(**cfg["det"].as_dict()))
+    ot = O.Tables.build(W.MATERIAL_CODES)
+    s = cfg["src"]
+    osrc = O.Source(kind=s.kind, pos=s.pos, dir=s.dir, radius=s.radius, height=s.height, n_sides=s.n_sides)
+    probe = 20_000
+    t0 = time.perf_counter()
+    for E in cfg["energies"]:
+        O.transport(om, ot, osrc, E, probe, n_threads=threads)
+    rate = probe * len(cfg["energies"]) / (time.perf_counter() - t0)
+    n = int(max(probe, min(cfg["n_hist"], rate * budget_s / len(cfg["energies"]))))
+    t0 = time.perf_counter()
+    for E in cfg["energies"]:
+        O.transport(om, ot, osrc, E, n, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": n * len(cfg["energies"]) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d histories per energy x %d energies of the same workload (history ids 0..%d), "
+                      "%.1f s" % (n, len(cfg["energies"]), n - 1, dt)}
+
+
+def run_reference(args, cfg, rank, world):
+    if rank != 0:
+        return
+    cb = cpu_baseline(cfg, budget_s=max(5.0, 20.0 / max(1, args.steps + args.warmup)))
+    per_step = cb["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": per_step, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["desc"], "n_hist_per_energy": cfg["n_hist"], "seed": 1,
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": cb, "e2e": {"value": per_step, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gadep", choices=["gadep", "reference"])
+    ap.add_argument("--workload", default="coax", choices=["coax", "bare"])
+    ap.add_argument("--hist", type=int, default=0, help="histories per energy (default: the workload's)")
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    cfg = workload_config(args.workload, args.hist)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, cfg, rank, world)
+        return
+
+    import torch
+    from paper_2605_25963_gb300 import api
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+
+    t0 = time.perf_counter()
+    mesh = api.detmesh_build(cfg["det"])
+    t_mesh = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    bvh = api.gadep_bvh_build(mesh, dev)
+    t_bvh = time.perf_counter() - t0
+    mats = api.Materials.default()
+    n = cfg["n_hist"]
+    offset = rank * n                      # disjoint history ids per rank
+    opts = api.make_opts(history_offset=offset, block=args.block, chunk=args.chunk)
+    plans = [api.Plan(bvh, mats, api.make_instances([(E, cfg["src"], n, i, [])]), opts)
+             for i, E in enumerate(cfg["energies"])]
+    stream = torch.cuda.current_stream()
+    spectra = [torch.zeros(opts.n_bins, dtype=torch.int32, device="cuda") for _ in plans]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step(events=None):
+        for i, (p, s) in enumerate(zip(plans, spectra)):
+            if events is not None:
+                events[i][0].record(stream)
+            p.launch(spectra=s)
+            if events is not None:
+                events[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(dev)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    step_ms = []
+    launch_ms = [[] for _ in plans]
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in plans]
+        step(ev)
+        torch.cuda.synchronize()
+        for i, (a, b) in enumerate(ev):
+            launch_ms[i].append(a.elapsed_time(b))
+        step_ms.append(ev[0][0].elapsed_time(ev[-1][1]))
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = float(sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    hist_per_step = n * len(plans) * world
+    value = hist_per_step * args.steps / (total_ms / 1e3)
+
+    # results of the last step (FEPE per energy)
+    fepe = []
+    for p in plans:
+        res, _, _, _ = p.results(want_spectra=False)
+        fepe.append({"E_keV": None, "fepe": res[0]["fepe"], "sigma": res[0]["sigma"], "n_err": res[0]["n_err"],
+                     "segments": res[0]["n_segments"]})
+    for f, E in zip(fepe, cfg["energies"]):
+        f["E_keV"] = E
+
+    # algorithmic work of one step (instrumented copy of the kernel, untimed)
+    nodes = tris = 0
+    for i, E in enumerate(cfg["energies"]):
+        _, nv, nt = api.gadep_count_work(bvh, mats, api.make_instances([(E, cfg["src"], n, i, [])]), opts)
+        nodes += nv
+        tris += nt
+    flops_per_step = FLOP_PER_NODE * nodes + FLOP_PER_TRI * tris
+    kernel_s = sum(sum(x) for x in launch_ms) / 1e3 / args.steps     # per step, all four launches
+    achieved_tflops = flops_per_step / kernel_s / 1e12
+    sm_max = (clocks or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
+    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    segs = sum(f["segments"] for f in fepe)
+
+    # end to end through the public API with host buffers (tables and instance
+    # uploaded, spectrum and tallies read back, every call)
+    e2e = None
+    if not args.no_e2e:
+        xs_bytes = 3 * 1000 * 16            # staged tables of Ge, Al, Cu
+        n_region = len(mesh.arrays()[3]) + 1
+        h2d = len(plans) * (xs_bytes + 16 * n_region + 96 + 8)   # tables, regions, instance, prefix
+        d2h = len(plans) * (opts.n_bins * 4 + 216 + 32)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.steps)):
+            for i, E in enumerate(cfg["energies"]):
+                api.gadep_run(bvh, mats, cfg["src"], E, n, instance=i, opts=opts)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": hist_per_step * max(1, args.steps) / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(cfg)
+
+    if rank == 0:
+        g, blk, smem = plans[0].shape()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": cfg["desc"], "n_hist_per_energy": n, "energies_keV": list(cfg["energies"]),
+                       "seed": 1, "triangles": bvh.stats()["n_tri"], "grid": g, "block": blk,
+                       "smem_bytes": smem, "l2": "flushed between steps (512 MB write)",
+                       "mesh_build_s": round(t_mesh, 4), "bvh_build_s": round(t_bvh, 4)},
+            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / peak_tflops, "traffic": recorded_traffic(args.workload),
+                         "peak_note": "FP32 non-tensor: %d SMs x %d lanes x 2 x %.0f MHz (derived)" % (
+                             SM_COUNT, FP32_LANES_PER_SM, sm_max),
+                         "per_query": {"nodes": nodes / max(segs, 1), "tris": tris / max(segs, 1)},
+                         "queries_per_step": segs},
+            "cpu_baseline": cb,
+            "e2e": e2e,
+            "gpu_launches": args.steps * len(plans),
+            "clocks": clocks,
+            "fepe": fepe,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,314 @@
+/*
+ * gadep.h -- C ABI of libgadep: DetMesh detector surfaces + GPU photon transport
+ * (GB300, sm_103a).
+ *
+ * Method: DetMesh-Gadep, "Triangulated Surface Modeling and GPU-based Monte Carlo
+ * Efficiency Calibration of High-Purity Germanium Detectors" (arXiv 2605.25963).
+ * The CPU builds the detector's triangulated surfaces from a parameter array and
+ * initialises the transport; the GPU transports photons through the meshes;
+ * scoring turns tallies into the full-energy-peak efficiency (Fig. 4).
+ *
+ * Conventions for every call:
+ *   - Returns gadep_status: GADEP_OK (0) or a negative code.  No call aborts,
+ *     traps, prints or throws; gadep_last_error() returns a thread-local message
+ *     for the last failing call of the calling thread.
+ *   - Handles (detmesh_mesh, gadep_bvh, gadep_plan) are owned by the library and
+ *     released with the matching *_destroy call.  Input arrays are copied; the
+ *     caller may free them when the call returns.
+ *   - Units: mm, keV, g/cm^3; attenuation coefficients in mm^-1.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Output buffers documented as "host or device" are inspected with
+ *     cudaPointerGetAttributes; device buffers must be on the plan's device.
+ */
+#ifndef GADEP_H
+#define GADEP_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GADEP_OK = 0,
+    GADEP_E_INVAL = -1,     /* bad argument, size or pointer */
+    GADEP_E_MESH = -2,      /* mesh not closed / not manifold / solids overlap */
+    GADEP_E_NOMEM = -3,     /* host or device allocation failed */
+    GADEP_E_CUDA = -4,      /* CUDA runtime error */
+    GADEP_E_TIMEOUT = -5,   /* a bounded device wait ran out */
+    GADEP_E_DEVICE = -6     /* the device error word was set (see gadep_result.dev_err) */
+} gadep_status;
+
+/* Thread-local description of the last error of this thread (never NULL). */
+const char *gadep_last_error(void);
+/* ABI version of this header: 1. */
+int32_t gadep_abi_version(void);
+
+/* ------------------------------------------------------------------------- */
+/* DetMesh: parametric detector surfaces (Sec. 2.2-2.3, Table 2)              */
+/* ------------------------------------------------------------------------- */
+
+enum { GADEP_DET_BARE_CYLINDER = 0, GADEP_DET_COAX = 1 };
+enum { GADEP_MAT_VACUUM = 0, GADEP_MAT_GE = 1, GADEP_MAT_AL = 2, GADEP_MAT_CU = 3,
+       GADEP_MAT_WATER = 4, GADEP_N_MAT_CODES = 5 };
+
+/* Detector parameters.  d[0..9] = d1..d10 and D[0..6] = D1..D7 of Table 2:
+ *   d1 endcap (entrance window) outer radius   d2 window thickness
+ *   d3 endcap side-wall thickness               d4 crystal cup (holder) wall thickness
+ *   d5 vacuum gap window -> crystal front       d6 gap crystal side -> cup inner wall
+ *   d7 endcap depth (bottom outer face at z = -d7)
+ *   d8 cup depth (outer bottom at z = -d8)      d9 endcap bottom thickness
+ *   d10 cup bottom thickness
+ *   D1 crystal length  D2 crystal radius  D3 front-edge rounding radius
+ *   D4 outer dead-layer thickness  D5 borehole depth  D6 borehole radius
+ *   D7 borehole contact-layer thickness
+ * Frame: z axis = detector axis, z grows toward the source; the window's outer
+ * face is z = 0 (COAX) / the crystal front face is z = 0 (BARE_CYLINDER).
+ * n_theta: angular segments theta_i = 2 pi i / n_theta (Sec. 2.2.2);
+ * n_phi: rounding subdivisions phi_j = (pi/2) j / n_phi (Sec. 2.2.2);
+ * z_slices: axial bands of the crystal side wall (>= 1).
+ * sep_delta: separation applied to coincident back faces, per nesting level,
+ * innermost shifted most (Sec. 2.4.2, Fig. 6).  cup_rim_drop: cup rim below the
+ * crystal front face.  Optional source solid: regular src_n_sides-gon prism of
+ * circumradius src_r, z in [src_z0, src_z0 + src_h], water.
+ * Solids, in this order (ids are the mesh's solid indices):
+ *   BARE_CYLINDER: 0 active Ge crystal (R = D2, L = D1, rounding D3); [1 source]
+ *   COAX: 0 endcap Al, 1 endcap vacuum, 2 holder Cu, 3 crystal (dead Ge),
+ *         4 active Ge (R_active = D2 - D4, L_active = D1 - D4, Eq. of Sec. 2.3.2),
+ *         5 bore contact (dead Ge), 6 bore vacuum, [7 source]
+ * Density groups: 0 dead layer (COAX solid 3), 1 endcap, 2 active Ge, 3 source
+ * matrix; other solids -1. */
+typedef struct {
+    int32_t kind;
+    double  d[10];
+    double  D[7];
+    int32_t n_theta, n_phi, z_slices;
+    double  cup_rim_drop;
+    double  sep_delta;
+    int32_t has_source_solid;
+    double  src_r, src_h, src_z0;
+    int32_t src_n_sides;
+} detmesh_params;
+
+/* Per-solid attributes.  parent: innermost solid containing this one, -1 = world
+ * (the nesting tree, derived from the paper's parity rule at build time). */
+typedef struct {
+    int32_t material;   /* GADEP_MAT_* code = row of the attenuation tables */
+    int32_t active;     /* 1: deposits count toward the spectrum */
+    int32_t group;      /* density-scale group, -1 = none */
+    int32_t parent;
+} gadep_solid;
+
+typedef struct detmesh_mesh detmesh_mesh;
+
+/* Build the triangulated surfaces on the host (Sec. 2.2-2.3).  Triangles are
+ * counter-clockwise seen from outside (normal n = (v1-v0) x (v2-v0) points out,
+ * Sec. 2.2.2 Eq. n).  Validates: every solid closed and 2-manifold, positive
+ * volume, no two solids overlapping (sampled vertex containment).
+ * Errors: GADEP_E_INVAL (bad parameters), GADEP_E_MESH (validation failed). */
+gadep_status detmesh_build(const detmesh_params *p, detmesh_mesh **out);
+
+/* Wrap caller triangles (any closed, non-overlapping solids) as a mesh.
+ * xyz [n_vert][3] mm, tri [n_tri][3] vertex indices, tri_solid [n_tri] in
+ * [0, n_solid); material/active/group [n_solid].  Parents are derived with the
+ * parity rule.  Same validation as detmesh_build. */
+gadep_status detmesh_from_arrays(const float *xyz, int32_t n_vert, const int32_t *tri,
+                                 const int32_t *tri_solid, int32_t n_tri,
+                                 const int32_t *material, const int32_t *active,
+                                 const int32_t *group, int32_t n_solid, detmesh_mesh **out);
+
+/* Borrowed views into the mesh (valid until detmesh_destroy). Any out pointer may be NULL. */
+gadep_status detmesh_get(const detmesh_mesh *m, const float **xyz, int32_t *n_vert,
+                         const int32_t **tri, const int32_t **tri_solid, int32_t *n_tri,
+                         const gadep_solid **solids, int32_t *n_solid);
+
+/* Signed volume (mm^3, divergence theorem) and Euler characteristic V - E + F of one solid. */
+gadep_status detmesh_solid_stats(const detmesh_mesh *m, int32_t solid, double *volume,
+                                 int32_t *euler);
+
+/* Region of a point by the parity rule of Sec. 2.4.2: the innermost solid with an
+ * odd number of ray crossings (-1 = world).  FP64 on the host. */
+gadep_status detmesh_locate(const detmesh_mesh *m, const double p[3], int32_t *solid);
+
+void detmesh_destroy(detmesh_mesh *m);
+
+/* ------------------------------------------------------------------------- */
+/* Cross-section tables                                                        */
+/* ------------------------------------------------------------------------- */
+
+/* Fill mu[n_mat][3][n_grid] (photoabsorption, Compton, pair; mm^-1) at the
+ * n_grid energies E_k = exp(ln E_min + k (ln E_max - ln E_min)/(n_grid - 1))
+ * for material codes codes[n_mat], from closed-form synthetic models: Born
+ * K-shell photoabsorption x 5/4, Klein-Nishina Compton on free electrons,
+ * near-threshold pair production (stand-ins for the evaluated photon data the
+ * paper uses, Sec. 2.4.1).  Computed in FP64, stored as FP32. */
+gadep_status gadep_xs_build(const int32_t *codes, int32_t n_mat, int32_t n_grid, double E_min,
+                            double E_max, float *mu);
+
+/* ------------------------------------------------------------------------- */
+/* Acceleration structure                                                      */
+/* ------------------------------------------------------------------------- */
+
+typedef struct gadep_bvh gadep_bvh;
+typedef struct {
+    int32_t n_nodes, n_leaves, max_depth, max_leaf_tris, n_tri, n_region;
+    double  sah_cost;
+    int64_t node_bytes, tri_bytes;
+} gadep_bvh_stats;
+
+/* Binned-SAH BVH over all triangles of the mesh (the tree the paper's Gadep uses
+ * to accelerate triangle queries, Sec. 2.4.3), compacted to 64-byte nodes and
+ * 48-byte triangles, copied to `device`.  The mesh may be destroyed afterwards.
+ * device = -1 builds the host copy only (stats and validation work; transport
+ * calls on such a handle fail with GADEP_E_INVAL). */
+gadep_status gadep_bvh_build(const detmesh_mesh *m, int32_t device, gadep_bvh **out);
+gadep_status gadep_bvh_get_stats(const gadep_bvh *b, gadep_bvh_stats *out);
+/* Host-side invariant check: every triangle in exactly one leaf, child boxes
+ * inside parents, leaf boxes contain their triangles.  GADEP_E_MESH if violated. */
+gadep_status gadep_bvh_validate(const gadep_bvh *b);
+void gadep_bvh_destroy(gadep_bvh *b);
+
+/* Nearest-hit queries (the traversal step of the transport, exposed for testing).
+ * rays: device float [n][8] = (o.x, o.y, o.z, t_min, d.x, d.y, d.z, exclude) where
+ * exclude is a triangle index of the mesh stored as float bits (-1 = none).
+ * Outputs (device, [n]): t (INFINITY when nothing is hit), mesh triangle index
+ * (-1), entering flag (1 when d . n < 0).  Asynchronous on `stream`. */
+gadep_status gadep_nearest_hit(const gadep_bvh *b, const float *rays, int64_t n, float *t_out,
+                               int32_t *tri_out, int32_t *entering_out, void *stream);
+
+/* ------------------------------------------------------------------------- */
+/* Transport                                                                   */
+/* ------------------------------------------------------------------------- */
+
+/* Attenuation tables on a log grid: mu[n_mat][3][n_grid] host memory (pe, Compton,
+ * pair, mm^-1 at unit density), indexed by the solids' material codes.  Linear
+ * interpolation in ln E, end intervals clamped; mu_pair is taken as 0 at and below
+ * 2 m_e c^2. */
+typedef struct {
+    int32_t n_mat, n_grid;
+    double  E_min, E_max;
+    const float *mu;
+} gadep_materials;
+
+enum { GADEP_SRC_POINT = 0, GADEP_SRC_DISK = 1, GADEP_SRC_PRISM = 2, GADEP_SRC_PENCIL = 3 };
+/* Source: POINT at pos, isotropic.  DISK: uniform in the disk of `radius` centred
+ * at pos in the plane z = pos.z, isotropic.  PRISM: uniform in the regular
+ * n_sides-gon prism of circumradius `radius`, base centre pos, height `height`
+ * (the mesh's source solid `solid`), isotropic.  PENCIL: from pos along dir. */
+typedef struct {
+    int32_t kind;
+    float   pos[3];
+    float   dir[3];
+    float   radius, height;
+    int32_t n_sides;
+    int32_t solid;
+} gadep_source;
+
+enum { GADEP_VARIANT_AUTO = 0, GADEP_VARIANT_MEGA = 1, GADEP_VARIANT_WAVEFRONT = 2 };
+#define GADEP_MAX_GROUPS 8
+
+typedef struct {
+    uint64_t seed;            /* Philox key */
+    uint64_t history_offset;  /* first history id (runs with disjoint id ranges add up exactly) */
+    float    e_cut_keV;       /* photons below this deposit locally (default 10) */
+    float    fep_delta_keV;   /* full-energy peak: E0 - E_dep <= fep_delta (default 0.01) */
+    float    e_max_keV;       /* spectrum range [0, e_max) (default 3000) */
+    int32_t  n_bins;          /* spectrum bins (default 4096) */
+    int32_t  step_cap;        /* segments per history before it is ended as an error (1e4) */
+    int32_t  variant;         /* GADEP_VARIANT_* */
+    int32_t  block;           /* threads per block (0 = default) */
+    int32_t  chunk;           /* histories a warp takes from the work counter at once (0 = default) */
+    int32_t  blocks_per_sm;   /* persistent grid = SMs x this (0 = occupancy maximum) */
+    int32_t  n_group;         /* density groups scored by gadep_grad (<= 4) */
+    float    group_scale[GADEP_MAX_GROUPS];  /* density scale per group (default 1) */
+} gadep_opts;
+
+/* Fill *o with the defaults above (seed 1, offset 0, variant AUTO, scales 1). */
+void gadep_opts_default(gadep_opts *o);
+
+/* Per-instance result.  fepe = n_fep / n_hist; sigma = sqrt(fepe (1 - fepe) / n_hist).
+ * dev_err: OR of device error bits (1 step cap, 2 Compton sampler bound,
+ * 4 photon lost inside a solid, 8 traversal stack overflow, 16 non-finite state). */
+typedef struct {
+    uint64_t n_hist, n_fep, n_zero, n_over, n_err;
+    uint64_t n_segments, n_interactions;
+    double   fepe, sigma;
+    double   sum_dep_active, sum_dep_all, sum_esc;
+    uint32_t dev_err;
+} gadep_result;
+
+/* One transport instance: n_hist histories of energy energy_keV from `src`,
+ * history ids opts.history_offset + [0, n_hist), Philox instance id `instance`.
+ * spectrum: n_bins uint32 counts, host or device (zeroed by the call).
+ * edep_trace: optional device float [n_trace] receiving the active deposit of the
+ * first n_trace histories (NULL to skip).  result: host.  Synchronises `stream`
+ * before returning.  n_hist < 2^32 (the spectrum counts are 32-bit). */
+gadep_status gadep_run(const gadep_bvh *b, const gadep_materials *mat, const gadep_source *src,
+                       float energy_keV, uint64_t n_hist, uint32_t instance,
+                       const gadep_opts *opts, uint32_t *spectrum, float *edep_trace,
+                       uint64_t n_trace, gadep_result *result, void *stream);
+
+/* Batched: n_inst instances, each with its own energy, source, history count,
+ * Philox instance id and density scales, in one persistent launch drawing
+ * histories from a device work counter.  spectra [n_inst][n_bins] host or device;
+ * results [n_inst] host. */
+typedef struct {
+    float        energy_keV;
+    gadep_source src;
+    uint64_t     n_hist;
+    uint32_t     instance;
+    float        group_scale[GADEP_MAX_GROUPS];
+} gadep_instance;
+
+gadep_status gadep_run_batch(const gadep_bvh *b, const gadep_materials *mat, int32_t n_inst,
+                             const gadep_instance *inst, const gadep_opts *opts,
+                             uint32_t *spectra, gadep_result *results, void *stream);
+
+/* Density-perturbation gradient: for each instance and group p,
+ * dfepe[i][p] = d FEPE_i / d s_p = mean over histories of FEP * score_p with
+ * score_p = (collisions in group p)/s_p - sum over segments in group p of
+ * mu_unit(E) * length, accumulated on the fly (no stored tracks);
+ * dsigma[i][p] its standard error.  Also fills spectra/results like
+ * gadep_run_batch (the same histories).  dfepe, dsigma: host [n_inst][opts.n_group]. */
+gadep_status gadep_grad(const gadep_bvh *b, const gadep_materials *mat, int32_t n_inst,
+                        const gadep_instance *inst, const gadep_opts *opts, uint32_t *spectra,
+                        gadep_result *results, double *dfepe, double *dsigma, void *stream);
+
+/* Plans: the device-resident form of a batched run, for repeated launches and
+ * CUDA-graph capture.  gadep_plan_create uploads tables, regions and instances and
+ * allocates tallies; gadep_plan_launch only zeroes the tallies and launches the
+ * kernel on `stream` (no allocation, no host copy, no synchronisation);
+ * gadep_plan_results copies tallies back, synchronises `stream` and finalises.
+ * grad != 0 accumulates the density-perturbation scores. */
+typedef struct gadep_plan gadep_plan;
+gadep_status gadep_plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t n_inst,
+                               const gadep_instance *inst, const gadep_opts *opts, int32_t grad,
+                               gadep_plan **out);
+/* spectra_dev: device [n_inst][n_bins] uint32, or NULL to use the plan's own buffer. */
+gadep_status gadep_plan_launch(gadep_plan *p, uint32_t *spectra_dev, void *stream);
+gadep_status gadep_plan_results(gadep_plan *p, uint32_t *spectra_host, gadep_result *results,
+                                double *dfepe, double *dsigma, void *stream);
+/* Launch shape the plan uses: grid blocks, threads per block, dynamic shared bytes. */
+gadep_status gadep_plan_shape(const gadep_plan *p, int32_t *grid, int32_t *block,
+                              int32_t *smem_bytes);
+void gadep_plan_destroy(gadep_plan *p);
+
+/* Work counters of the traversal for one batch (same histories as gadep_run_batch):
+ * BVH nodes visited and triangles tested, summed over all segment queries.  Runs
+ * an instrumented copy of the transport kernel; used to turn the measured time
+ * into algorithmic bytes and FLOPs per query.  results: host [n_inst]. */
+gadep_status gadep_count_work(const gadep_bvh *b, const gadep_materials *mat, int32_t n_inst,
+                              const gadep_instance *inst, const gadep_opts *opts,
+                              gadep_result *results, uint64_t *nodes_visited,
+                              uint64_t *tris_tested, void *stream);
+
+/* Philox4x32-10 stream words of one history computed on the GPU (layout:
+ * key = (seed lo, seed hi), counter = (block, hid lo, hid hi, instance)).
+ * out: device uint32 [n_words].  For testing the device generator. */
+gadep_status gadep_philox_words(uint64_t seed, uint64_t hid, uint32_t instance, int32_t n_words,
+                                uint32_t *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

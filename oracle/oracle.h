@@ -99,6 +99,11 @@ int       orc_mesh_open_edges(const orc_mesh *m, int solid);
 /* parity-rule region of a point: innermost solid whose triangle count along +dir is odd */
 int       orc_locate(const orc_mesh *m, const double p[3], const double dir[3]);
 
+/* Nearest crossing along o + t d with t > t_min, skipping triangle `exclude`
+   (-1 none): brute force over every triangle.  Returns the triangle or -1. */
+int       orc_nearest_hit(const orc_mesh *m, const double o[3], const double d[3], double t_min,
+                          int exclude, double *t, int *entering);
+
 /* ---------------- sources and sampling ---------------- */
 enum { ORC_SRC_POINT = 0, ORC_SRC_DISK = 1, ORC_SRC_PRISM = 2, ORC_SRC_PENCIL = 3 };
 typedef struct {

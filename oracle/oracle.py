@@ -127,6 +127,8 @@ def lib():
         for f in ("orc_mesh_euler", "orc_mesh_open_edges"):
             getattr(L, f).argtypes = [C.POINTER(MeshC), C.c_int]
         L.orc_locate.argtypes = [C.POINTER(MeshC), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.orc_nearest_hit.argtypes = [C.POINTER(MeshC), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                      C.c_double, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
         L.orc_sample_birth.argtypes = [C.POINTER(SourceC), C.c_uint64, C.c_uint64, C.c_uint32,
                                        C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.orc_kahn_samples.argtypes = [C.c_double, C.c_uint64, C.c_int, C.POINTER(C.c_double)]
@@ -312,6 +314,14 @@ class Mesh:
         a = (C.c_double * 3)(*p)
         b = (C.c_double * 3)(*d)
         return lib().orc_locate(self._p, a, b)
+
+    def nearest_hit(self, o, d, t_min=0.0, exclude=-1):
+        a = (C.c_double * 3)(*o)
+        b = (C.c_double * 3)(*d)
+        t = C.c_double()
+        e = C.c_int()
+        k = lib().orc_nearest_hit(self._p, a, b, t_min, exclude, C.byref(t), C.byref(e))
+        return k, t.value, e.value
 
     def __del__(self):
         if getattr(self, "_p", None) and _lib is not None:

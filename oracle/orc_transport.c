@@ -236,6 +236,26 @@ int orc_locate(const orc_mesh *m, const double p[3], const double dir[3])
     return r;
 }
 
+int orc_nearest_hit(const orc_mesh *m, const double o[3], const double d[3], double t_min,
+                    int exclude, double *t, int *entering)
+{
+    int best = -1;
+    double bt = INFINITY;
+    int be = 0;
+    for (int k = 0; k < m->n_tri; ++k) {
+        if (k == exclude) continue;
+        double th; int ent;
+        const double *a = m->xyz + 3 * m->tri[3 * k];
+        const double *b = m->xyz + 3 * m->tri[3 * k + 1];
+        const double *c = m->xyz + 3 * m->tri[3 * k + 2];
+        if (!ray_tri(o, d, a, b, c, &th, &ent)) continue;
+        if (th > t_min && th < bt) { bt = th; best = k; be = ent; }
+    }
+    *t = bt;
+    *entering = be;
+    return best;
+}
+
 /* ---------- sampling ---------- */
 
 static void iso_dir(rng_t *r, double d[3])

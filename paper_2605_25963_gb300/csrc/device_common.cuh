@@ -1,0 +1,203 @@
+// device_common.cuh -- device building blocks of the photon transport (sm_103a).
+//
+//   philox4x32_10   counter-based generator (Salmon et al., SC'11), one stream
+//                   per history: key = seed, counter = (block, hid lo, hid hi, instance)
+//   Stream          4 words per Philox block, u = (2 (x >> 9) + 1) 2^-24
+//   Shear, tri_test watertight ray/triangle test of Woop, Benthin & Wald (JCGT
+//                   2013): vertices are translated to the ray origin, sheared so
+//                   the ray runs along +z', and the 2-D edge functions U, V, W
+//                   decide the hit; products are never contracted into FMAs so a
+//                   shared edge gives exactly opposite values in its two
+//                   triangles, and exact zeros are re-evaluated in FP64.
+//   traverse        nearest hit in the two-child BVH with a per-thread stack
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gadep {
+namespace dev {
+
+constexpr float kMeC2 = 510.99895f;
+constexpr float kTwoMeC2 = 1021.9979f;
+constexpr float kTwoPi = 6.28318530717958647692f;
+constexpr int kStack = 64;
+
+enum : uint32_t { ERR_STEPCAP = 1u, ERR_KAHN = 2u, ERR_LOST = 4u, ERR_STACK = 8u, ERR_NONFINITE = 16u };
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+struct Stream {
+    uint32_t block, c1, c2, c3;
+    uint4 buf;
+    int idx;
+    __device__ __forceinline__ void init(unsigned long long hid, uint32_t inst)
+    {
+        block = 0u; c1 = (uint32_t)hid; c2 = (uint32_t)(hid >> 32); c3 = inst; idx = 4;
+    }
+    __device__ __forceinline__ uint32_t word(uint32_t k0, uint32_t k1)
+    {
+        if (idx == 4) {
+            buf = philox4x32_10(make_uint4(block, c1, c2, c3), k0, k1);
+            ++block;
+            idx = 0;
+        }
+        const uint32_t x = idx == 0 ? buf.x : (idx == 1 ? buf.y : (idx == 2 ? buf.z : buf.w));
+        ++idx;
+        return x;
+    }
+    __device__ __forceinline__ float u01(uint32_t k0, uint32_t k1)
+    {
+        return __uint2float_rn(2u * (word(k0, k1) >> 9) + 1u) * 5.9604644775390625e-8f;
+    }
+};
+
+__device__ __forceinline__ float pick(float x, float y, float z, int k)
+{
+    return k == 0 ? x : (k == 1 ? y : z);
+}
+
+struct Shear {
+    int kx, ky, kz;
+    float Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ Shear make_shear(float dx, float dy, float dz)
+{
+    const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
+    Shear s;
+    s.kz = (ax > ay) ? ((ax > az) ? 0 : 2) : ((ay > az) ? 1 : 2);
+    s.kx = s.kz == 2 ? 0 : s.kz + 1;
+    s.ky = s.kx == 2 ? 0 : s.kx + 1;
+    const float dkz = pick(dx, dy, dz, s.kz);
+    if (dkz < 0.0f) { const int t = s.kx; s.kx = s.ky; s.ky = t; }
+    s.Sx = pick(dx, dy, dz, s.kx) / dkz;
+    s.Sy = pick(dx, dy, dz, s.ky) / dkz;
+    s.Sz = 1.0f / dkz;
+    return s;
+}
+
+// Watertight test of triangle i against the ray (o, shear); on a hit with
+// t_min < t < t_best updates t_best / best / entering (entering: d . n < 0).
+__device__ __forceinline__ void tri_test(const float4 *__restrict__ tris, int i, float ox, float oy,
+                                         float oz, const Shear &sh, float t_min, float &t_best,
+                                         int &best, bool &entering)
+{
+    const float4 a = __ldg(tris + 3 * i), b = __ldg(tris + 3 * i + 1), c = __ldg(tris + 3 * i + 2);
+    const float Ax0 = a.x - ox, Ay0 = a.y - oy, Az0 = a.z - oz;
+    const float Bx0 = b.x - ox, By0 = b.y - oy, Bz0 = b.z - oz;
+    const float Cx0 = c.x - ox, Cy0 = c.y - oy, Cz0 = c.z - oz;
+    const float Akz = pick(Ax0, Ay0, Az0, sh.kz), Bkz = pick(Bx0, By0, Bz0, sh.kz), Ckz = pick(Cx0, Cy0, Cz0, sh.kz);
+    const float Ax = fmaf(-sh.Sx, Akz, pick(Ax0, Ay0, Az0, sh.kx));
+    const float Ay = fmaf(-sh.Sy, Akz, pick(Ax0, Ay0, Az0, sh.ky));
+    const float Bx = fmaf(-sh.Sx, Bkz, pick(Bx0, By0, Bz0, sh.kx));
+    const float By = fmaf(-sh.Sy, Bkz, pick(Bx0, By0, Bz0, sh.ky));
+    const float Cx = fmaf(-sh.Sx, Ckz, pick(Cx0, Cy0, Cz0, sh.kx));
+    const float Cy = fmaf(-sh.Sy, Ckz, pick(Cx0, Cy0, Cz0, sh.ky));
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        // products of two binary32 values are exact in binary64: exact signs
+        U = (float)__dsub_rn(__dmul_rn((double)Cx, (double)By), __dmul_rn((double)Cy, (double)Bx));
+        V = (float)__dsub_rn(__dmul_rn((double)Ax, (double)Cy), __dmul_rn((double)Ay, (double)Cx));
+        W = (float)__dsub_rn(__dmul_rn((double)Bx, (double)Ay), __dmul_rn((double)By, (double)Ax));
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return;
+    const float det = U + V + W;
+    if (det == 0.0f) return;
+    const float T = U * (sh.Sz * Akz) + V * (sh.Sz * Bkz) + W * (sh.Sz * Ckz);
+    const float t = T / det;
+    if (t > t_min && t < t_best) {
+        t_best = t;
+        best = i;
+        entering = det > 0.0f;
+    }
+}
+
+struct TravStats { uint32_t nodes, tris; };
+
+// Nearest triangle along o + t d with t_min < t (exclusive), skipping `exclude`
+// (BVH-order index).  Returns the BVH-order index or -1; t_hit / entering set on
+// a hit.  Sets ERR_STACK in err if the stack would overflow (query abandoned).
+template <bool COUNT>
+__device__ __forceinline__ int traverse(const float4 *__restrict__ nodes,
+                                        const float4 *__restrict__ tris, float ox, float oy,
+                                        float oz, float dx, float dy, float dz, float t_min,
+                                        int exclude, float &t_hit, bool &entering, uint32_t &err,
+                                        TravStats &st)
+{
+    const Shear sh = make_shear(dx, dy, dz);
+    const float ix = 1.0f / (fabsf(dx) > 1e-30f ? dx : copysignf(1e-30f, dx));
+    const float iy = 1.0f / (fabsf(dy) > 1e-30f ? dy : copysignf(1e-30f, dy));
+    const float iz = 1.0f / (fabsf(dz) > 1e-30f ? dz : copysignf(1e-30f, dz));
+    const float oix = ox * ix, oiy = oy * iy, oiz = oz * iz;
+    float t_best = INFINITY;
+    int best = -1;
+    bool ent = false;
+    int stack[kStack];
+    int sp = 0;
+    int node = 0;
+    while (true) {
+        const float4 n0 = __ldg(nodes + 4 * node + 0);
+        const float4 n1 = __ldg(nodes + 4 * node + 1);
+        const float4 n2 = __ldg(nodes + 4 * node + 2);
+        const int4 n3 = __ldg(reinterpret_cast<const int4 *>(nodes) + 4 * node + 3);
+        if (COUNT) st.nodes++;
+        const float a0 = fmaf(n0.x, ix, -oix), a1 = fmaf(n0.y, ix, -oix);
+        const float a2 = fmaf(n0.z, iy, -oiy), a3 = fmaf(n0.w, iy, -oiy);
+        const float a4 = fmaf(n2.x, iz, -oiz), a5 = fmaf(n2.y, iz, -oiz);
+        const float b0 = fmaf(n1.x, ix, -oix), b1 = fmaf(n1.y, ix, -oix);
+        const float b2 = fmaf(n1.z, iy, -oiy), b3 = fmaf(n1.w, iy, -oiy);
+        const float b4 = fmaf(n2.z, iz, -oiz), b5 = fmaf(n2.w, iz, -oiz);
+        const float tmin0 = fmaxf(fmaxf(fminf(a0, a1), fminf(a2, a3)), fmaxf(fminf(a4, a5), t_min));
+        const float tmax0 = fminf(fminf(fmaxf(a0, a1), fmaxf(a2, a3)), fminf(fmaxf(a4, a5), t_best));
+        const float tmin1 = fmaxf(fmaxf(fminf(b0, b1), fminf(b2, b3)), fmaxf(fminf(b4, b5), t_min));
+        const float tmax1 = fminf(fminf(fmaxf(b0, b1), fmaxf(b2, b3)), fminf(fmaxf(b4, b5), t_best));
+        bool h0 = tmin0 <= tmax0, h1 = tmin1 <= tmax1;
+        if (h0 && n3.x < 0) {
+            const int first = ~n3.x;
+            for (int i = first; i < first + n3.z; ++i) {
+                if (COUNT) st.tris++;
+                if (i != exclude) tri_test(tris, i, ox, oy, oz, sh, t_min, t_best, best, ent);
+            }
+            h0 = false;
+        }
+        if (h1 && n3.y < 0) {
+            const int first = ~n3.y;
+            for (int i = first; i < first + n3.w; ++i) {
+                if (COUNT) st.tris++;
+                if (i != exclude) tri_test(tris, i, ox, oy, oz, sh, t_min, t_best, best, ent);
+            }
+            h1 = false;
+        }
+        if (h0 && h1) {
+            const bool first0 = tmin0 <= tmin1;
+            if (sp >= kStack) { err |= ERR_STACK; return -1; }
+            stack[sp++] = first0 ? n3.y : n3.x;
+            node = first0 ? n3.x : n3.y;
+        } else if (h0) {
+            node = n3.x;
+        } else if (h1) {
+            node = n3.y;
+        } else {
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+    }
+    if (best >= 0) { t_hit = t_best; entering = ent; }
+    return best;
+}
+
+}  // namespace dev
+}  // namespace gadep

@@ -1,0 +1,65 @@
+// gadep_internal.h -- host-side structures shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gadep.h"
+
+namespace gadep {
+
+// Error reporting: every failing C-ABI call records a thread-local message.
+gadep_status fail(gadep_status s, const char *fmt, ...);
+void clear_error();
+
+// Geometry of a closed, region-labelled triangle soup, FP64 on the host.
+struct MeshData {
+    std::vector<double> xyz;          // [n_vert][3]
+    std::vector<int32_t> tri;         // [n_tri][3]
+    std::vector<int32_t> tri_solid;   // [n_tri]
+    std::vector<gadep_solid> solids;  // [n_solid]
+    int32_t n_vert() const { return (int32_t)(xyz.size() / 3); }
+    int32_t n_tri() const { return (int32_t)tri_solid.size(); }
+    int32_t n_solid() const { return (int32_t)solids.size(); }
+};
+
+// Parity rule of Sec. 2.4.2 on the host: innermost solid with an odd number of
+// crossings along a generic ray from p; -1 = world.  Returns -2 when every
+// trial ray grazed an edge (cannot happen for points off the surfaces).
+int32_t locate_point(const MeshData &m, const double p[3]);
+double solid_volume(const MeshData &m, int32_t s);
+int32_t solid_euler(const MeshData &m, int32_t s);
+// Validate closedness/orientation and derive the nesting tree (solids[].parent).
+gadep_status validate_and_nest(MeshData &m);
+
+}  // namespace gadep
+
+struct detmesh_mesh {
+    gadep::MeshData geo;
+    std::vector<float> xyz_f;  // FP32 copy handed to the BVH and to callers
+};
+
+// Device-side compacted BVH.  Node = 4 x 16 bytes:
+//   f4[0] = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
+//   f4[1] = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
+//   f4[2] = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
+//   i4[3] = (child0, child1, count0, count1)
+// child >= 0: inner node index; child < 0: leaf with first triangle ~child and
+// `count` triangles (count 0 = empty slot, its box is inverted).
+// Triangle = 3 x float4: (v0, region id bits), (v1, 0), (v2, 0) with region id =
+// solid + 1 (0 = world).
+struct gadep_bvh {
+    int device = 0;
+    gadep::MeshData geo;                 // for host-side localisation of sources
+    std::vector<float> nodes;            // 16 floats per node
+    std::vector<float> tris;             // 12 floats per triangle (BVH order)
+    std::vector<int32_t> tri_orig;       // BVH order -> mesh triangle index
+    std::vector<int32_t> regions;        // 4 ints per region: material, active, group, parent region
+    gadep_bvh_stats stats{};
+    void *d_nodes = nullptr, *d_tris = nullptr, *d_tri_orig = nullptr, *d_regions = nullptr;
+};
+
+namespace gadep {
+gadep_status upload_bvh(gadep_bvh *b);
+void free_bvh_device(gadep_bvh *b);
+}  // namespace gadep

@@ -1,0 +1,1096 @@
+// transport.cu -- GPU photon transport through the detector mesh (paper Sec. 2.4).
+//
+// One persistent "megakernel" runs whole histories.  Every warp takes histories
+// from a device work counter in chunks (the work queue of a batched run is the
+// flattened history range of all instances, so one launch serves any number of
+// instances with uneven history counts); a lane whose history ends takes the
+// next one at once, so lanes stay busy while long histories continue.
+//
+// Per history (paper's Gadep step, photon part):
+//   birth        source position and isotropic direction (Philox stream of the
+//                history), birth region precomputed on the host by the parity rule;
+//   flight       partial cross-section free flight (Sec. 2.4.1): one number of
+//                mean free paths lambda = -ln u per flight, consumed segment by
+//                segment (lambda -= mu * length); the segment ends at the nearest
+//                triangle (BVH query, Sec. 2.4.3) or at the interaction point;
+//   crossing     region update by the nesting tree: entering solid s -> s,
+//                leaving s -> parent(s) (equal to the parity rule of Sec. 2.4.2 for
+//                nested closed solids; the tree itself is built with that rule);
+//   interaction  process by partial attenuation coefficients: photoabsorption,
+//                Compton (Kahn's rejection sampler), pair production (two 511 keV
+//                photons back to back, the second one tracked afterwards);
+//                charged secondaries deposit their energy locally;
+//   tally        energy deposited in active solids per history -> pulse-height
+//                spectrum (warp-aggregated atomics), full-energy-peak count,
+//                FP64 sums; with GRAD, density-perturbation scores
+//                score_p = n_coll,p / s_p - sum_p mu_unit * length per history.
+// Cross-section tables (float4 per grid point) and the region table are staged
+// in shared memory per block.  Arithmetic is FP32; counts are integers; sums of
+// scores are FP64.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+#include "gadep_internal.h"
+
+namespace gadep {
+
+gadep_status build_bvh_host(const detmesh_mesh *m, gadep_bvh *out);
+
+namespace dev {
+
+struct InstDev {
+    float E0;
+    int32_t src_kind;
+    float px, py, pz;
+    float dx, dy, dz;
+    float radius, height;
+    int32_t n_sides;
+    int32_t birth_region;
+    uint32_t inst_id;
+    uint32_t pad0;
+    unsigned long long hist_offset;
+    float scale[GADEP_MAX_GROUPS];
+};
+
+struct TallyDev {
+    unsigned long long n_hist, n_fep, n_zero, n_over, n_err, n_segments, n_interactions;
+    unsigned long long err_bits;
+    double sum_dep_active, sum_dep_all, sum_esc;
+    double fep_score[GADEP_MAX_GROUPS], fep_score_sq[GADEP_MAX_GROUPS];
+};
+
+struct Params {
+    const float4 *nodes;
+    const float4 *tris;
+    const float4 *xs;                 // [n_mat][n_grid] (pe, compton, pair, 0), mm^-1
+    const int4 *regions;              // (material slot or -1, active, group, parent)
+    const InstDev *inst;
+    const unsigned long long *inst_end;  // inclusive prefix sums of n_hist
+    TallyDev *tally;
+    uint32_t *spectra;
+    unsigned long long *work;
+    float *edep_trace;
+    unsigned long long n_trace;
+    unsigned long long total;
+    int n_mat, n_grid, n_region, n_inst;
+    float lnE_min, inv_dlnE;
+    uint32_t key0, key1;
+    float e_cut, fep_delta, e_max, bin_scale;
+    int n_bins, step_cap, n_group, chunk;
+};
+
+// Per-lane partial tallies of one instance, flushed on instance change and at exit.
+template <bool GRAD>
+struct Acc {
+    int inst;
+    uint32_t hist, fep, zero, over, err, seg, inter, errbits;
+    float dep, dep_all, esc;
+    double score[GRAD ? 4 : 1], score2[GRAD ? 4 : 1];
+    __device__ void reset(int i)
+    {
+        inst = i; hist = fep = zero = over = err = seg = inter = errbits = 0u;
+        dep = dep_all = esc = 0.0f;
+#pragma unroll
+        for (int g = 0; g < (GRAD ? 4 : 1); ++g) { score[g] = 0.0; score2[g] = 0.0; }
+    }
+    __device__ void flush_lane(TallyDev *T) const
+    {
+        if (inst < 0 || hist == 0) return;
+        TallyDev &t = T[inst];
+        atomicAdd(&t.n_hist, (unsigned long long)hist);
+        if (fep) atomicAdd(&t.n_fep, (unsigned long long)fep);
+        if (zero) atomicAdd(&t.n_zero, (unsigned long long)zero);
+        if (over) atomicAdd(&t.n_over, (unsigned long long)over);
+        if (err) { atomicAdd(&t.n_err, (unsigned long long)err); atomicOr(&t.err_bits, (unsigned long long)errbits); }
+        atomicAdd(&t.n_segments, (unsigned long long)seg);
+        atomicAdd(&t.n_interactions, (unsigned long long)inter);
+        atomicAdd(&t.sum_dep_active, (double)dep);
+        atomicAdd(&t.sum_dep_all, (double)dep_all);
+        atomicAdd(&t.sum_esc, (double)esc);
+        if (GRAD) {
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                atomicAdd(&t.fep_score[g], score[g]);
+                atomicAdd(&t.fep_score_sq[g], score2[g]);
+            }
+        }
+    }
+};
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <bool GRAD>
+__device__ void flush_warp(const Acc<GRAD> &a, TallyDev *T)
+{
+    int same = 0;
+    __match_all_sync(0xffffffffu, a.inst, &same);
+    if (!same || a.inst < 0) { a.flush_lane(T); return; }
+    const int lane = threadIdx.x & 31;
+    const uint32_t hist = __reduce_add_sync(0xffffffffu, a.hist);
+    const uint32_t fep = __reduce_add_sync(0xffffffffu, a.fep);
+    const uint32_t zero = __reduce_add_sync(0xffffffffu, a.zero);
+    const uint32_t over = __reduce_add_sync(0xffffffffu, a.over);
+    const uint32_t err = __reduce_add_sync(0xffffffffu, a.err);
+    const uint32_t errbits = __reduce_or_sync(0xffffffffu, a.errbits);
+    const uint32_t seg = __reduce_add_sync(0xffffffffu, a.seg);
+    const uint32_t inter = __reduce_add_sync(0xffffffffu, a.inter);
+    const double dep = warp_sum((double)a.dep), dep_all = warp_sum((double)a.dep_all),
+                 esc = warp_sum((double)a.esc);
+    double sc[4] = { 0, 0, 0, 0 }, sc2[4] = { 0, 0, 0, 0 };
+    if (GRAD) {
+#pragma unroll
+        for (int g = 0; g < 4; ++g) { sc[g] = warp_sum(a.score[g]); sc2[g] = warp_sum(a.score2[g]); }
+    }
+    if (lane == 0 && hist) {
+        TallyDev &t = T[a.inst];
+        atomicAdd(&t.n_hist, (unsigned long long)hist);
+        if (fep) atomicAdd(&t.n_fep, (unsigned long long)fep);
+        if (zero) atomicAdd(&t.n_zero, (unsigned long long)zero);
+        if (over) atomicAdd(&t.n_over, (unsigned long long)over);
+        if (err) { atomicAdd(&t.n_err, (unsigned long long)err); atomicOr(&t.err_bits, (unsigned long long)errbits); }
+        atomicAdd(&t.n_segments, (unsigned long long)seg);
+        atomicAdd(&t.n_interactions, (unsigned long long)inter);
+        atomicAdd(&t.sum_dep_active, dep);
+        atomicAdd(&t.sum_dep_all, dep_all);
+        atomicAdd(&t.sum_esc, esc);
+        if (GRAD) {
+#pragma unroll
+            for (int g = 0; g < 4; ++g) { atomicAdd(&t.fep_score[g], sc[g]); atomicAdd(&t.fep_score_sq[g], sc2[g]); }
+        }
+    }
+}
+
+__device__ __forceinline__ void rotate(float &dx, float &dy, float &dz, float c, float sphi, float cphi)
+{
+    const float s = sqrtf(fmaxf(0.0f, 1.0f - c * c));
+    const float r = sqrtf(dx * dx + dy * dy);
+    float nx, ny, nz;
+    if (r < 1e-9f) {
+        nx = s * cphi; ny = s * sphi; nz = dz > 0.0f ? c : -c;
+    } else {
+        const float ir = 1.0f / r;
+        nx = dx * c + s * (dx * dz * cphi - dy * sphi) * ir;
+        ny = dy * c + s * (dy * dz * cphi + dx * sphi) * ir;
+        nz = dz * c - s * r * cphi;
+    }
+    const float inv = rsqrtf(nx * nx + ny * ny + nz * nz);
+    dx = nx * inv; dy = ny * inv; dz = nz * inv;
+}
+
+__device__ __forceinline__ void iso_dir(Stream &rng, uint32_t k0, uint32_t k1, float &dx, float &dy, float &dz)
+{
+    const float c = 2.0f * rng.u01(k0, k1) - 1.0f;
+    float sp, cp;
+    sincospif(2.0f * rng.u01(k0, k1), &sp, &cp);
+    const float s = sqrtf(fmaxf(0.0f, 1.0f - c * c));
+    dx = s * cp; dy = s * sp; dz = c;
+}
+
+// Interpolated attenuation (pe, compton, pair) of a staged material at energy E.
+__device__ __forceinline__ void mu_at(const float4 *tab, int n_grid, float lnE_min, float inv_dl,
+                                      float E, float &pe, float &co, float &pa)
+{
+    const float g = (logf(E) - lnE_min) * inv_dl;
+    int k = (int)floorf(g);
+    k = min(max(k, 0), n_grid - 2);
+    const float f = fminf(fmaxf(g - (float)k, 0.0f), 1.0f);
+    const float4 a = tab[k], b = tab[k + 1];
+    pe = fmaf(f, b.x - a.x, a.x);
+    co = fmaf(f, b.y - a.y, a.y);
+    pa = E > kTwoMeC2 ? fmaf(f, b.z - a.z, a.z) : 0.0f;
+}
+
+template <bool GRAD, bool COUNT>
+__global__ void __launch_bounds__(256, 2) transport_kernel(const Params P, unsigned long long *counters)
+{
+    extern __shared__ float4 smem[];
+    float4 *s_xs = smem;
+    int4 *s_reg = reinterpret_cast<int4 *>(smem + (size_t)P.n_mat * P.n_grid);
+    unsigned long long *s_end = reinterpret_cast<unsigned long long *>(s_reg + P.n_region);
+    for (int i = threadIdx.x; i < P.n_mat * P.n_grid; i += blockDim.x) s_xs[i] = P.xs[i];
+    for (int i = threadIdx.x; i < P.n_region; i += blockDim.x) s_reg[i] = P.regions[i];
+    for (int i = threadIdx.x; i < P.n_inst; i += blockDim.x) s_end[i] = P.inst_end[i];
+    __syncthreads();
+
+    const uint32_t FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const uint32_t k0 = P.key0, k1 = P.key1;
+
+    unsigned long long pool_next = 0, pool_end = 0;
+    bool exhausted = false;
+    bool busy = false;
+    int inst = 0;
+    unsigned long long g_hist = 0;
+    Stream rng;
+    float ox = 0, oy = 0, oz = 0, dx = 0, dy = 0, dz = 1, E = 0, E0 = 0, lam = 0, t_cur = 0;
+    int region = 0, last_tri = -1, steps = 0;
+    bool has_sec = false;
+    float sox = 0, soy = 0, soz = 0, sdx = 0, sdy = 0, sdz = 0;
+    int sreg = 0;
+    float edep = 0, dep_all = 0, esc = 0;
+    uint32_t herr = 0;
+    float score[GRAD ? 4 : 1];
+#pragma unroll
+    for (int g = 0; g < (GRAD ? 4 : 1); ++g) score[g] = 0.0f;
+    Acc<GRAD> acc;
+    acc.reset(-1);
+    TravStats ts{ 0u, 0u };
+
+    while (true) {
+        // ---------------- refill idle lanes from the work counter ----------------
+        uint32_t need = __ballot_sync(FULL, !busy);
+        while (need && !exhausted) {
+            if (pool_next == pool_end) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(P.work, (unsigned long long)P.chunk);
+                base = __shfl_sync(FULL, base, 0);
+                if (base >= P.total) { exhausted = true; break; }
+                pool_next = base;
+                pool_end = min(base + (unsigned long long)P.chunk, P.total);
+            }
+            const uint32_t avail = (uint32_t)(pool_end - pool_next);
+            const uint32_t take = min((uint32_t)__popc(need), avail);
+            const uint32_t rank = __popc(need & lt_mask);
+            if (!busy && rank < take) {
+                g_hist = pool_next + rank;
+                while (g_hist >= s_end[inst]) ++inst;
+                if (acc.inst != inst) { acc.flush_lane(P.tally); acc.reset(inst); }
+                const InstDev &I = P.inst[inst];
+                const unsigned long long local = g_hist - (inst ? s_end[inst - 1] : 0ull);
+                rng.init(I.hist_offset + local, I.inst_id);
+                ox = I.px; oy = I.py; oz = I.pz;
+                if (I.src_kind == GADEP_SRC_DISK) {
+                    const float r = I.radius * sqrtf(rng.u01(k0, k1));
+                    float sp, cp;
+                    sincospif(2.0f * rng.u01(k0, k1), &sp, &cp);
+                    ox = fmaf(r, cp, ox); oy = fmaf(r, sp, oy);
+                } else if (I.src_kind == GADEP_SRC_PRISM) {
+                    const int N = I.n_sides;
+                    int kk = (int)((float)N * rng.u01(k0, k1));
+                    kk = min(kk, N - 1);
+                    const float s1 = sqrtf(rng.u01(k0, k1)), u3 = rng.u01(k0, k1);
+                    float sa, ca, sb, cb;
+                    sincospif(2.0f * (float)kk / (float)N, &sa, &ca);
+                    sincospif(2.0f * (float)((kk + 1) % N) / (float)N, &sb, &cb);
+                    const float wa = s1 * (1.0f - u3), wb = s1 * u3;
+                    ox += I.radius * (wa * ca + wb * cb);
+                    oy += I.radius * (wa * sa + wb * sb);
+                    oz = fmaf(I.height, rng.u01(k0, k1), oz);
+                }
+                if (I.src_kind == GADEP_SRC_PENCIL) { dx = I.dx; dy = I.dy; dz = I.dz; }
+                else iso_dir(rng, k0, k1, dx, dy, dz);
+                E = E0 = I.E0;
+                region = I.birth_region;
+                t_cur = 0.0f; last_tri = -1; steps = 0;
+                has_sec = false;
+                edep = dep_all = esc = 0.0f;
+                herr = 0u;
+#pragma unroll
+                for (int g = 0; g < (GRAD ? 4 : 1); ++g) score[g] = 0.0f;
+                lam = -logf(rng.u01(k0, k1));
+                busy = true;
+            }
+            pool_next += take;
+            need = __ballot_sync(FULL, !busy);
+        }
+        if (__ballot_sync(FULL, busy) == 0) break;
+
+        // ---------------- one segment of the current photon ----------------
+        bool finished = false;
+        if (busy) {
+            if (++steps > P.step_cap) {
+                herr |= ERR_STEPCAP;
+                finished = true;
+            } else {
+                float t_hit = INFINITY;
+                bool entering = false;
+                const int hit = traverse<COUNT>(P.nodes, P.tris, ox, oy, oz, dx, dy, dz, t_cur, last_tri,
+                                                t_hit, entering, herr, ts);
+                const int4 R = s_reg[region];
+                float pe = 0.0f, co = 0.0f, pa = 0.0f;
+                if (R.x >= 0) mu_at(s_xs + (size_t)R.x * P.n_grid, P.n_grid, P.lnE_min, P.inv_dlnE, E, pe, co, pa);
+                const float mu_unit = pe + co + pa;
+                const float sc = R.z >= 0 ? P.inst[inst].scale[R.z] : 1.0f;
+                const float mu = mu_unit * sc;
+                const float d_int = mu > 0.0f ? lam / mu : INFINITY;
+                acc.seg++;
+                if (herr & ERR_STACK) {
+                    finished = true;
+                } else if (d_int < t_hit - t_cur) {
+                    // ---- interaction ----
+                    acc.inter++;
+                    if (GRAD && R.z >= 0 && R.z < 4) score[R.z] += 1.0f / sc - mu_unit * d_int;
+                    const float tt = t_cur + d_int;
+                    const float px = fmaf(tt, dx, ox), py = fmaf(tt, dy, oy), pz = fmaf(tt, dz, oz);
+                    const float u = rng.u01(k0, k1) * mu_unit;
+                    float dep;
+                    bool alive = true;
+                    if (u < pe) {
+                        dep = E; E = 0.0f; alive = false;
+                    } else if (u < pe + co || pa == 0.0f) {
+                        const float k = E * (1.0f / kMeC2);
+                        const float a2k = 1.0f + 2.0f * k;
+                        const float br = a2k / (9.0f + 2.0f * k);
+                        float x = 1.0f;
+                        bool ok = false;
+                        for (int trial = 0; trial < 1000; ++trial) {
+                            const float r1 = rng.u01(k0, k1), r2 = rng.u01(k0, k1), r3 = rng.u01(k0, k1);
+                            if (r1 <= br) {
+                                x = 1.0f + 2.0f * k * r2;
+                                if (r3 <= 4.0f * (1.0f / x - 1.0f / (x * x))) { ok = true; break; }
+                            } else {
+                                x = a2k / (1.0f + 2.0f * k * r2);
+                                const float cc = 1.0f - (x - 1.0f) / k;
+                                if (r3 <= 0.5f * (cc * cc + 1.0f / x)) { ok = true; break; }
+                            }
+                        }
+                        if (!ok) {
+                            herr |= ERR_KAHN;
+                            dep = 0.0f;
+                            alive = false;
+                        } else {
+                            const float c = 1.0f - (x - 1.0f) / k;
+                            float sp, cp;
+                            sincospif(2.0f * rng.u01(k0, k1), &sp, &cp);
+                            const float Ep = E / x;
+                            dep = E - Ep;
+                            rotate(dx, dy, dz, c, sp, cp);
+                            E = Ep;
+                            if (E < P.e_cut) { dep += E; E = 0.0f; alive = false; }
+                        }
+                    } else {
+                        dep = E - kTwoMeC2;
+                        float nx, ny, nz;
+                        iso_dir(rng, k0, k1, nx, ny, nz);
+                        E = kMeC2;
+                        dx = nx; dy = ny; dz = nz;
+                        has_sec = true;
+                        sox = px; soy = py; soz = pz;
+                        sdx = -nx; sdy = -ny; sdz = -nz;
+                        sreg = region;
+                    }
+                    if (R.y) edep += dep;
+                    dep_all += dep;
+                    if (herr) {
+                        finished = true;
+                    } else if (alive) {
+                        ox = px; oy = py; oz = pz;
+                        t_cur = 0.0f; last_tri = -1;
+                        lam = -logf(rng.u01(k0, k1));
+                    } else if (has_sec) {
+                        has_sec = false;
+                        ox = sox; oy = soy; oz = soz; dx = sdx; dy = sdy; dz = sdz;
+                        E = kMeC2; region = sreg;
+                        t_cur = 0.0f; last_tri = -1;
+                        lam = -logf(rng.u01(k0, k1));
+                    } else {
+                        finished = true;
+                    }
+                } else if (hit < 0) {
+                    // leaves the mesh
+                    if (region != 0) herr |= ERR_LOST;
+                    esc += E;
+                    E = 0.0f;
+                    if (!herr && has_sec) {
+                        has_sec = false;
+                        ox = sox; oy = soy; oz = soz; dx = sdx; dy = sdy; dz = sdz;
+                        E = kMeC2; region = sreg;
+                        t_cur = 0.0f; last_tri = -1;
+                        lam = -logf(rng.u01(k0, k1));
+                    } else {
+                        finished = true;
+                    }
+                } else {
+                    // ---- boundary crossing ----
+                    const float len = t_hit - t_cur;
+                    lam -= mu * len;
+                    if (GRAD && R.z >= 0 && R.z < 4) score[R.z] -= mu_unit * len;
+                    t_cur = t_hit;
+                    last_tri = hit;
+                    const int treg = __float_as_int(__ldg(&P.tris[3 * hit].w));
+                    region = entering ? treg : s_reg[treg].w;
+                }
+            }
+            if (!finished && !(isfinite(dx) && isfinite(E) && isfinite(lam))) {
+                herr |= ERR_NONFINITE;
+                finished = true;
+            }
+        }
+
+        // ---------------- tally of finished histories (warp-converged) ----------------
+        const bool binned = finished && herr == 0u && edep > 0.0f && edep < P.e_max;
+        int bin = 0;
+        if (binned) bin = min((int)(edep * P.bin_scale), P.n_bins - 1);
+        const uint32_t key = binned ? (uint32_t)(inst * P.n_bins + bin) : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(FULL, key);
+        if (binned && lane == __ffs(peers) - 1)
+            atomicAdd(&P.spectra[(size_t)inst * P.n_bins + bin], (uint32_t)__popc(peers));
+        if (finished) {
+            acc.hist++;
+            if (herr) {
+                acc.err++;
+                acc.errbits |= herr;
+            } else {
+                const bool fep = (E0 - edep) <= P.fep_delta;
+                if (fep) {
+                    acc.fep++;
+                    if (GRAD) {
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) {
+                            const double s = (double)score[g];
+                            acc.score[g] += s;
+                            acc.score2[g] += s * s;
+                        }
+                    }
+                }
+                if (edep == 0.0f) acc.zero++;
+                else if (edep >= P.e_max) acc.over++;
+                acc.dep += edep; acc.dep_all += dep_all; acc.esc += esc;
+            }
+            if (g_hist < P.n_trace) P.edep_trace[g_hist] = herr ? -1.0f : edep;
+            busy = false;
+        }
+    }
+    flush_warp<GRAD>(acc, P.tally);
+    if (COUNT) {
+        atomicAdd(&counters[0], (unsigned long long)ts.nodes);
+        atomicAdd(&counters[1], (unsigned long long)ts.tris);
+    }
+}
+
+__global__ void nearest_hit_kernel(const float4 *nodes, const float4 *tris, const int32_t *tri_orig,
+                                   const int32_t *orig_to_bvh, int32_t n_tri, const float *rays, long long n,
+                                   float *t_out, int32_t *tri_out, int32_t *ent_out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float *r = rays + 8 * i;
+    const int ex_mesh = __float_as_int(r[7]);
+    const int ex = (ex_mesh >= 0 && ex_mesh < n_tri) ? orig_to_bvh[ex_mesh] : -1;
+    float t = INFINITY;
+    bool ent = false;
+    uint32_t err = 0;
+    TravStats st{ 0, 0 };
+    const int hit = traverse<false>(nodes, tris, r[0], r[1], r[2], r[4], r[5], r[6], r[3], ex, t, ent, err, st);
+    t_out[i] = hit >= 0 ? t : INFINITY;
+    tri_out[i] = hit >= 0 ? tri_orig[hit] : -1;
+    ent_out[i] = hit >= 0 ? (ent ? 1 : 0) : (err ? -2 : -1);
+}
+
+__global__ void philox_words_kernel(unsigned long long seed, unsigned long long hid, uint32_t inst,
+                                    int n_words, uint32_t *out)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (4 * b >= n_words) return;
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)hid, (uint32_t)(hid >> 32), inst),
+                                  (uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint32_t v[4] = { w.x, w.y, w.z, w.w };
+    for (int k = 0; k < 4 && 4 * b + k < n_words; ++k) out[4 * b + k] = v[k];
+}
+
+}  // namespace dev
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+gadep_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(GADEP_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+template <class T>
+gadep_status dalloc(T **p, size_t n, const char *what)
+{
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? GADEP_E_NOMEM : GADEP_E_CUDA, "%s: cudaMalloc: %s",
+                    what, cudaGetErrorString(e));
+    }
+    return GADEP_OK;
+}
+
+int is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return 0; }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+gadep_status upload_bvh(gadep_bvh *b)
+{
+    DeviceGuard g(b->device);
+    if (!g.ok) return fail(GADEP_E_CUDA, "gadep_bvh_build: cannot select device %d", b->device);
+    gadep_status st;
+    if ((st = dalloc((float **)&b->d_nodes, b->nodes.size(), "bvh nodes")) != GADEP_OK) return st;
+    if ((st = dalloc((float **)&b->d_tris, b->tris.size(), "bvh triangles")) != GADEP_OK) return st;
+    const size_t nt = b->tri_orig.size();
+    if ((st = dalloc((int32_t **)&b->d_tri_orig, 2 * nt, "bvh triangle map")) != GADEP_OK) return st;
+    std::vector<int32_t> maps(2 * nt);
+    for (size_t i = 0; i < nt; ++i) { maps[i] = b->tri_orig[i]; maps[nt + b->tri_orig[i]] = (int32_t)i; }
+    cudaError_t e;
+    if ((e = cudaMemcpy(b->d_nodes, b->nodes.data(), b->nodes.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_tris, b->tris.data(), b->tris.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_tri_orig, maps.data(), maps.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "gadep_bvh_build: upload");
+    return GADEP_OK;
+}
+
+void free_bvh_device(gadep_bvh *b)
+{
+    if (!b->d_nodes && !b->d_tris && !b->d_tri_orig) return;
+    DeviceGuard g(b->device);
+    cudaFree(b->d_nodes);
+    cudaFree(b->d_tris);
+    cudaFree(b->d_tri_orig);
+    b->d_nodes = b->d_tris = b->d_tri_orig = nullptr;
+}
+
+}  // namespace gadep
+
+using gadep::DeviceGuard;
+using gadep::is_device_ptr;
+
+struct gadep_plan {
+    const gadep_bvh *bvh = nullptr;
+    int device = 0;
+    int n_inst = 0;
+    bool grad = false;
+    gadep_opts opts{};
+    int n_bins = 0;
+    std::vector<gadep::dev::InstDev> inst;
+    std::vector<unsigned long long> inst_end;
+    float4 *d_xs = nullptr;
+    int4 *d_regions = nullptr;
+    gadep::dev::InstDev *d_inst = nullptr;
+    unsigned long long *d_end = nullptr;
+    gadep::dev::TallyDev *d_tally = nullptr;
+    uint32_t *d_spectra = nullptr;
+    unsigned long long *d_work = nullptr;
+    unsigned long long *d_counters = nullptr;
+    gadep::dev::Params P{};
+    int grid = 0, block = 256, smem = 0;
+    bool count = false;
+    uint32_t *last_spectra = nullptr;
+};
+
+namespace {
+
+using gadep::fail;
+
+gadep_status check_opts(const gadep_opts *o)
+{
+    if (!o) return fail(GADEP_E_INVAL, "NULL opts");
+    if (!(o->e_cut_keV >= 0.0f) || !(o->fep_delta_keV >= 0.0f) || !(o->e_max_keV > 0.0f) ||
+        o->n_bins < 1 || o->n_bins > (1 << 20) || o->step_cap < 1 || o->n_group < 0 ||
+        o->n_group > 4 || o->block < 0 || o->block > 256 || (o->block % 32) != 0 || o->chunk < 0 ||
+        o->blocks_per_sm < 0 || o->blocks_per_sm > 32)
+        return fail(GADEP_E_INVAL, "bad gadep_opts (n_bins in [1, 2^20], step_cap >= 1, n_group <= 4, "
+                                   "block a multiple of 32 <= 256)");
+    for (int g = 0; g < GADEP_MAX_GROUPS; ++g)
+        if (!(o->group_scale[g] >= 0.0f) || !std::isfinite(o->group_scale[g]))
+            return fail(GADEP_E_INVAL, "bad group scale");
+    return GADEP_OK;
+}
+
+template <bool GRAD, bool COUNT>
+void *kernel_ptr() { return (void *)gadep::dev::transport_kernel<GRAD, COUNT>; }
+
+void *pick_kernel(bool grad, bool count)
+{
+    if (grad) return count ? kernel_ptr<true, true>() : kernel_ptr<true, false>();
+    return count ? kernel_ptr<false, true>() : kernel_ptr<false, false>();
+}
+
+}  // namespace
+
+extern "C" void gadep_opts_default(gadep_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->seed = 1;
+    o->history_offset = 0;
+    o->e_cut_keV = 10.0f;
+    o->fep_delta_keV = 0.01f;
+    o->e_max_keV = 3000.0f;
+    o->n_bins = 4096;
+    o->step_cap = 10000;
+    o->variant = GADEP_VARIANT_AUTO;
+    o->block = 0;
+    o->chunk = 0;
+    o->blocks_per_sm = 0;
+    o->n_group = 0;
+    for (int g = 0; g < GADEP_MAX_GROUPS; ++g) o->group_scale[g] = 1.0f;
+}
+
+extern "C" gadep_status gadep_bvh_build(const detmesh_mesh *m, int32_t device, gadep_bvh **out)
+{
+    gadep::clear_error();
+    if (!m || !out) return fail(GADEP_E_INVAL, "gadep_bvh_build: NULL argument");
+    *out = nullptr;
+    if (device != -1) {
+        int n_dev = 0;
+        if (cudaGetDeviceCount(&n_dev) != cudaSuccess) { cudaGetLastError(); n_dev = 0; }
+        if (device < 0 || device >= n_dev) return fail(GADEP_E_INVAL, "gadep_bvh_build: no CUDA device %d", device);
+    }
+    gadep_bvh *b = new (std::nothrow) gadep_bvh();
+    if (!b) return fail(GADEP_E_NOMEM, "gadep_bvh_build: out of host memory");
+    b->device = device;
+    gadep_status st = gadep::build_bvh_host(m, b);
+    if (st == GADEP_OK && device >= 0) st = gadep::upload_bvh(b);
+    if (st != GADEP_OK) { gadep::free_bvh_device(b); delete b; return st; }
+    *out = b;
+    return GADEP_OK;
+}
+
+extern "C" void gadep_bvh_destroy(gadep_bvh *b)
+{
+    if (!b) return;
+    gadep::free_bvh_device(b);
+    delete b;
+}
+
+extern "C" gadep_status gadep_nearest_hit(const gadep_bvh *b, const float *rays, int64_t n, float *t_out,
+                                          int32_t *tri_out, int32_t *entering_out, void *stream)
+{
+    gadep::clear_error();
+    if (!b || n < 0 || (n > 0 && (!rays || !t_out || !tri_out || !entering_out)))
+        return fail(GADEP_E_INVAL, "gadep_nearest_hit: bad arguments");
+    if (b->device < 0 || !b->d_nodes) return fail(GADEP_E_INVAL, "gadep_nearest_hit: the BVH has no device copy");
+    if (n == 0) return GADEP_OK;
+    if (!is_device_ptr(rays) || !is_device_ptr(t_out) || !is_device_ptr(tri_out) || !is_device_ptr(entering_out))
+        return fail(GADEP_E_INVAL, "gadep_nearest_hit: rays and outputs must be device memory");
+    DeviceGuard g(b->device);
+    const int threads = 128;
+    const long long blocks = (n + threads - 1) / threads;
+    const int32_t *maps = (const int32_t *)b->d_tri_orig;
+    gadep::dev::nearest_hit_kernel<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(
+        (const float4 *)b->d_nodes, (const float4 *)b->d_tris, maps, maps + b->tri_orig.size(),
+        (int32_t)b->tri_orig.size(), rays, n,
+        t_out, tri_out, entering_out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GADEP_OK : gadep::cuda_fail(e, "gadep_nearest_hit");
+}
+
+extern "C" gadep_status gadep_philox_words(uint64_t seed, uint64_t hid, uint32_t instance, int32_t n_words,
+                                           uint32_t *out, void *stream)
+{
+    gadep::clear_error();
+    if (n_words < 0 || (n_words > 0 && !out)) return fail(GADEP_E_INVAL, "gadep_philox_words: bad arguments");
+    if (n_words == 0) return GADEP_OK;
+    if (!is_device_ptr(out)) return fail(GADEP_E_INVAL, "gadep_philox_words: out must be device memory");
+    const int blocks4 = (n_words + 3) / 4;
+    gadep::dev::philox_words_kernel<<<(blocks4 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(seed, hid, instance,
+                                                                                          n_words, out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GADEP_OK : gadep::cuda_fail(e, "gadep_philox_words");
+}
+
+extern "C" void gadep_plan_destroy(gadep_plan *p)
+{
+    if (!p) return;
+    {
+        DeviceGuard g(p->device);
+        cudaFree(p->d_xs);
+        cudaFree(p->d_regions);
+        cudaFree(p->d_inst);
+        cudaFree(p->d_end);
+        cudaFree(p->d_tally);
+        cudaFree(p->d_spectra);
+        cudaFree(p->d_work);
+        cudaFree(p->d_counters);
+    }
+    delete p;
+}
+
+namespace gadep {
+
+gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t n_inst,
+                         const gadep_instance *inst, const gadep_opts *opts, bool grad, bool count,
+                         gadep_plan **out)
+{
+    if (!out) return fail(GADEP_E_INVAL, "plan: NULL out");
+    *out = nullptr;
+    if (!b || !mat || !inst || n_inst < 1 || n_inst > 4096) return fail(GADEP_E_INVAL, "plan: bad arguments (1 <= n_inst <= 4096)");
+    if (b->device < 0 || !b->d_nodes) return fail(GADEP_E_INVAL, "plan: the BVH was built without a device copy");
+    gadep_status st = check_opts(opts);
+    if (st != GADEP_OK) return st;
+    if (!mat->mu || mat->n_mat < 1 || mat->n_mat > 1024 || mat->n_grid < 2 || mat->n_grid > 65536 ||
+        !(mat->E_min > 0.0) || !(mat->E_max > mat->E_min))
+        return fail(GADEP_E_INVAL, "plan: bad gadep_materials");
+    const MeshData &geo = b->geo;
+    // compact the materials the mesh uses; all-zero tables behave as vacuum (-1)
+    const size_t ng = (size_t)mat->n_grid;
+    std::vector<int> slot(mat->n_mat, -2);
+    std::vector<float4> xs;
+    std::vector<int32_t> regions(b->regions);
+    for (int32_t r = 0; r < (int32_t)regions.size() / 4; ++r) {
+        const int code = regions[4 * r];
+        if (code < 0 || code >= mat->n_mat) return fail(GADEP_E_INVAL, "plan: solid material %d has no table", code);
+        if (slot[code] == -2) {
+            bool any = false;
+            for (size_t c = 0; c < 3 * ng; ++c) {
+                const float v = mat->mu[(size_t)code * 3 * ng + c];
+                if (!(v >= 0.0f) || !std::isfinite(v)) return fail(GADEP_E_INVAL, "plan: negative or non-finite attenuation");
+                any = any || v > 0.0f;
+            }
+            if (!any) {
+                slot[code] = -1;
+            } else {
+                slot[code] = (int)(xs.size() / ng);
+                for (size_t g = 0; g < ng; ++g) {
+                    const float *m = mat->mu + (size_t)code * 3 * ng;
+                    xs.push_back(make_float4(m[g], m[ng + g], m[2 * ng + g], 0.0f));
+                }
+            }
+        }
+        regions[4 * r] = slot[code];
+    }
+    regions[0] = -1;  // the world region is vacuum whatever the table says
+    const int n_mat_c = (int)(xs.size() / ng);
+    gadep_plan *p = new (std::nothrow) gadep_plan();
+    if (!p) return fail(GADEP_E_NOMEM, "plan: out of host memory");
+    p->bvh = b;
+    p->device = b->device;
+    p->n_inst = n_inst;
+    p->grad = grad;
+    p->count = count;
+    p->opts = *opts;
+    p->n_bins = opts->n_bins;
+    // instances
+    unsigned long long total = 0;
+    for (int32_t i = 0; i < n_inst; ++i) {
+        const gadep_instance &I = inst[i];
+        const gadep_source &s = I.src;
+        if (!(I.energy_keV > 0.0f) || !std::isfinite(I.energy_keV) || I.energy_keV > 1e5f) {
+            gadep_plan_destroy(p);
+            return fail(GADEP_E_INVAL, "plan: instance %d energy must be in (0, 1e5] keV", i);
+        }
+        if (I.n_hist >= (1ull << 32)) { gadep_plan_destroy(p); return fail(GADEP_E_INVAL, "plan: n_hist must be < 2^32"); }
+        dev::InstDev d{};
+        d.E0 = I.energy_keV;
+        d.src_kind = s.kind;
+        d.px = s.pos[0]; d.py = s.pos[1]; d.pz = s.pos[2];
+        d.dx = s.dir[0]; d.dy = s.dir[1]; d.dz = s.dir[2];
+        d.radius = s.radius; d.height = s.height; d.n_sides = s.n_sides;
+        d.inst_id = I.instance;
+        d.hist_offset = opts->history_offset;
+        for (int g = 0; g < GADEP_MAX_GROUPS; ++g) {
+            d.scale[g] = I.group_scale[g];
+            if (!(d.scale[g] >= 0.0f) || !std::isfinite(d.scale[g])) { gadep_plan_destroy(p); return fail(GADEP_E_INVAL, "plan: bad group scale"); }
+        }
+        if (s.kind == GADEP_SRC_PRISM) {
+            if (s.solid < 0 || s.solid >= geo.n_solid() || s.n_sides < 3 || !(s.radius > 0) || !(s.height > 0)) {
+                gadep_plan_destroy(p);
+                return fail(GADEP_E_INVAL, "plan: prism source needs a valid solid, n_sides >= 3, radius, height");
+            }
+            d.birth_region = s.solid + 1;
+        } else if (s.kind == GADEP_SRC_POINT || s.kind == GADEP_SRC_DISK || s.kind == GADEP_SRC_PENCIL) {
+            if (s.kind == GADEP_SRC_DISK && !(s.radius > 0)) { gadep_plan_destroy(p); return fail(GADEP_E_INVAL, "plan: disk radius"); }
+            if (s.kind == GADEP_SRC_PENCIL) {
+                const double n2 = (double)s.dir[0] * s.dir[0] + (double)s.dir[1] * s.dir[1] + (double)s.dir[2] * s.dir[2];
+                if (!(std::fabs(n2 - 1.0) < 1e-5)) { gadep_plan_destroy(p); return fail(GADEP_E_INVAL, "plan: pencil direction must be a unit vector"); }
+            }
+            const double q[3] = { s.pos[0], s.pos[1], s.pos[2] };
+            const int32_t r = locate_point(geo, q);
+            if (r == -2) { gadep_plan_destroy(p); return fail(GADEP_E_INVAL, "plan: source position lies on a surface"); }
+            d.birth_region = r + 1;
+        } else {
+            gadep_plan_destroy(p);
+            return fail(GADEP_E_INVAL, "plan: unknown source kind %d", s.kind);
+        }
+        p->inst.push_back(d);
+        total += I.n_hist;
+        p->inst_end.push_back(total);
+    }
+    // launch shape
+    p->block = opts->block ? opts->block : 256;
+    const size_t smem = xs.size() * sizeof(float4) + regions.size() * 4 + (size_t)n_inst * 8;
+    p->smem = (int)smem;
+    DeviceGuard g(p->device);
+    if (!g.ok) { gadep_plan_destroy(p); return fail(GADEP_E_CUDA, "plan: cannot select device %d", p->device); }
+    int dev_smem = 0, n_sm = 0;
+    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, p->device);
+    if (smem > (size_t)dev_smem) {
+        gadep_plan_destroy(p);
+        return fail(GADEP_E_INVAL, "plan: tables need %zu bytes of shared memory, the device has %d", smem, dev_smem);
+    }
+    void *kfn = pick_kernel(grad, count);
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) { gadep_plan_destroy(p); return cuda_fail(e, "plan: cudaFuncSetAttribute"); }
+    int bps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn, p->block, smem);
+    if (e != cudaSuccess || bps < 1) { gadep_plan_destroy(p); return fail(GADEP_E_CUDA, "plan: kernel does not fit on the device"); }
+    if (opts->blocks_per_sm > 0) bps = std::min(bps, opts->blocks_per_sm);
+    p->grid = n_sm * bps;
+    // device buffers
+    if ((st = dalloc(&p->d_xs, std::max<size_t>(xs.size(), 1), "plan tables")) != GADEP_OK ||
+        (st = dalloc((int32_t **)&p->d_regions, regions.size(), "plan regions")) != GADEP_OK ||
+        (st = dalloc(&p->d_inst, (size_t)n_inst, "plan instances")) != GADEP_OK ||
+        (st = dalloc(&p->d_end, (size_t)n_inst, "plan prefix")) != GADEP_OK ||
+        (st = dalloc(&p->d_tally, (size_t)n_inst, "plan tallies")) != GADEP_OK ||
+        (st = dalloc(&p->d_spectra, (size_t)n_inst * p->n_bins, "plan spectra")) != GADEP_OK ||
+        (st = dalloc(&p->d_work, 1, "plan work counter")) != GADEP_OK ||
+        (st = dalloc(&p->d_counters, 4, "plan counters")) != GADEP_OK) {
+        gadep_plan_destroy(p);
+        return st;
+    }
+    if ((!xs.empty() && (e = cudaMemcpy(p->d_xs, xs.data(), xs.size() * sizeof(float4), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (e = cudaMemcpy(p->d_regions, regions.data(), regions.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(p->d_inst, p->inst.data(), p->inst.size() * sizeof(dev::InstDev), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(p->d_end, p->inst_end.data(), p->inst_end.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        gadep_plan_destroy(p);
+        return cuda_fail(e, "plan: upload");
+    }
+    dev::Params &P = p->P;
+    P.nodes = (const float4 *)b->d_nodes;
+    P.tris = (const float4 *)b->d_tris;
+    P.xs = p->d_xs;
+    P.regions = p->d_regions;
+    P.inst = p->d_inst;
+    P.inst_end = p->d_end;
+    P.tally = p->d_tally;
+    P.spectra = p->d_spectra;
+    P.work = p->d_work;
+    P.edep_trace = nullptr;
+    P.n_trace = 0;
+    P.total = total;
+    P.n_mat = n_mat_c;
+    P.n_grid = mat->n_grid;
+    P.n_region = (int)(regions.size() / 4);
+    P.n_inst = n_inst;
+    P.lnE_min = (float)std::log(mat->E_min);
+    P.inv_dlnE = (float)((mat->n_grid - 1) / (std::log(mat->E_max) - std::log(mat->E_min)));
+    P.key0 = (uint32_t)opts->seed;
+    P.key1 = (uint32_t)(opts->seed >> 32);
+    P.e_cut = opts->e_cut_keV;
+    P.fep_delta = opts->fep_delta_keV;
+    P.e_max = opts->e_max_keV;
+    P.bin_scale = (float)opts->n_bins / opts->e_max_keV;
+    P.n_bins = opts->n_bins;
+    P.step_cap = opts->step_cap;
+    P.n_group = opts->n_group;
+    P.chunk = opts->chunk > 0 ? opts->chunk : 256;
+    *out = p;
+    return GADEP_OK;
+}
+
+gadep_status plan_launch(gadep_plan *p, uint32_t *spectra_dev, float *edep_trace, uint64_t n_trace,
+                         cudaStream_t s)
+{
+    DeviceGuard g(p->device);
+    dev::Params P = p->P;
+    if (spectra_dev) P.spectra = spectra_dev;
+    P.edep_trace = edep_trace;
+    P.n_trace = edep_trace ? n_trace : 0;
+    p->last_spectra = P.spectra;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(p->d_tally, 0, sizeof(dev::TallyDev) * p->n_inst, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(P.spectra, 0, sizeof(uint32_t) * (size_t)p->n_inst * p->n_bins, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->d_work, 0, sizeof(unsigned long long), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->d_counters, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
+        return cuda_fail(e, "plan launch: memset");
+    if (P.total == 0) return GADEP_OK;
+    if (p->grad) {
+        if (p->count) dev::transport_kernel<true, true><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
+        else dev::transport_kernel<true, false><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
+    } else {
+        if (p->count) dev::transport_kernel<false, true><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
+        else dev::transport_kernel<false, false><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? GADEP_OK : cuda_fail(e, "plan launch: kernel");
+}
+
+gadep_status plan_results(gadep_plan *p, uint32_t *spectra_host, gadep_result *res, double *dfepe,
+                          double *dsigma, unsigned long long *counters, cudaStream_t s)
+{
+    DeviceGuard g(p->device);
+    std::vector<dev::TallyDev> T(p->n_inst);
+    cudaError_t e = cudaMemcpyAsync(T.data(), p->d_tally, sizeof(dev::TallyDev) * p->n_inst, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && spectra_host)
+        e = cudaMemcpyAsync(spectra_host, p->last_spectra ? p->last_spectra : p->d_spectra,
+                            sizeof(uint32_t) * (size_t)p->n_inst * p->n_bins, cudaMemcpyDeviceToHost, s);
+    unsigned long long cnt[4] = { 0, 0, 0, 0 };
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, p->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "plan results");
+    if (counters) std::memcpy(counters, cnt, sizeof(cnt));
+    bool dev_err = false;
+    for (int i = 0; i < p->n_inst; ++i) {
+        const dev::TallyDev &t = T[i];
+        if (res) {
+            gadep_result &r = res[i];
+            std::memset(&r, 0, sizeof(r));
+            r.n_hist = t.n_hist; r.n_fep = t.n_fep; r.n_zero = t.n_zero; r.n_over = t.n_over; r.n_err = t.n_err;
+            r.n_segments = t.n_segments; r.n_interactions = t.n_interactions;
+            r.fepe = t.n_hist ? (double)t.n_fep / (double)t.n_hist : 0.0;
+            r.sigma = t.n_hist ? std::sqrt(r.fepe * (1.0 - r.fepe) / (double)t.n_hist) : 0.0;
+            r.sum_dep_active = t.sum_dep_active; r.sum_dep_all = t.sum_dep_all; r.sum_esc = t.sum_esc;
+            r.dev_err = (uint32_t)t.err_bits;
+        }
+        if (t.err_bits) dev_err = true;
+        if (p->grad) {
+            const double n = (double)t.n_hist;
+            for (int g2 = 0; g2 < p->opts.n_group; ++g2) {
+                const double m1 = n > 0 ? t.fep_score[g2] / n : 0.0;
+                const double m2 = n > 0 ? t.fep_score_sq[g2] / n : 0.0;
+                if (dfepe) dfepe[(size_t)i * p->opts.n_group + g2] = m1;
+                if (dsigma) dsigma[(size_t)i * p->opts.n_group + g2] = n > 0 ? std::sqrt(std::max(m2 - m1 * m1, 0.0) / n) : 0.0;
+            }
+        }
+    }
+    if (dev_err) return fail(GADEP_E_DEVICE, "device error word set (see gadep_result.dev_err)");
+    return GADEP_OK;
+}
+
+}  // namespace gadep
+
+extern "C" gadep_status gadep_plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t n_inst,
+                                          const gadep_instance *inst, const gadep_opts *opts, int32_t grad,
+                                          gadep_plan **out)
+{
+    gadep::clear_error();
+    return gadep::plan_create(b, mat, n_inst, inst, opts, grad != 0, false, out);
+}
+
+extern "C" gadep_status gadep_plan_launch(gadep_plan *p, uint32_t *spectra_dev, void *stream)
+{
+    gadep::clear_error();
+    if (!p) return fail(GADEP_E_INVAL, "gadep_plan_launch: NULL plan");
+    if (spectra_dev && !is_device_ptr(spectra_dev)) return fail(GADEP_E_INVAL, "gadep_plan_launch: spectra must be device memory");
+    return gadep::plan_launch(p, spectra_dev, nullptr, 0, (cudaStream_t)stream);
+}
+
+extern "C" gadep_status gadep_plan_results(gadep_plan *p, uint32_t *spectra_host, gadep_result *results,
+                                           double *dfepe, double *dsigma, void *stream)
+{
+    gadep::clear_error();
+    if (!p) return fail(GADEP_E_INVAL, "gadep_plan_results: NULL plan");
+    return gadep::plan_results(p, spectra_host, results, dfepe, dsigma, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" gadep_status gadep_plan_shape(const gadep_plan *p, int32_t *grid, int32_t *block, int32_t *smem_bytes)
+{
+    gadep::clear_error();
+    if (!p) return fail(GADEP_E_INVAL, "gadep_plan_shape: NULL plan");
+    if (grid) *grid = p->grid;
+    if (block) *block = p->block;
+    if (smem_bytes) *smem_bytes = p->smem;
+    return GADEP_OK;
+}
+
+namespace {
+
+// run a batch through a temporary plan; spectra may be host or device
+gadep_status run_batch(const gadep_bvh *b, const gadep_materials *mat, int32_t n_inst, const gadep_instance *inst,
+                       const gadep_opts *opts, bool grad, uint32_t *spectra, float *edep_trace, uint64_t n_trace,
+                       gadep_result *results, double *dfepe, double *dsigma, unsigned long long *counters,
+                       bool count, cudaStream_t s)
+{
+    if (edep_trace && !is_device_ptr(edep_trace)) return fail(GADEP_E_INVAL, "edep_trace must be device memory");
+    gadep_plan *p = nullptr;
+    gadep_status st = gadep::plan_create(b, mat, n_inst, inst, opts, grad, count, &p);
+    if (st != GADEP_OK) return st;
+    const bool dev_spec = spectra && is_device_ptr(spectra);
+    st = gadep::plan_launch(p, dev_spec ? spectra : nullptr, edep_trace, n_trace, s);
+    if (st == GADEP_OK)
+        st = gadep::plan_results(p, dev_spec ? nullptr : spectra, results, dfepe, dsigma, counters, s);
+    gadep_plan_destroy(p);
+    return st;
+}
+
+}  // namespace
+
+extern "C" gadep_status gadep_run(const gadep_bvh *b, const gadep_materials *mat, const gadep_source *src,
+                                  float energy_keV, uint64_t n_hist, uint32_t instance, const gadep_opts *opts,
+                                  uint32_t *spectrum, float *edep_trace, uint64_t n_trace, gadep_result *result,
+                                  void *stream)
+{
+    gadep::clear_error();
+    if (!src || !result) return fail(GADEP_E_INVAL, "gadep_run: NULL source or result");
+    gadep_instance I;
+    std::memset(&I, 0, sizeof(I));
+    I.energy_keV = energy_keV;
+    I.src = *src;
+    I.n_hist = n_hist;
+    I.instance = instance;
+    if (opts)
+        for (int g = 0; g < GADEP_MAX_GROUPS; ++g) I.group_scale[g] = opts->group_scale[g];
+    return run_batch(b, mat, 1, &I, opts, false, spectrum, edep_trace, n_trace, result, nullptr, nullptr,
+                     nullptr, false, (cudaStream_t)stream);
+}
+
+extern "C" gadep_status gadep_run_batch(const gadep_bvh *b, const gadep_materials *mat, int32_t n_inst,
+                                        const gadep_instance *inst, const gadep_opts *opts, uint32_t *spectra,
+                                        gadep_result *results, void *stream)
+{
+    gadep::clear_error();
+    if (!results) return fail(GADEP_E_INVAL, "gadep_run_batch: NULL results");
+    return run_batch(b, mat, n_inst, inst, opts, false, spectra, nullptr, 0, results, nullptr, nullptr, nullptr,
+                     false, (cudaStream_t)stream);
+}
+
+extern "C" gadep_status gadep_grad(const gadep_bvh *b, const gadep_materials *mat, int32_t n_inst,
+                                   const gadep_instance *inst, const gadep_opts *opts, uint32_t *spectra,
+                                   gadep_result *results, double *dfepe, double *dsigma, void *stream)
+{
+    gadep::clear_error();
+    if (!results || !dfepe || !dsigma) return fail(GADEP_E_INVAL, "gadep_grad: NULL output");
+    if (!opts || opts->n_group < 1) return fail(GADEP_E_INVAL, "gadep_grad: opts.n_group must be >= 1");
+    return run_batch(b, mat, n_inst, inst, opts, true, spectra, nullptr, 0, results, dfepe, dsigma, nullptr, false,
+                     (cudaStream_t)stream);
+}
+
+// Work counters of the traversal (nodes visited, triangles tested) for one batch:
+// the COUNT instantiation of the same kernel, used to derive algorithmic bytes
+// and FLOPs per segment query.
+extern "C" gadep_status gadep_count_work(const gadep_bvh *b, const gadep_materials *mat, int32_t n_inst,
+                                         const gadep_instance *inst, const gadep_opts *opts,
+                                         gadep_result *results, uint64_t *nodes_visited,
+                                         uint64_t *tris_tested, void *stream)
+{
+    gadep::clear_error();
+    if (!results || !nodes_visited || !tris_tested) return fail(GADEP_E_INVAL, "gadep_count_work: NULL output");
+    unsigned long long c[4] = { 0, 0, 0, 0 };
+    gadep_status st = run_batch(b, mat, n_inst, inst, opts, false, nullptr, nullptr, 0, results, nullptr, nullptr,
+                                c, true, (cudaStream_t)stream);
+    *nodes_visited = c[0];
+    *tris_tested = c[1];
+    return st;
+}

@@ -1,0 +1,163 @@
+"""Host-side checks of libgadep (no GPU needed).
+
+  * the library loads and exports every function include/gadep.h declares;
+  * DetMesh surfaces equal the oracle's surfaces (vertex sets, triangle counts,
+    per-solid volumes, Euler characteristics, nesting tree);
+  * the library's attenuation tables equal the oracle's tables to 1 ulp;
+  * BVH invariants on the host copy;
+  * invalid inputs fail with status codes, broken meshes with GADEP_E_MESH.
+"""
+import ctypes as C
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2605_25963_gb300 import api, capi
+from paper_2605_25963_gb300 import workloads as W
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gadep.h")
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "defined")))
+
+
+def test_library_exports_every_declared_symbol():
+    L = capi.load()
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(capi.EXPORTS)
+    assert L.gadep_abi_version() == 1
+
+
+def det_pair(orc, d):
+    return api.detmesh_build(d), orc.Mesh.build(orc.Det(**d.as_dict()))
+
+
+@pytest.mark.parametrize("name", ["BARE_CYLINDER", "COAX_P", "COAX_N", "BATCH_DET", "GRAD_DET"])
+def test_detmesh_matches_oracle_surfaces(orc, name):
+    d = getattr(W, name)
+    m, o = det_pair(orc, d)
+    X, T, S, solids = m.arrays()
+    OX, OT, OS, osol = o.arrays()
+    assert len(T) == len(OT) and len(solids) == o.n_solid
+    for s in range(o.n_solid):
+        v, e = m.solid_stats(s)
+        assert v == pytest.approx(o.volume(s), rel=1e-6), s
+        assert e == o.euler(s) == 2, s
+        # the same vertex set per solid (FP32 storage vs FP64)
+        a = np.unique(np.round(X[np.unique(T[S == s])].astype(np.float64), 4), axis=0)
+        b = np.unique(np.round(OX[np.unique(OT[OS == s])], 4), axis=0)
+        assert a.shape == b.shape, s
+        assert np.allclose(a, b, atol=2e-4), s
+        assert (S == s).sum() == (OS == s).sum()
+        assert solids[s]["material"] == osol["material"][s]
+        assert solids[s]["active"] == osol["active"][s]
+        assert solids[s]["group"] == osol["group"][s]
+        assert solids[s]["parent"] == osol["parent"][s], (s, solids[s], osol["parent"][s])
+    # outward normals: n = (v1 - v0) x (v2 - v0) has positive flux volume per solid
+    for s in range(o.n_solid):
+        assert m.solid_stats(s)[0] > 0
+
+
+def test_detmesh_locate_matches_oracle(orc):
+    m, o = det_pair(orc, W.GRAD_DET)
+    rng = np.random.default_rng(7)
+    pts = np.column_stack([rng.uniform(-45, 45, 400), rng.uniform(-45, 45, 400), rng.uniform(-130, 45, 400)])
+    for p in pts:
+        assert m.locate(p) == o.locate(p, (0.2672612, 0.5345225, 0.8017837)), p
+
+
+def test_tables_match_oracle(orc):
+    mu = api.gadep_xs_build()
+    ref = orc.Tables.build(W.MATERIAL_CODES).array()
+    assert mu.shape == ref.shape == (5, 3, 1000)
+    a = mu.view(np.int32).astype(np.int64)
+    b = ref.view(np.int32).astype(np.int64)
+    assert np.max(np.abs(a - b)) <= 1          # at most one unit in the last place
+    assert np.array_equal(mu[0], np.zeros_like(mu[0]))
+    assert np.all(mu[:, 2, :][:, np.exp(np.linspace(np.log(10), np.log(3000), 1000)) <= 2 * 510.99895] == 0)
+
+
+@pytest.mark.parametrize("name", ["BARE_CYLINDER", "COAX_P", "GRAD_DET"])
+def test_bvh_host_invariants(name):
+    m = api.detmesh_build(getattr(W, name))
+    b = api.gadep_bvh_build(m, device=-1)
+    b.validate()
+    st = b.stats()
+    assert st["n_tri"] == len(m.arrays()[1])
+    assert st["max_leaf_tris"] <= 4
+    assert st["max_depth"] < 60
+    assert st["node_bytes"] == 64 * st["n_nodes"] and st["tri_bytes"] == 48 * st["n_tri"]
+    # a binary tree over leaves with <= 4 triangles
+    assert st["n_leaves"] == st["n_nodes"] + 1
+    assert st["n_leaves"] >= st["n_tri"] / 4
+
+
+def test_invalid_parameters_rejected():
+    bad = W.Detector(**{**W.COAX_P.as_dict(), "n_theta": 2})
+    with pytest.raises(capi.GadepError) as e:
+        api.detmesh_build(bad)
+    assert e.value.status == capi.GADEP_E_INVAL
+    overlapping = W.Detector(**{**W.COAX_P.as_dict(), "D": (62.0, 40.0, 3.0, 0.7, 48.0, 5.0, 0.0003)})
+    with pytest.raises(capi.GadepError) as e:
+        api.detmesh_build(overlapping)
+    assert e.value.status == capi.GADEP_E_INVAL
+    with pytest.raises(capi.GadepError):
+        api.detmesh_build(W.Detector(kind=7))
+    with pytest.raises(capi.GadepError):
+        api.gadep_xs_build(codes=(1, 99))
+
+
+def test_broken_meshes_rejected():
+    xyz, tri, ts = W.box_mesh([(0, 0, 0, 1, 1, 1)])
+    ok = api.detmesh_from_arrays(xyz, tri, ts, [1], [1], [-1])
+    assert ok.solid_stats(0)[0] == pytest.approx(1.0)
+    # open surface: drop one triangle
+    with pytest.raises(capi.GadepError) as e:
+        api.detmesh_from_arrays(xyz, tri[:-1], ts[:-1], [1], [1], [-1])
+    assert e.value.status == capi.GADEP_E_MESH
+    # inward normals
+    with pytest.raises(capi.GadepError) as e:
+        api.detmesh_from_arrays(xyz, tri[:, ::-1], ts, [1], [1], [-1])
+    assert e.value.status == capi.GADEP_E_MESH
+    # one flipped triangle: inconsistent orientation
+    t2 = tri.copy()
+    t2[3] = t2[3][::-1]
+    with pytest.raises(capi.GadepError) as e:
+        api.detmesh_from_arrays(xyz, t2, ts, [1], [1], [-1])
+    assert e.value.status == capi.GADEP_E_MESH
+    # two intersecting boxes
+    xyz2, tri2, ts2 = W.box_mesh([(0, 0, 0, 2, 2, 2), (1, 1, 1, 3, 3, 3)])
+    with pytest.raises(capi.GadepError) as e:
+        api.detmesh_from_arrays(xyz2, tri2, ts2, [1, 2], [1, 0], [-1, -1])
+    assert e.value.status == capi.GADEP_E_MESH
+    # nested boxes: nesting tree from the parity rule
+    xyz3, tri3, ts3 = W.box_mesh([(0, 0, 0, 4, 4, 4), (1, 1, 1, 3, 3, 3), (10, 0, 0, 11, 1, 1)])
+    m = api.detmesh_from_arrays(xyz3, tri3, ts3, [1, 2, 3], [0, 1, 0], [-1, -1, -1])
+    assert [s["parent"] for s in m.arrays()[3]] == [-1, 0, -1]
+    assert m.locate((2, 2, 2)) == 1 and m.locate((0.5, 2, 2)) == 0 and m.locate((5, 5, 5)) == -1
+
+
+def test_transport_needs_device_copy():
+    m = api.detmesh_build(W.BARE_CYLINDER)
+    b = api.gadep_bvh_build(m, device=-1)
+    mat = api.Materials.default()
+    with pytest.raises(capi.GadepError) as e:
+        api.gadep_run(b, mat, W.BARE_POINT_100, 662.0, 10)
+    assert e.value.status == capi.GADEP_E_INVAL
+
+
+def test_opts_defaults():
+    o = api.make_opts()
+    assert o.seed == 1 and o.n_bins == 4096 and o.step_cap == 10000
+    assert abs(o.e_cut_keV - 10.0) < 1e-6 and abs(o.fep_delta_keV - 0.01) < 1e-9
+    assert list(o.group_scale) == [1.0] * 8
