@@ -170,11 +170,17 @@ void gadep_bvh_destroy(gadep_bvh *b);
 
 /* Nearest-hit queries (the traversal step of the transport, exposed for testing).
  * rays: device float [n][8] = (o.x, o.y, o.z, t_min, d.x, d.y, d.z, exclude) where
- * exclude is a triangle index of the mesh stored as float bits (-1 = none).
+ * exclude is a triangle index of the mesh stored as float bits (-1 = none); hits
+ * need t > t_min.  regions: optional device int32 [n], the region of each origin
+ * (0 = world, s + 1 = solid s): the query then searches only that region's tree
+ * (its own solid's and its child solids' triangles, the surfaces a photon there
+ * can reach first, Sec. 2.4.2 nesting); NULL searches every triangle.
  * Outputs (device, [n]): t (INFINITY when nothing is hit), mesh triangle index
- * (-1), entering flag (1 when d . n < 0).  Asynchronous on `stream`. */
-gadep_status gadep_nearest_hit(const gadep_bvh *b, const float *rays, int64_t n, float *t_out,
-                               int32_t *tri_out, int32_t *entering_out, void *stream);
+ * (-1), entering flag (1 when d . n < 0; -2 when the traversal stack overflowed).
+ * Asynchronous on `stream`. */
+gadep_status gadep_nearest_hit(const gadep_bvh *b, const float *rays, const int32_t *regions,
+                               int64_t n, float *t_out, int32_t *tri_out, int32_t *entering_out,
+                               void *stream);
 
 /* ------------------------------------------------------------------------- */
 /* Transport                                                                   */

@@ -161,16 +161,20 @@ def gadep_bvh_build(mesh: Mesh, device: int = 0) -> Bvh:
     return Bvh(h)
 
 
-def gadep_nearest_hit(bvh: Bvh, rays, stream=None):
-    """rays: CUDA float32 tensor [n, 8] = (o, t_min, d, exclude as float bits)."""
+def gadep_nearest_hit(bvh: Bvh, rays, regions=None, stream=None):
+    """rays: CUDA float32 tensor [n, 8] = (o, t_min, d, exclude as float bits);
+    regions: optional CUDA int32 tensor [n] (0 = world, s + 1 = solid s)."""
     torch = _torch()
     assert rays.is_cuda and rays.dtype == torch.float32 and rays.shape[1] == 8 and rays.is_contiguous()
     n = rays.shape[0]
+    if regions is not None:
+        assert regions.is_cuda and regions.dtype == torch.int32 and regions.numel() == n
     t = torch.empty(n, dtype=torch.float32, device=rays.device)
     tri = torch.empty(n, dtype=torch.int32, device=rays.device)
     ent = torch.empty(n, dtype=torch.int32, device=rays.device)
-    check(capi.load().gadep_nearest_hit(bvh.handle, rays.data_ptr(), n, t.data_ptr(), tri.data_ptr(),
-                                        ent.data_ptr(), _stream(stream)))
+    check(capi.load().gadep_nearest_hit(bvh.handle, rays.data_ptr(),
+                                        regions.data_ptr() if regions is not None else None, n,
+                                        t.data_ptr(), tri.data_ptr(), ent.data_ptr(), _stream(stream)))
     return t, tri, ent
 
 

@@ -121,7 +121,7 @@ def load(build_if_missing: bool = True):
         "gadep_bvh_get_stats": (st, [vp, P(gadep_bvh_stats)]),
         "gadep_bvh_validate": (st, [vp]),
         "gadep_bvh_destroy": (None, [vp]),
-        "gadep_nearest_hit": (st, [vp, vp, C.c_int64, vp, vp, vp, vp]),
+        "gadep_nearest_hit": (st, [vp, vp, vp, C.c_int64, vp, vp, vp, vp]),
         "gadep_opts_default": (None, [P(gadep_opts)]),
         "gadep_run": (st, [vp, P(gadep_materials), P(gadep_source), C.c_float, C.c_uint64, C.c_uint32,
                            P(gadep_opts), vp, vp, C.c_uint64, P(gadep_result), vp]),

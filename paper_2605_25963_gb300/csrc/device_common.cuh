@@ -87,13 +87,15 @@ __device__ __forceinline__ Shear make_shear(float dx, float dy, float dz)
     return s;
 }
 
-// Watertight test of triangle i against the ray (o, shear); on a hit with
-// t_min < t < t_best updates t_best / best / entering (entering: d . n < 0).
-__device__ __forceinline__ void tri_test(const float4 *__restrict__ tris, int i, float ox, float oy,
-                                         float oz, const Shear &sh, float t_min, float &t_best,
+// Watertight test of triangle slot i against the ray (o, shear), skipped when its
+// mesh id (v1.w) is `exclude`; on a hit with t_min < t < t_best updates
+// t_best / best / entering (entering: d . n < 0).
+__device__ __forceinline__ void tri_test(const float4 *__restrict__ tris, int i, int exclude, float ox,
+                                         float oy, float oz, const Shear &sh, float t_min, float &t_best,
                                          int &best, bool &entering)
 {
     const float4 a = __ldg(tris + 3 * i), b = __ldg(tris + 3 * i + 1), c = __ldg(tris + 3 * i + 2);
+    if (__float_as_int(b.w) == exclude) return;
     const float Ax0 = a.x - ox, Ay0 = a.y - oy, Az0 = a.z - oz;
     const float Bx0 = b.x - ox, By0 = b.y - oy, Bz0 = b.z - oz;
     const float Cx0 = c.x - ox, Cy0 = c.y - oy, Cz0 = c.z - oz;
@@ -127,16 +129,37 @@ __device__ __forceinline__ void tri_test(const float4 *__restrict__ tris, int i,
 
 struct TravStats { uint32_t nodes, tris; };
 
-// Nearest triangle along o + t d with t_min < t (exclusive), skipping `exclude`
-// (BVH-order index).  Returns the BVH-order index or -1; t_hit / entering set on
-// a hit.  Sets ERR_STACK in err if the stack would overflow (query abandoned).
+// Child word of a node: >= 0 inner node index; < 0 leaf ~(first << 3 | count).
+constexpr int kSentinel = 0x7fffffff;
+
+__device__ __forceinline__ void leaf_test(const float4 *__restrict__ tris, int ref, int exclude, float ox,
+                                          float oy, float oz, const Shear &sh, float t_min, float &t_best,
+                                          int &best, bool &ent, uint32_t &ntested)
+{
+    const int code = ~ref;
+    const int first = code >> 3, count = code & 7;
+    for (int i = first; i < first + count; ++i) {
+        ++ntested;
+        tri_test(tris, i, exclude, ox, oy, oz, sh, t_min, t_best, best, ent);
+    }
+}
+
+// Nearest triangle along o + t d with t_min < t (exclusive) in the tree rooted at
+// `root` (-1: empty), skipping mesh triangle `exclude`.  Returns the triangle slot
+// or -1; t_hit / entering set on a hit.  Sets ERR_STACK in err if the stack would
+// overflow (query abandoned).
+// Loop structure after Aila & Laine (HPG 2009): an inner-node loop that runs
+// until every lane of the warp holds a leaf (postponing at most one leaf per
+// lane), then a leaf loop, so lanes execute node steps and triangle tests in
+// lockstep instead of branching between them at every node.
 template <bool COUNT>
 __device__ __forceinline__ int traverse(const float4 *__restrict__ nodes,
-                                        const float4 *__restrict__ tris, float ox, float oy,
+                                        const float4 *__restrict__ tris, int root, float ox, float oy,
                                         float oz, float dx, float dy, float dz, float t_min,
                                         int exclude, float &t_hit, bool &entering, uint32_t &err,
                                         TravStats &st)
 {
+    if (root < 0) return -1;
     const Shear sh = make_shear(dx, dy, dz);
     const float ix = 1.0f / (fabsf(dx) > 1e-30f ? dx : copysignf(1e-30f, dx));
     const float iy = 1.0f / (fabsf(dy) > 1e-30f ? dy : copysignf(1e-30f, dy));
@@ -146,55 +169,52 @@ __device__ __forceinline__ int traverse(const float4 *__restrict__ nodes,
     int best = -1;
     bool ent = false;
     int stack[kStack];
+    stack[0] = kSentinel;
     int sp = 0;
-    int node = 0;
-    while (true) {
-        const float4 n0 = __ldg(nodes + 4 * node + 0);
-        const float4 n1 = __ldg(nodes + 4 * node + 1);
-        const float4 n2 = __ldg(nodes + 4 * node + 2);
-        const int4 n3 = __ldg(reinterpret_cast<const int4 *>(nodes) + 4 * node + 3);
-        if (COUNT) st.nodes++;
-        const float a0 = fmaf(n0.x, ix, -oix), a1 = fmaf(n0.y, ix, -oix);
-        const float a2 = fmaf(n0.z, iy, -oiy), a3 = fmaf(n0.w, iy, -oiy);
-        const float a4 = fmaf(n2.x, iz, -oiz), a5 = fmaf(n2.y, iz, -oiz);
-        const float b0 = fmaf(n1.x, ix, -oix), b1 = fmaf(n1.y, ix, -oix);
-        const float b2 = fmaf(n1.z, iy, -oiy), b3 = fmaf(n1.w, iy, -oiy);
-        const float b4 = fmaf(n2.z, iz, -oiz), b5 = fmaf(n2.w, iz, -oiz);
-        const float tmin0 = fmaxf(fmaxf(fminf(a0, a1), fminf(a2, a3)), fmaxf(fminf(a4, a5), t_min));
-        const float tmax0 = fminf(fminf(fmaxf(a0, a1), fmaxf(a2, a3)), fminf(fmaxf(a4, a5), t_best));
-        const float tmin1 = fmaxf(fmaxf(fminf(b0, b1), fminf(b2, b3)), fmaxf(fminf(b4, b5), t_min));
-        const float tmax1 = fminf(fminf(fmaxf(b0, b1), fmaxf(b2, b3)), fminf(fmaxf(b4, b5), t_best));
-        bool h0 = tmin0 <= tmax0, h1 = tmin1 <= tmax1;
-        if (h0 && n3.x < 0) {
-            const int first = ~n3.x;
-            for (int i = first; i < first + n3.z; ++i) {
-                if (COUNT) st.tris++;
-                if (i != exclude) tri_test(tris, i, ox, oy, oz, sh, t_min, t_best, best, ent);
+    int node = root;
+    int leaf = 0;
+    uint32_t nn = 0, nt = 0;
+    while (node != kSentinel) {
+        while ((unsigned)node < (unsigned)kSentinel) {
+            const float4 n0 = __ldg(nodes + 4 * node + 0);
+            const float4 n1 = __ldg(nodes + 4 * node + 1);
+            const float4 n2 = __ldg(nodes + 4 * node + 2);
+            const int4 n3 = __ldg(reinterpret_cast<const int4 *>(nodes) + 4 * node + 3);
+            ++nn;
+            const float a0 = fmaf(n0.x, ix, -oix), a1 = fmaf(n0.y, ix, -oix);
+            const float a2 = fmaf(n0.z, iy, -oiy), a3 = fmaf(n0.w, iy, -oiy);
+            const float a4 = fmaf(n2.x, iz, -oiz), a5 = fmaf(n2.y, iz, -oiz);
+            const float b0 = fmaf(n1.x, ix, -oix), b1 = fmaf(n1.y, ix, -oix);
+            const float b2 = fmaf(n1.z, iy, -oiy), b3 = fmaf(n1.w, iy, -oiy);
+            const float b4 = fmaf(n2.z, iz, -oiz), b5 = fmaf(n2.w, iz, -oiz);
+            const float tmin0 = fmaxf(fmaxf(fminf(a0, a1), fminf(a2, a3)), fmaxf(fminf(a4, a5), t_min));
+            const float tmax0 = fminf(fminf(fmaxf(a0, a1), fmaxf(a2, a3)), fminf(fmaxf(a4, a5), t_best));
+            const float tmin1 = fmaxf(fmaxf(fminf(b0, b1), fminf(b2, b3)), fmaxf(fminf(b4, b5), t_min));
+            const float tmax1 = fminf(fminf(fmaxf(b0, b1), fmaxf(b2, b3)), fminf(fmaxf(b4, b5), t_best));
+            const bool h0 = tmin0 <= tmax0, h1 = tmin1 <= tmax1;
+            if (!h0 && !h1) {
+                node = stack[sp--];
+            } else {
+                const bool first0 = h0 && (!h1 || tmin0 <= tmin1);
+                node = first0 ? n3.x : n3.y;
+                if (h0 && h1) {
+                    if (sp + 1 >= kStack) { err |= ERR_STACK; return -1; }
+                    stack[++sp] = first0 ? n3.y : n3.x;
+                }
             }
-            h0 = false;
-        }
-        if (h1 && n3.y < 0) {
-            const int first = ~n3.y;
-            for (int i = first; i < first + n3.w; ++i) {
-                if (COUNT) st.tris++;
-                if (i != exclude) tri_test(tris, i, ox, oy, oz, sh, t_min, t_best, best, ent);
+            if (node < 0 && leaf >= 0) {     // postpone this leaf, keep descending
+                leaf = node;
+                node = stack[sp--];
             }
-            h1 = false;
+            if (!__any_sync(__activemask(), leaf >= 0)) break;
         }
-        if (h0 && h1) {
-            const bool first0 = tmin0 <= tmin1;
-            if (sp >= kStack) { err |= ERR_STACK; return -1; }
-            stack[sp++] = first0 ? n3.y : n3.x;
-            node = first0 ? n3.x : n3.y;
-        } else if (h0) {
-            node = n3.x;
-        } else if (h1) {
-            node = n3.y;
-        } else {
-            if (sp == 0) break;
-            node = stack[--sp];
+        while (leaf < 0) {
+            leaf_test(tris, leaf, exclude, ox, oy, oz, sh, t_min, t_best, best, ent, nt);
+            leaf = node;
+            if (node < 0) node = stack[sp--];
         }
     }
+    if (COUNT) { st.nodes += nn; st.tris += nt; }
     if (best >= 0) { t_hit = t_best; entering = ent; }
     return best;
 }

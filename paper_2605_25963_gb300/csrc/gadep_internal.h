@@ -43,23 +43,28 @@ struct detmesh_mesh {
 //   f4[0] = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
 //   f4[1] = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
 //   f4[2] = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
-//   i4[3] = (child0, child1, count0, count1)
-// child >= 0: inner node index; child < 0: leaf with first triangle ~child and
-// `count` triangles (count 0 = empty slot, its box is inverted).
-// Triangle = 3 x float4: (v0, region id bits), (v1, 0), (v2, 0) with region id =
-// solid + 1 (0 = world).
+//   i4[3] = (child0, child1, 0, 0)
+// child >= 0: inner node index; child < 0: leaf ~(first << 3 | count) holding
+// triangles [first, first + count) (count 0 = empty slot, its box is inverted).
+// Triangle = 3 x float4: (v0, region id bits), (v1, mesh triangle id bits), (v2, 0)
+// with region id = solid + 1 (0 = world).
+// Trees: one per region (the triangles of the region's own solid and of its child
+// solids) plus one over every triangle; all share the node and triangle arrays.
 struct gadep_bvh {
     int device = 0;
     gadep::MeshData geo;                 // for host-side localisation of sources
     std::vector<float> nodes;            // 16 floats per node
-    std::vector<float> tris;             // 12 floats per triangle (BVH order)
-    std::vector<int32_t> tri_orig;       // BVH order -> mesh triangle index
-    std::vector<int32_t> regions;        // 4 ints per region: material, active, group, parent region
+    std::vector<float> tris;             // 12 floats per triangle slot (leaf order, per tree)
+    std::vector<int32_t> tri_orig;       // triangle slot -> mesh triangle index
+    std::vector<int32_t> regions;        // 4 ints per region: material, active | (group + 1) << 1,
+                                         // parent region, root node of the region's tree (-1 = none)
+    int32_t root_all = -1;               // tree over every triangle
     gadep_bvh_stats stats{};
     void *d_nodes = nullptr, *d_tris = nullptr, *d_tri_orig = nullptr, *d_regions = nullptr;
 };
 
 namespace gadep {
+std::vector<std::vector<int32_t>> region_triangle_sets(const MeshData &g);
 gadep_status upload_bvh(gadep_bvh *b);
 void free_bvh_device(gadep_bvh *b);
 }  // namespace gadep

@@ -83,7 +83,24 @@ struct Params {
     uint32_t key0, key1;
     float e_cut, fep_delta, e_max, bin_scale;
     int n_bins, step_cap, n_group, chunk;
+    float root_lo[3], root_hi[3];       // bounds of every triangle (padded)
 };
+
+// Slab test of the ray (t >= 0) against an axis-aligned box.
+__device__ __forceinline__ bool ray_hits_box(const float lo[3], const float hi[3], float ox, float oy, float oz,
+                                             float dx, float dy, float dz)
+{
+    float t0 = 0.0f, t1 = INFINITY;
+    const float o[3] = { ox, oy, oz }, d[3] = { dx, dy, dz };
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float inv = 1.0f / (fabsf(d[k]) > 1e-30f ? d[k] : copysignf(1e-30f, d[k]));
+        float a = (lo[k] - o[k]) * inv, b = (hi[k] - o[k]) * inv;
+        t0 = fmaxf(t0, fminf(a, b));
+        t1 = fminf(t1, fmaxf(a, b));
+    }
+    return t0 <= t1;
+}
 
 // Per-lane partial tallies of one instance, flushed on instance change and at exit.
 template <bool GRAD>
@@ -212,7 +229,9 @@ __device__ __forceinline__ void mu_at(const float4 *tab, int n_grid, float lnE_m
 }
 
 template <bool GRAD, bool COUNT>
-__global__ void __launch_bounds__(256, 2) transport_kernel(const Params P, unsigned long long *counters)
+// 4 blocks of 256 threads per SM (64 registers): measured faster than 2 or 3
+// blocks despite the register spills, as the traversal is latency bound.
+__global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsigned long long *counters)
 {
     extern __shared__ float4 smem[];
     float4 *s_xs = smem;
@@ -299,8 +318,17 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params P, unsig
                 herr = 0u;
 #pragma unroll
                 for (int g = 0; g < (GRAD ? 4 : 1); ++g) score[g] = 0.0f;
-                lam = -logf(rng.u01(k0, k1));
-                busy = true;
+                if (region == 0 && !ray_hits_box(P.root_lo, P.root_hi, ox, oy, oz, dx, dy, dz)) {
+                    // Born in the world and aimed away from every solid: the one
+                    // segment of this history escapes with nothing deposited.  It
+                    // ends here so the lane can take the next history at once.
+                    acc.hist++; acc.zero++; acc.seg++;
+                    acc.esc += E0;
+                    if (g_hist < P.n_trace) P.edep_trace[g_hist] = 0.0f;
+                } else {
+                    lam = -logf(rng.u01(k0, k1));
+                    busy = true;
+                }
             }
             pool_next += take;
             need = __ballot_sync(FULL, !busy);
@@ -316,13 +344,15 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params P, unsig
             } else {
                 float t_hit = INFINITY;
                 bool entering = false;
-                const int hit = traverse<COUNT>(P.nodes, P.tris, ox, oy, oz, dx, dy, dz, t_cur, last_tri,
-                                                t_hit, entering, herr, ts);
+                // region record: material slot, active | (group + 1) << 1, parent, tree root
                 const int4 R = s_reg[region];
+                const int group = (R.y >> 1) - 1;
+                const int hit = traverse<COUNT>(P.nodes, P.tris, R.w, ox, oy, oz, dx, dy, dz, t_cur, last_tri,
+                                                t_hit, entering, herr, ts);
                 float pe = 0.0f, co = 0.0f, pa = 0.0f;
                 if (R.x >= 0) mu_at(s_xs + (size_t)R.x * P.n_grid, P.n_grid, P.lnE_min, P.inv_dlnE, E, pe, co, pa);
                 const float mu_unit = pe + co + pa;
-                const float sc = R.z >= 0 ? P.inst[inst].scale[R.z] : 1.0f;
+                const float sc = group >= 0 ? P.inst[inst].scale[group] : 1.0f;
                 const float mu = mu_unit * sc;
                 const float d_int = mu > 0.0f ? lam / mu : INFINITY;
                 acc.seg++;
@@ -331,7 +361,7 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params P, unsig
                 } else if (d_int < t_hit - t_cur) {
                     // ---- interaction ----
                     acc.inter++;
-                    if (GRAD && R.z >= 0 && R.z < 4) score[R.z] += 1.0f / sc - mu_unit * d_int;
+                    if (GRAD && group >= 0 && group < 4) score[group] += 1.0f / sc - mu_unit * d_int;
                     const float tt = t_cur + d_int;
                     const float px = fmaf(tt, dx, ox), py = fmaf(tt, dy, oy), pz = fmaf(tt, dz, oz);
                     const float u = rng.u01(k0, k1) * mu_unit;
@@ -381,7 +411,7 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params P, unsig
                         sdx = -nx; sdy = -ny; sdz = -nz;
                         sreg = region;
                     }
-                    if (R.y) edep += dep;
+                    if (R.y & 1) edep += dep;
                     dep_all += dep;
                     if (herr) {
                         finished = true;
@@ -416,11 +446,11 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params P, unsig
                     // ---- boundary crossing ----
                     const float len = t_hit - t_cur;
                     lam -= mu * len;
-                    if (GRAD && R.z >= 0 && R.z < 4) score[R.z] -= mu_unit * len;
+                    if (GRAD && group >= 0 && group < 4) score[group] -= mu_unit * len;
                     t_cur = t_hit;
-                    last_tri = hit;
+                    last_tri = __float_as_int(__ldg(&P.tris[3 * hit + 1].w));   // mesh triangle id
                     const int treg = __float_as_int(__ldg(&P.tris[3 * hit].w));
-                    region = entering ? treg : s_reg[treg].w;
+                    region = entering ? treg : s_reg[treg].z;
                 }
             }
             if (!finished && !(isfinite(dx) && isfinite(E) && isfinite(lam))) {
@@ -470,22 +500,30 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params P, unsig
     }
 }
 
-__global__ void nearest_hit_kernel(const float4 *nodes, const float4 *tris, const int32_t *tri_orig,
-                                   const int32_t *orig_to_bvh, int32_t n_tri, const float *rays, long long n,
-                                   float *t_out, int32_t *tri_out, int32_t *ent_out)
+// One query per thread.  region[i] (0 = world, s + 1 = solid s) selects that
+// region's tree; without regions, or for an out-of-range id, the tree over every
+// triangle is used.
+__global__ void nearest_hit_kernel(const float4 *nodes, const float4 *tris, const int32_t *region_roots,
+                                   int32_t n_region, int32_t root_all, const int32_t *regions,
+                                   const float *rays, long long n, float *t_out, int32_t *tri_out,
+                                   int32_t *ent_out)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float *r = rays + 8 * i;
-    const int ex_mesh = __float_as_int(r[7]);
-    const int ex = (ex_mesh >= 0 && ex_mesh < n_tri) ? orig_to_bvh[ex_mesh] : -1;
+    const int ex = __float_as_int(r[7]);
+    int root = root_all;
+    if (regions) {
+        const int g = regions[i];
+        if (g >= 0 && g < n_region) root = region_roots[g];
+    }
     float t = INFINITY;
     bool ent = false;
     uint32_t err = 0;
     TravStats st{ 0, 0 };
-    const int hit = traverse<false>(nodes, tris, r[0], r[1], r[2], r[4], r[5], r[6], r[3], ex, t, ent, err, st);
+    const int hit = traverse<false>(nodes, tris, root, r[0], r[1], r[2], r[4], r[5], r[6], r[3], ex, t, ent, err, st);
     t_out[i] = hit >= 0 ? t : INFINITY;
-    tri_out[i] = hit >= 0 ? tri_orig[hit] : -1;
+    tri_out[i] = hit >= 0 ? __float_as_int(__ldg(&tris[3 * hit + 1].w)) : -1;
     ent_out[i] = hit >= 0 ? (ent ? 1 : 0) : (err ? -2 : -1);
 }
 
@@ -558,26 +596,26 @@ gadep_status upload_bvh(gadep_bvh *b)
     gadep_status st;
     if ((st = dalloc((float **)&b->d_nodes, b->nodes.size(), "bvh nodes")) != GADEP_OK) return st;
     if ((st = dalloc((float **)&b->d_tris, b->tris.size(), "bvh triangles")) != GADEP_OK) return st;
-    const size_t nt = b->tri_orig.size();
-    if ((st = dalloc((int32_t **)&b->d_tri_orig, 2 * nt, "bvh triangle map")) != GADEP_OK) return st;
-    std::vector<int32_t> maps(2 * nt);
-    for (size_t i = 0; i < nt; ++i) { maps[i] = b->tri_orig[i]; maps[nt + b->tri_orig[i]] = (int32_t)i; }
+    const size_t nr = b->regions.size() / 4;
+    std::vector<int32_t> roots(nr);
+    for (size_t r = 0; r < nr; ++r) roots[r] = b->regions[4 * r + 3];
+    if ((st = dalloc((int32_t **)&b->d_regions, nr, "bvh region roots")) != GADEP_OK) return st;
     cudaError_t e;
     if ((e = cudaMemcpy(b->d_nodes, b->nodes.data(), b->nodes.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(b->d_tris, b->tris.data(), b->tris.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(b->d_tri_orig, maps.data(), maps.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+        (e = cudaMemcpy(b->d_regions, roots.data(), nr * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "gadep_bvh_build: upload");
     return GADEP_OK;
 }
 
 void free_bvh_device(gadep_bvh *b)
 {
-    if (!b->d_nodes && !b->d_tris && !b->d_tri_orig) return;
+    if (!b->d_nodes && !b->d_tris && !b->d_regions) return;
     DeviceGuard g(b->device);
     cudaFree(b->d_nodes);
     cudaFree(b->d_tris);
-    cudaFree(b->d_tri_orig);
-    b->d_nodes = b->d_tris = b->d_tri_orig = nullptr;
+    cudaFree(b->d_regions);
+    b->d_nodes = b->d_tris = b->d_regions = nullptr;
 }
 
 }  // namespace gadep
@@ -684,24 +722,23 @@ extern "C" void gadep_bvh_destroy(gadep_bvh *b)
     delete b;
 }
 
-extern "C" gadep_status gadep_nearest_hit(const gadep_bvh *b, const float *rays, int64_t n, float *t_out,
-                                          int32_t *tri_out, int32_t *entering_out, void *stream)
+extern "C" gadep_status gadep_nearest_hit(const gadep_bvh *b, const float *rays, const int32_t *regions, int64_t n,
+                                          float *t_out, int32_t *tri_out, int32_t *entering_out, void *stream)
 {
     gadep::clear_error();
     if (!b || n < 0 || (n > 0 && (!rays || !t_out || !tri_out || !entering_out)))
         return fail(GADEP_E_INVAL, "gadep_nearest_hit: bad arguments");
     if (b->device < 0 || !b->d_nodes) return fail(GADEP_E_INVAL, "gadep_nearest_hit: the BVH has no device copy");
     if (n == 0) return GADEP_OK;
-    if (!is_device_ptr(rays) || !is_device_ptr(t_out) || !is_device_ptr(tri_out) || !is_device_ptr(entering_out))
-        return fail(GADEP_E_INVAL, "gadep_nearest_hit: rays and outputs must be device memory");
+    if (!is_device_ptr(rays) || !is_device_ptr(t_out) || !is_device_ptr(tri_out) || !is_device_ptr(entering_out) ||
+        (regions && !is_device_ptr(regions)))
+        return fail(GADEP_E_INVAL, "gadep_nearest_hit: rays, regions and outputs must be device memory");
     DeviceGuard g(b->device);
     const int threads = 128;
     const long long blocks = (n + threads - 1) / threads;
-    const int32_t *maps = (const int32_t *)b->d_tri_orig;
     gadep::dev::nearest_hit_kernel<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(
-        (const float4 *)b->d_nodes, (const float4 *)b->d_tris, maps, maps + b->tri_orig.size(),
-        (int32_t)b->tri_orig.size(), rays, n,
-        t_out, tri_out, entering_out);
+        (const float4 *)b->d_nodes, (const float4 *)b->d_tris, (const int32_t *)b->d_regions,
+        (int32_t)(b->regions.size() / 4), b->root_all, regions, rays, n, t_out, tri_out, entering_out);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GADEP_OK : gadep::cuda_fail(e, "gadep_nearest_hit");
 }
@@ -906,6 +943,23 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
     P.step_cap = opts->step_cap;
     P.n_group = opts->n_group;
     P.chunk = opts->chunk > 0 ? opts->chunk : 256;
+    // scene bounds seen from the world = union of the world tree's root child boxes
+    for (int k = 0; k < 3; ++k) { P.root_lo[k] = 0.0f; P.root_hi[k] = -1.0f; }
+    if (b->regions[3] >= 0) {
+        const float *f = b->nodes.data() + (size_t)b->regions[3] * 16;
+        int32_t w[4];
+        std::memcpy(w, &f[12], 16);
+        for (int k = 0; k < 3; ++k) { P.root_lo[k] = INFINITY; P.root_hi[k] = -INFINITY; }
+        for (int c = 0; c < 2; ++c) {
+            if (w[c] < 0 && ((~w[c]) & 7) == 0) continue;  // empty leaf slot
+            const float lo[3] = { f[4 * c + 0], f[4 * c + 2], f[8 + 2 * c] };
+            const float hi[3] = { f[4 * c + 1], f[4 * c + 3], f[9 + 2 * c] };
+            for (int k = 0; k < 3; ++k) {
+                P.root_lo[k] = std::min(P.root_lo[k], lo[k]);
+                P.root_hi[k] = std::max(P.root_hi[k], hi[k]);
+            }
+        }
+    }
     *out = p;
     return GADEP_OK;
 }

@@ -96,10 +96,12 @@ def test_bvh_host_invariants(name):
     assert st["n_tri"] == len(m.arrays()[1])
     assert st["max_leaf_tris"] <= 4
     assert st["max_depth"] < 60
-    assert st["node_bytes"] == 64 * st["n_nodes"] and st["tri_bytes"] == 48 * st["n_tri"]
-    # a binary tree over leaves with <= 4 triangles
-    assert st["n_leaves"] == st["n_nodes"] + 1
-    assert st["n_leaves"] >= st["n_tri"] / 4
+    # one tree over every triangle + one per region over its own and its children's
+    # triangles: each triangle is stored three times (global, own region, parent region)
+    assert st["node_bytes"] == 64 * st["n_nodes"] and st["tri_bytes"] == 3 * 48 * st["n_tri"]
+    n_trees = 1 + st["n_region"]
+    assert st["n_nodes"] + 1 <= st["n_leaves"] <= st["n_nodes"] + n_trees
+    assert st["n_leaves"] >= 3 * st["n_tri"] / 4
 
 
 def test_invalid_parameters_rejected():

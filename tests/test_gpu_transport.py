@@ -110,8 +110,20 @@ def test_volume_source_parity(orc, otab, mats):
 
 
 def test_nearest_hit_matches_bruteforce(orc):
+    """GPU traversal vs FP64 brute force over the same triangles (the oracle's own
+    vertices rounded to binary32, the precision the GPU stores).  Distances agree
+    to 1e-5 relative wherever the hit is well conditioned; at grazing incidence the
+    binary32 translation of vertices to the ray origin bounds the error by
+    ~eps32 (|o| + |v|) / |cos|, which the tolerance adds."""
+    eps32 = 2.0 ** -24
     for name in ("COAX_P", "BARE_CYLINDER"):
-        m, b, om = scene(orc, name)
+        m, b, om64 = scene(orc, name)
+        gpu_solid = m.arrays()[2]          # triangle -> solid of the library's mesh
+        X, T, S, sol = om64.arrays()
+        X32 = X.astype(np.float32).astype(np.float64)
+        om = orc.Mesh.from_arrays(X32, T, S, sol["material"], sol["active"], sol["group"], sol["parent"])
+        nrm = np.cross(X32[T[:, 1]] - X32[T[:, 0]], X32[T[:, 2]] - X32[T[:, 0]])
+        nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
         rng = np.random.default_rng(11)
         n = 3000
         o = np.column_stack([rng.uniform(-40, 40, n), rng.uniform(-40, 40, n), rng.uniform(-125, 30, n)])
@@ -121,34 +133,51 @@ def test_nearest_hit_matches_bruteforce(orc):
         rays[:, 0:3] = o
         rays[:, 4:7] = d
         rays[:, 7] = np.array([-1] * n, np.int32).view(np.float32)
-        t, tri, ent = api.gadep_nearest_hit(b, torch.from_numpy(rays).cuda())
-        t, tri, ent = t.cpu().numpy(), tri.cpu().numpy(), ent.cpu().numpy()
-        o32 = rays[:, 0:3].astype(np.float64)
-        d32 = rays[:, 4:7].astype(np.float64)
-        agree = 0
-        for i in range(n):
-            k, tt, ee = om.nearest_hit(o32[i], d32[i])
-            if k < 0:
-                assert tri[i] == -1 and np.isinf(t[i])
-                agree += 1
-                continue
-            assert abs(t[i] - tt) <= 1e-5 * max(tt, 1.0) + 2e-5, (i, t[i], tt)
-            if tri[i] == k:
-                assert ent[i] == ee
-                agree += 1
-        assert agree >= 0.998 * n
-        # continuing past the first hit with the crossed triangle excluded
-        hit = tri >= 0
+
+        def check(rays_np, t_gpu, tri_gpu, ent_gpu, excl):
+            strict = agree = 0
+            first = []
+            for i in range(len(rays_np)):
+                oo = rays_np[i, 0:3].astype(np.float64)
+                dd = rays_np[i, 4:7].astype(np.float64)
+                k, tt, ee = om.nearest_hit(oo, dd, float(rays_np[i, 3]), int(excl[i]))
+                first.append(k)
+                if k < 0:
+                    assert tri_gpu[i] == -1 and np.isinf(t_gpu[i]), i
+                    strict += 1
+                    agree += 1
+                    continue
+                cosv = abs(np.dot(dd, nrm[k]))
+                scale = np.abs(oo).max() + np.abs(X32[T[k]]).max()
+                tol = 1e-5 * max(tt, 1.0) + 8 * eps32 * scale / max(cosv, 1e-3)
+                assert abs(t_gpu[i] - tt) <= tol, (name, i, t_gpu[i], tt, cosv)
+                strict += abs(t_gpu[i] - tt) <= 1e-5 * max(tt, 1.0)
+                # the two meshes triangulate independently: compare the surface hit
+                if tri_gpu[i] >= 0 and gpu_solid[tri_gpu[i]] == S[k] and ent_gpu[i] == ee:
+                    agree += 1
+            return strict / len(rays_np), agree / len(rays_np), np.array(first)
+
+        t, tri, ent = (x.cpu().numpy() for x in api.gadep_nearest_hit(b, torch.from_numpy(rays).cuda()))
+        strict, agree, k_orc = check(rays, t, tri, ent, [-1] * n)
+        assert strict >= 0.99 and agree >= 0.998, (strict, agree)
+        # continuing past the first hit with the crossed triangle excluded (each side
+        # excludes its own triangle; rays whose first surface differed are skipped)
+        hit = (tri >= 0) & (k_orc >= 0)
+        hit &= np.array([gpu_solid[a] == S[c] if a >= 0 and c >= 0 else False for a, c in zip(tri, k_orc)])
         rays2 = rays[hit].copy()
         rays2[:, 3] = t[hit]
         rays2[:, 7] = tri[hit].astype(np.int32).view(np.float32)
-        t2, tri2, _ = api.gadep_nearest_hit(b, torch.from_numpy(rays2).cuda())
-        t2, tri2 = t2.cpu().numpy(), tri2.cpu().numpy()
-        for j in range(min(len(rays2), 1500)):
-            k, tt, _ = om.nearest_hit(rays2[j, 0:3].astype(np.float64), rays2[j, 4:7].astype(np.float64),
-                                      float(rays2[j, 3]), int(tri[hit][j]))
-            if k >= 0 and tri2[j] >= 0:
-                assert abs(t2[j] - tt) <= 1e-5 * max(tt, 1.0) + 2e-5
+        t2, tri2, ent2 = (x.cpu().numpy() for x in api.gadep_nearest_hit(b, torch.from_numpy(rays2).cuda()))
+        strict, agree, _ = check(rays2, t2, tri2, ent2, k_orc[hit])
+        assert strict >= 0.99 and agree >= 0.99, (strict, agree)
+        # queries restricted to the tree of the origin's region (own solid + child
+        # solids) find the same nearest surface as the search over every triangle
+        reg = np.array([om.locate(rays[i, 0:3].astype(np.float64), (0.2672612, 0.5345225, 0.8017837)) + 1
+                        for i in range(n)], dtype=np.int32)
+        t3, tri3, ent3 = (x.cpu().numpy() for x in api.gadep_nearest_hit(
+            b, torch.from_numpy(rays).cuda(), regions=torch.from_numpy(reg).cuda()))
+        strict, agree, _ = check(rays, t3, tri3, ent3, [-1] * n)
+        assert strict >= 0.99 and agree >= 0.998, (strict, agree)
 
 
 def test_philox_device_stream_matches_oracle(orc):
