@@ -254,6 +254,30 @@ gadep_status gadep_run(const gadep_bvh *b, const gadep_materials *mat, const gad
                        const gadep_opts *opts, uint32_t *spectrum, float *edep_trace,
                        uint64_t n_trace, gadep_result *result, void *stream);
 
+/* gadep_run without device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot let a library allocate device memory while
+ * they run -- work issued while a stream is being captured (cudaMalloc is not
+ * permitted then), applications whose own allocator owns all device memory, and
+ * loops that cannot take the device-wide synchronisation that cudaFree implies.
+ * It computes the same histories as gadep_run with the same arguments (n_trace 0)
+ * and returns the same result.
+ * Scratch: instead of allocating, the call keeps the staged tables, region table,
+ * instance record, tallies and work counter in one fixed device array of 345,456
+ * bytes (337 KiB) that every GPU loading the library holds until the process exits.
+ * Limits (GADEP_E_INVAL beyond them): at most 63 solids, and (materials with
+ * non-zero tables used by the mesh) x n_grid <= 12288, n_grid <= 12288.
+ * spectrum_dev: caller's device buffer of opts->n_bins uint32 (zeroed by the call);
+ * result: host.  Synchronises `stream` before returning.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array and leave the last call's contents in
+ * it; the call clears what must start at zero.  Calls that overlap on the GPU
+ * (different streams or host threads at the same time) race on it. */
+gadep_status gadep_run_noalloc(const gadep_bvh *b, const gadep_materials *mat, const gadep_source *src,
+                               float energy_keV, uint64_t n_hist, uint32_t instance,
+                               const gadep_opts *opts, uint32_t *spectrum_dev, gadep_result *result,
+                               void *stream);
+
 /* Batched: n_inst instances, each with its own energy, source, history count,
  * Philox instance id and density scales, in one persistent launch drawing
  * histories from a device work counter.  spectra [n_inst][n_bins] host or device;

@@ -249,6 +249,21 @@ def gadep_run(bvh: Bvh, mat: Materials, src: W.Source, energy, n_hist, instance=
     return result_dict(r), spec
 
 
+def gadep_run_noalloc(bvh: Bvh, mat: Materials, src: W.Source, energy, n_hist, spectrum, instance=0, opts=None,
+                      stream=None):
+    """gadep_run for callers that cannot have the library allocate device memory
+    (stream capture, an application-owned allocator, no cudaFree syncs): scratch
+    lives in a fixed device array inside the library.  spectrum: the caller's
+    CUDA uint32/int32 tensor of n_bins counts.  Calls that overlap on the GPU race
+    on that array; the first call on a device should precede any stream capture."""
+    o = opts if opts is not None else make_opts()
+    s = make_source(src)
+    r = capi.gadep_result()
+    check(capi.load().gadep_run_noalloc(bvh.handle, C.byref(mat.c), C.byref(s), energy, n_hist, instance,
+                                        C.byref(o), spectrum.data_ptr(), C.byref(r), _stream(stream)))
+    return result_dict(r)
+
+
 def gadep_run_batch(bvh: Bvh, mat: Materials, instances, opts=None, spectra=None, stream=None):
     o = opts if opts is not None else make_opts()
     n = len(instances)

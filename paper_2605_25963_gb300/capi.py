@@ -23,7 +23,7 @@ EXPORTS = (
     "gadep_bvh_get_stats", "gadep_bvh_validate", "gadep_bvh_destroy", "gadep_nearest_hit",
     "gadep_opts_default", "gadep_run", "gadep_run_batch", "gadep_grad", "gadep_plan_create",
     "gadep_plan_launch", "gadep_plan_results", "gadep_plan_shape", "gadep_plan_destroy",
-    "gadep_count_work", "gadep_philox_words",
+    "gadep_count_work", "gadep_philox_words", "gadep_run_noalloc",
 )
 
 
@@ -138,6 +138,8 @@ def load(build_if_missing: bool = True):
         "gadep_count_work": (st, [vp, P(gadep_materials), C.c_int32, P(gadep_instance), P(gadep_opts),
                                   P(gadep_result), P(C.c_uint64), P(C.c_uint64), vp]),
         "gadep_philox_words": (st, [C.c_uint64, C.c_uint64, C.c_uint32, C.c_int32, vp, vp]),
+        "gadep_run_noalloc": (st, [vp, P(gadep_materials), P(gadep_source), C.c_float, C.c_uint64, C.c_uint32,
+                                   P(gadep_opts), vp, P(gadep_result), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -27,6 +27,10 @@ struct MeshData {
 // crossings along a generic ray from p; -1 = world.  Returns -2 when every
 // trial ray grazed an edge (cannot happen for points off the surfaces).
 int32_t locate_point(const MeshData &m, const double p[3]);
+// Same rule without heap memory, for meshes of at most kLocateMaxSolids solids
+// (-3 when there are more).
+constexpr int kLocateMaxSolids = 63;
+int32_t locate_point_fixed(const MeshData &m, const double p[3]);
 double solid_volume(const MeshData &m, int32_t s);
 int32_t solid_euler(const MeshData &m, int32_t s);
 // Validate closedness/orientation and derive the nesting tree (solids[].parent).

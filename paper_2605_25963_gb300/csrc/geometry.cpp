@@ -189,6 +189,40 @@ int32_t locate_point(const MeshData &m, const double p[3])
     return locate_with(m, tris_by_solid(m), solid_boxes(m), p);
 }
 
+int32_t locate_point_fixed(const MeshData &m, const double p[3])
+{
+    // The same parity rule with per-solid counters in fixed arrays: one pass over
+    // every triangle per trial direction, no heap memory.
+    constexpr int kMax = kLocateMaxSolids;
+    if (m.n_solid() > kMax) return -3;
+    for (const auto &dd : kDirs) {
+        const double n = std::sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+        const double d[3] = { dd[0] / n, dd[1] / n, dd[2] / n };
+        int count[kMax] = { 0 };
+        double first[kMax];
+        for (int s = 0; s < kMax; ++s) first[s] = INFINITY;
+        bool ok = true;
+        for (int32_t t = 0; t < m.n_tri() && ok; ++t) {
+            double th;
+            const int r = mt_hit(p, d, &m.xyz[3 * m.tri[3 * t]], &m.xyz[3 * m.tri[3 * t + 1]],
+                                 &m.xyz[3 * m.tri[3 * t + 2]], &th);
+            if (r < 0) ok = false;
+            else if (r == 1) {
+                const int32_t s = m.tri_solid[t];
+                count[s]++;
+                first[s] = std::min(first[s], th);
+            }
+        }
+        if (!ok) continue;
+        int32_t best = -1;
+        double best_t = INFINITY;
+        for (int32_t s = 0; s < m.n_solid(); ++s)
+            if ((count[s] & 1) && first[s] < best_t) { best_t = first[s]; best = s; }
+        return best;
+    }
+    return -2;
+}
+
 gadep_status validate_and_nest(MeshData &m)
 {
     const int32_t ns = m.n_solid();

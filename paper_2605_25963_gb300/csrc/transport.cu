@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -1147,4 +1148,263 @@ extern "C" gadep_status gadep_count_work(const gadep_bvh *b, const gadep_materia
     *nodes_visited = c[0];
     *tris_tested = c[1];
     return st;
+}
+
+// ---------------------------------------------------------------------------
+// Single-instance run without any device allocation (gadep_run_noalloc).
+//
+// For callers that must not allocate device memory during a run: code that
+// issues work while a stream is being captured (cudaMalloc is not allowed
+// then), applications that hand all device memory to their own allocator and
+// forbid libraries from taking more, and loops that cannot afford the device
+// synchronisation cudaFree implies.  Everything gadep_run keeps in allocated
+// scratch -- the staged attenuation tables, the region table, the instance
+// record, the tallies and the work counter -- lives here in one file-scope
+// device array of fixed size, owned by every GPU that loads the library until
+// the process exits.
+// ---------------------------------------------------------------------------
+
+namespace gadep {
+namespace noalloc {
+
+constexpr int kMaxTable = 12288;                    // float4 table entries: used materials x grid points
+constexpr int kMaxRegions = kLocateMaxSolids + 1;   // world + solids
+
+struct __align__(16) Layout {
+    float4 xs[kMaxTable];                // interleaved (pe, compton, pair, 0) tables
+    float raw[3 * kMaxTable];            // planar tables as copied from the caller
+    int4 regions[kMaxRegions];
+    dev::InstDev inst;
+    unsigned long long inst_end[2];
+    dev::TallyDev tally;
+    unsigned long long work;
+    unsigned long long counters[4];
+};
+
+}  // namespace noalloc
+}  // namespace gadep
+
+// 345,456 bytes (337 KiB) on every device that loads the library.
+static_assert(sizeof(gadep::noalloc::Layout) == 345456, "scratch size stated in gadep.h");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(gadep::noalloc::Layout)];
+
+namespace gadep {
+namespace noalloc {
+
+__global__ void interleave_tables(const float *raw, int n_mat, int n_grid, float4 *xs)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_mat * n_grid) return;
+    const int m = i / n_grid, g = i - m * n_grid;
+    const float *r = raw + (size_t)m * 3 * n_grid;
+    xs[i] = make_float4(r[g], r[n_grid + g], r[2 * n_grid + g], 0.0f);
+}
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+Layout *g_ptr[kMaxDevices] = { nullptr };
+
+// Device address of the scratch array on `device` (current), looked up once.
+gadep_status scratch_of(int device, Layout **out)
+{
+    if (device < 0 || device >= kMaxDevices) return fail(GADEP_E_INVAL, "gadep_run_noalloc: device index %d", device);
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return fail(GADEP_E_CUDA, "gadep_run_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        }
+        g_ptr[device] = (Layout *)p;
+    }
+    *out = g_ptr[device];
+    return GADEP_OK;
+}
+
+}  // namespace noalloc
+}  // namespace gadep
+
+extern "C" gadep_status gadep_run_noalloc(const gadep_bvh *b, const gadep_materials *mat, const gadep_source *src,
+                                          float energy_keV, uint64_t n_hist, uint32_t instance,
+                                          const gadep_opts *opts, uint32_t *spectrum_dev, gadep_result *result,
+                                          void *stream)
+{
+    using namespace gadep;
+    using noalloc::Layout;
+    clear_error();
+    if (!b || !mat || !src || !result || !spectrum_dev)
+        return fail(GADEP_E_INVAL, "gadep_run_noalloc: NULL argument");
+    if (b->device < 0 || !b->d_nodes) return fail(GADEP_E_INVAL, "gadep_run_noalloc: the BVH has no device copy");
+    gadep_status st = check_opts(opts);
+    if (st != GADEP_OK) return st;
+    if (n_hist >= (1ull << 32)) return fail(GADEP_E_INVAL, "gadep_run_noalloc: n_hist must be < 2^32");
+    if (!(energy_keV > 0.0f) || !std::isfinite(energy_keV) || energy_keV > 1e5f)
+        return fail(GADEP_E_INVAL, "gadep_run_noalloc: energy must be in (0, 1e5] keV");
+    if (!mat->mu || mat->n_mat < 1 || mat->n_mat > 1024 || mat->n_grid < 2 || mat->n_grid > noalloc::kMaxTable ||
+        !(mat->E_min > 0.0) || !(mat->E_max > mat->E_min))
+        return fail(GADEP_E_INVAL, "gadep_run_noalloc: bad gadep_materials");
+    const int n_region = (int)(b->regions.size() / 4);
+    if (n_region > noalloc::kMaxRegions)
+        return fail(GADEP_E_INVAL, "gadep_run_noalloc: at most %d solids (mesh has %d)", noalloc::kMaxRegions - 1,
+                    n_region - 1);
+    if (!is_device_ptr(spectrum_dev)) return fail(GADEP_E_INVAL, "gadep_run_noalloc: spectrum must be device memory");
+    DeviceGuard g(b->device);
+    if (!g.ok) return fail(GADEP_E_CUDA, "gadep_run_noalloc: cannot select device %d", b->device);
+    Layout *S = nullptr;
+    if ((st = noalloc::scratch_of(b->device, &S)) != GADEP_OK) return st;
+    const cudaStream_t s = (cudaStream_t)stream;
+    const size_t ng = (size_t)mat->n_grid;
+
+    // regions and the materials they use (all-zero tables act as vacuum; the world is vacuum)
+    int4 regions[noalloc::kMaxRegions];
+    int slot[1024];
+    for (int i = 0; i < mat->n_mat; ++i) slot[i] = -2;
+    int n_used = 0;
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < n_region; ++r) {
+        const int code = b->regions[4 * r];
+        if (code < 0 || code >= mat->n_mat) return fail(GADEP_E_INVAL, "gadep_run_noalloc: solid material %d has no table", code);
+        if (slot[code] == -2) {
+            const float *rows = mat->mu + (size_t)code * 3 * ng;
+            bool any = false;
+            for (size_t c = 0; c < 3 * ng; ++c) {
+                if (!(rows[c] >= 0.0f) || !std::isfinite(rows[c]))
+                    return fail(GADEP_E_INVAL, "gadep_run_noalloc: negative or non-finite attenuation");
+                any = any || rows[c] > 0.0f;
+            }
+            if (!any) {
+                slot[code] = -1;
+            } else {
+                if ((size_t)(n_used + 1) * ng > (size_t)noalloc::kMaxTable)
+                    return fail(GADEP_E_INVAL, "gadep_run_noalloc: tables exceed %d entries (materials x grid points)",
+                                noalloc::kMaxTable);
+                slot[code] = n_used++;
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(S->raw + (size_t)slot[code] * 3 * ng, rows, 3 * ng * sizeof(float),
+                                        cudaMemcpyHostToDevice, s);
+            }
+        }
+        regions[r] = make_int4(slot[code], b->regions[4 * r + 1], b->regions[4 * r + 2], b->regions[4 * r + 3]);
+    }
+    regions[0].x = -1;
+    // instance record with its birth region (parity rule for sources outside the mesh)
+    dev::InstDev d{};
+    d.E0 = energy_keV;
+    d.src_kind = src->kind;
+    d.px = src->pos[0]; d.py = src->pos[1]; d.pz = src->pos[2];
+    d.dx = src->dir[0]; d.dy = src->dir[1]; d.dz = src->dir[2];
+    d.radius = src->radius; d.height = src->height; d.n_sides = src->n_sides;
+    d.inst_id = instance;
+    d.hist_offset = opts->history_offset;
+    for (int k = 0; k < GADEP_MAX_GROUPS; ++k) d.scale[k] = opts->group_scale[k];
+    if (src->kind == GADEP_SRC_PRISM) {
+        if (src->solid < 0 || src->solid >= b->geo.n_solid() || src->n_sides < 3 || !(src->radius > 0) || !(src->height > 0))
+            return fail(GADEP_E_INVAL, "gadep_run_noalloc: prism source needs a valid solid, n_sides >= 3, radius, height");
+        d.birth_region = src->solid + 1;
+    } else if (src->kind == GADEP_SRC_POINT || src->kind == GADEP_SRC_DISK || src->kind == GADEP_SRC_PENCIL) {
+        if (src->kind == GADEP_SRC_DISK && !(src->radius > 0)) return fail(GADEP_E_INVAL, "gadep_run_noalloc: disk radius");
+        if (src->kind == GADEP_SRC_PENCIL) {
+            const double n2 = (double)src->dir[0] * src->dir[0] + (double)src->dir[1] * src->dir[1] +
+                              (double)src->dir[2] * src->dir[2];
+            if (!(std::fabs(n2 - 1.0) < 1e-5)) return fail(GADEP_E_INVAL, "gadep_run_noalloc: pencil direction must be a unit vector");
+        }
+        const double q[3] = { src->pos[0], src->pos[1], src->pos[2] };
+        const int32_t r = locate_point_fixed(b->geo, q);
+        if (r < -1) return fail(GADEP_E_INVAL, "gadep_run_noalloc: source position lies on a surface");
+        d.birth_region = r + 1;
+    } else {
+        return fail(GADEP_E_INVAL, "gadep_run_noalloc: unknown source kind %d", src->kind);
+    }
+    const unsigned long long ends[2] = { n_hist, n_hist };
+
+    // launch shape (same kernel and shape rule as gadep_run)
+    const int block = opts->block ? opts->block : 256;
+    const size_t smem = (size_t)n_used * ng * sizeof(float4) + (size_t)n_region * sizeof(int4) + 8;
+    int dev_smem = 0, n_sm = 0, bps = 0;
+    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, b->device);
+    if (smem > (size_t)dev_smem) return fail(GADEP_E_INVAL, "gadep_run_noalloc: tables need too much shared memory");
+    void *kfn = (void *)dev::transport_kernel<false, false>;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn, block, smem);
+    if (e == cudaSuccess && bps < 1) return fail(GADEP_E_CUDA, "gadep_run_noalloc: kernel does not fit on the device");
+    if (opts->blocks_per_sm > 0) bps = std::min(bps, opts->blocks_per_sm);
+
+    // stage inputs into the scratch array, clear what must start at zero
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S->regions, regions, (size_t)n_region * sizeof(int4), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&S->inst, &d, sizeof(d), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S->inst_end, ends, sizeof(ends), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&S->tally, 0, sizeof(S->tally), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&S->work, 0, sizeof(S->work), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->counters, 0, sizeof(S->counters), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(spectrum_dev, 0, sizeof(uint32_t) * (size_t)opts->n_bins, s);
+    if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(e, "gadep_run_noalloc: staging"); }
+    if (n_used > 0) {
+        const int n = n_used * (int)ng;
+        noalloc::interleave_tables<<<(n + 255) / 256, 256, 0, s>>>(S->raw, n_used, (int)ng, S->xs);
+    }
+    dev::Params P{};
+    P.nodes = (const float4 *)b->d_nodes;
+    P.tris = (const float4 *)b->d_tris;
+    P.xs = S->xs;
+    P.regions = S->regions;
+    P.inst = &S->inst;
+    P.inst_end = S->inst_end;
+    P.tally = &S->tally;
+    P.spectra = spectrum_dev;
+    P.work = &S->work;
+    P.edep_trace = nullptr;
+    P.n_trace = 0;
+    P.total = n_hist;
+    P.n_mat = n_used;
+    P.n_grid = mat->n_grid;
+    P.n_region = n_region;
+    P.n_inst = 1;
+    P.lnE_min = (float)std::log(mat->E_min);
+    P.inv_dlnE = (float)((mat->n_grid - 1) / (std::log(mat->E_max) - std::log(mat->E_min)));
+    P.key0 = (uint32_t)opts->seed;
+    P.key1 = (uint32_t)(opts->seed >> 32);
+    P.e_cut = opts->e_cut_keV;
+    P.fep_delta = opts->fep_delta_keV;
+    P.e_max = opts->e_max_keV;
+    P.bin_scale = (float)opts->n_bins / opts->e_max_keV;
+    P.n_bins = opts->n_bins;
+    P.step_cap = opts->step_cap;
+    P.n_group = opts->n_group;
+    P.chunk = opts->chunk > 0 ? opts->chunk : 256;
+    for (int k = 0; k < 3; ++k) { P.root_lo[k] = 0.0f; P.root_hi[k] = -1.0f; }
+    if (b->regions[3] >= 0) {
+        const float *f = b->nodes.data() + (size_t)b->regions[3] * 16;
+        int32_t w[4];
+        std::memcpy(w, &f[12], 16);
+        for (int k = 0; k < 3; ++k) { P.root_lo[k] = INFINITY; P.root_hi[k] = -INFINITY; }
+        for (int c = 0; c < 2; ++c) {
+            if (w[c] < 0 && ((~w[c]) & 7) == 0) continue;
+            const float lo[3] = { f[4 * c + 0], f[4 * c + 2], f[8 + 2 * c] };
+            const float hi[3] = { f[4 * c + 1], f[4 * c + 3], f[9 + 2 * c] };
+            for (int k = 0; k < 3; ++k) {
+                P.root_lo[k] = std::min(P.root_lo[k], lo[k]);
+                P.root_hi[k] = std::max(P.root_hi[k], hi[k]);
+            }
+        }
+    }
+    if (n_hist > 0)
+        dev::transport_kernel<false, false><<<n_sm * bps, block, smem, s>>>(P, S->counters);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "gadep_run_noalloc: launch");
+    // tallies back to the host, finalise
+    dev::TallyDev t;
+    e = cudaMemcpyAsync(&t, &S->tally, sizeof(t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "gadep_run_noalloc: results");
+    std::memset(result, 0, sizeof(*result));
+    result->n_hist = t.n_hist; result->n_fep = t.n_fep; result->n_zero = t.n_zero; result->n_over = t.n_over;
+    result->n_err = t.n_err; result->n_segments = t.n_segments; result->n_interactions = t.n_interactions;
+    result->fepe = t.n_hist ? (double)t.n_fep / (double)t.n_hist : 0.0;
+    result->sigma = t.n_hist ? std::sqrt(result->fepe * (1.0 - result->fepe) / (double)t.n_hist) : 0.0;
+    result->sum_dep_active = t.sum_dep_active; result->sum_dep_all = t.sum_dep_all; result->sum_esc = t.sum_esc;
+    result->dev_err = (uint32_t)t.err_bits;
+    if (t.err_bits) return fail(GADEP_E_DEVICE, "device error word set (see gadep_result.dev_err)");
+    return GADEP_OK;
 }
