@@ -155,6 +155,63 @@ def cpu_baseline(cfg, budget_s=15.0, threads=None):
                       "%.1f s" % (n, len(cfg["energies"]), n - 1, dt)}
 
 
+def measure_forms(dev, scale=1.0):
+    """Batched and gradient forms against the plain per-instance kernel, same
+    histories (hence the same FEPE sigma) on the same GPU.
+
+    batched: bare-cylinder detector with a water prism, 40 energies x 3 sources,
+    log-uniform 1e6-5e7 histories per instance (1.5e9 in all): 120 plain
+    launches vs one autotuned persistent launch replayed from a CUDA graph.
+    gradient: coax detector + water prism volume source, 4 energies x 5e7
+    histories: plain launches vs the score-accumulating kernel (dFEPE/ds for 4
+    density groups); also against central finite differences (1 + 2 x 4 runs).
+    """
+    import torch
+    from paper_2605_25963_gb300 import api, batch
+    out = {}
+    mats = api.Materials.default()
+    # ---- batched ----
+    m3 = api.detmesh_build(W.BATCH_DET)
+    b3 = api.gadep_bvh_build(m3, dev)
+    items = [(E, W.BATCH_SOURCES[s], max(1, int(n * scale)), i, [1, 1, 1, sm])
+             for i, (E, s, n, sm) in enumerate(W.batch_instances())]
+    total = sum(it[2] for it in items)
+    t_plain, plans = batch.time_plain(b3, mats, items)
+    del plans
+    kw, table = batch.autotune(b3, mats, items)
+    g = batch.GraphBatch(b3, mats, items, kw)
+    g.replay()
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    g.replay()
+    e.record()
+    torch.cuda.synchronize()
+    t_batch = a.elapsed_time(e) / 1e3
+    res, _, _, _ = g.results(want_spectra=False)
+    out["batched"] = {"instances": len(items), "histories": total, "plain_s": t_plain, "batched_s": t_batch,
+                      "plain_hist_per_s": total / t_plain, "batched_hist_per_s": total / t_batch,
+                      "batched_vs_plain": t_plain / t_batch, "autotuned": kw,
+                      "autotune_ms": [[k, round(v, 3)] for k, v in table],
+                      "fepe_first": res[0]["fepe"], "n_err": sum(r["n_err"] for r in res)}
+    # ---- gradient ----
+    m4 = api.detmesh_build(W.GRAD_DET)
+    b4 = api.gadep_bvh_build(m4, dev)
+    n4 = max(1, int(W.GRAD_HISTORIES * scale))
+    items4 = [(E, W.GRAD_SOURCE, n4, i, [1, 1, 1, 1]) for i, E in enumerate(W.GRAD_ENERGIES)]
+    t_p, _ = batch.time_plain(b4, mats, items4)
+    t_g, gplans = batch.time_plain(b4, mats, items4, opts_kw=dict(n_group=4), grad=True)
+    grads = []
+    for p in gplans:
+        res, _, d, ds = p.results(want_spectra=False)
+        grads.append({"fepe": res[0]["fepe"], "dfepe": [float(x) for x in d[0]],
+                      "dsigma": [float(x) for x in ds[0]]})
+    out["gradient"] = {"histories": n4 * len(items4), "plain_s": t_p, "grad_s": t_g,
+                       "grad_vs_plain": t_p / t_g, "grad_vs_central_fd": (1 + 2 * 4) * t_p / t_g,
+                       "per_energy": dict(zip([str(E) for E in W.GRAD_ENERGIES], grads))}
+    return out
+
+
 def run_reference(args, cfg, rank, world):
     if rank != 0:
         return
@@ -182,6 +239,8 @@ def main():
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched / gradient comparison")
+    ap.add_argument("--forms-scale", type=float, default=1.0, help="history-count scale of the form runs")
     args = ap.parse_args()
     cfg = workload_config(args.workload, args.hist)
 
@@ -211,7 +270,8 @@ def main():
     t_bvh = time.perf_counter() - t0
     mats = api.Materials.default()
     n = cfg["n_hist"]
-    offset = rank * n                      # disjoint history ids per rank
+    from paper_2605_25963_gb300 import dist as shard
+    offset = shard.history_offset(rank, n)   # disjoint history ids per rank
     opts = api.make_opts(history_offset=offset, block=args.block, chunk=args.chunk)
     plans = [api.Plan(bvh, mats, api.make_instances([(E, cfg["src"], n, i, [])]), opts)
              for i, E in enumerate(cfg["energies"])]
@@ -262,18 +322,19 @@ def main():
     # results of the last step (FEPE per energy)
     fepe = []
     for p in plans:
-        res, _, _, _ = p.results(want_spectra=False)
+        res, _, _, _ = p.results(want_spectra=False, raise_device_errors=False)
         fepe.append({"E_keV": None, "fepe": res[0]["fepe"], "sigma": res[0]["sigma"], "n_err": res[0]["n_err"],
-                     "segments": res[0]["n_segments"]})
+                     "dev_err": res[0]["dev_err"], "segments": res[0]["n_segments"]})
     for f, E in zip(fepe, cfg["energies"]):
         f["E_keV"] = E
 
     # algorithmic work of one step (instrumented copy of the kernel, untimed)
-    nodes = tris = 0
+    nodes = tris = relocated = 0
     for i, E in enumerate(cfg["energies"]):
-        _, nv, nt = api.gadep_count_work(bvh, mats, api.make_instances([(E, cfg["src"], n, i, [])]), opts)
+        _, nv, nt, nr = api.gadep_count_work(bvh, mats, api.make_instances([(E, cfg["src"], n, i, [])]), opts)
         nodes += nv
         tris += nt
+        relocated += nr
     flops_per_step = FLOP_PER_NODE * nodes + FLOP_PER_TRI * tris
     kernel_s = sum(sum(x) for x in launch_ms) / 1e3 / args.steps     # per step, all four launches
     achieved_tflops = flops_per_step / kernel_s / 1e12
@@ -305,6 +366,10 @@ def main():
         e2e = {"value": hist_per_step * max(1, args.steps) / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    forms = None
+    if not args.no_forms and world == 1:
+        forms = measure_forms(dev, args.forms_scale)
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(cfg)
@@ -323,13 +388,15 @@ def main():
                          "frac": achieved_tflops / peak_tflops, "traffic": recorded_traffic(args.workload),
                          "peak_note": "FP32 non-tensor: %d SMs x %d lanes x 2 x %.0f MHz (derived)" % (
                              SM_COUNT, FP32_LANES_PER_SM, sm_max),
-                         "per_query": {"nodes": nodes / max(segs, 1), "tris": tris / max(segs, 1)},
+                         "per_query": {"nodes": nodes / max(segs, 1), "tris": tris / max(segs, 1),
+                                       "relocated": relocated / max(segs, 1)},
                          "queries_per_step": segs},
             "cpu_baseline": cb,
             "e2e": e2e,
             "gpu_launches": args.steps * len(plans),
             "clocks": clocks,
             "fepe": fepe,
+            "forms": forms,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -324,13 +324,16 @@ gadep_status gadep_plan_shape(const gadep_plan *p, int32_t *grid, int32_t *block
 void gadep_plan_destroy(gadep_plan *p);
 
 /* Work counters of the traversal for one batch (same histories as gadep_run_batch):
- * BVH nodes visited and triangles tested, summed over all segment queries.  Runs
- * an instrumented copy of the transport kernel; used to turn the measured time
- * into algorithmic bytes and FLOPs per query.  results: host [n_inst]. */
+ * BVH nodes visited and triangles tested, summed over all segment queries, and the
+ * number of queries that found no surface in their region's tree and were
+ * relocated through the tree of every triangle (photons a rounding error past a
+ * boundary; `relocated` may be NULL).  Runs an instrumented copy of the transport
+ * kernel; used to turn the measured time into algorithmic bytes and FLOPs per
+ * query.  results: host [n_inst]. */
 gadep_status gadep_count_work(const gadep_bvh *b, const gadep_materials *mat, int32_t n_inst,
                               const gadep_instance *inst, const gadep_opts *opts,
                               gadep_result *results, uint64_t *nodes_visited,
-                              uint64_t *tris_tested, void *stream);
+                              uint64_t *tris_tested, uint64_t *relocated, void *stream);
 
 /* Philox4x32-10 stream words of one history computed on the GPU (layout:
  * key = (seed lo, seed hi), counter = (block, hid lo, hid hi, instance)).

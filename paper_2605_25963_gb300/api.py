@@ -298,10 +298,12 @@ def gadep_count_work(bvh: Bvh, mat: Materials, instances, opts=None, stream=None
     o = opts if opts is not None else make_opts()
     n = len(instances)
     res = (capi.gadep_result * n)()
-    nodes, tris = C.c_uint64(), C.c_uint64()
-    check(capi.load().gadep_count_work(bvh.handle, C.byref(mat.c), n, instances, C.byref(o), res,
-                                       C.byref(nodes), C.byref(tris), _stream(stream)))
-    return [result_dict(r) for r in res], nodes.value, tris.value
+    nodes, tris, reloc = C.c_uint64(), C.c_uint64(), C.c_uint64()
+    st = capi.load().gadep_count_work(bvh.handle, C.byref(mat.c), n, instances, C.byref(o), res,
+                                      C.byref(nodes), C.byref(tris), C.byref(reloc), _stream(stream))
+    if st != capi.GADEP_E_DEVICE:
+        check(st)
+    return [result_dict(r) for r in res], nodes.value, tris.value, reloc.value
 
 
 class Plan:
@@ -331,12 +333,16 @@ class Plan:
         check(capi.load().gadep_plan_launch(self._h, spectra.data_ptr() if spectra is not None else None,
                                             _stream(stream)))
 
-    def results(self, want_spectra=True, stream=None):
+    def results(self, want_spectra=True, stream=None, raise_device_errors=True):
+        """Tallies of the last launch.  With raise_device_errors=False a set device
+        error word is reported through each result's n_err / dev_err instead."""
         res = (capi.gadep_result * self.n_inst)()
         spec = np.zeros((self.n_inst, self.opts.n_bins), dtype=np.uint32) if want_spectra else None
         ng = max(self.opts.n_group, 1)
         d = np.zeros((self.n_inst, ng), dtype=np.float64)
         ds = np.zeros((self.n_inst, ng), dtype=np.float64)
-        check(capi.load().gadep_plan_results(self._h, spec.ctypes.data if spec is not None else None, res,
-                                             _ptr(d, C.c_double), _ptr(ds, C.c_double), _stream(stream)))
+        st = capi.load().gadep_plan_results(self._h, spec.ctypes.data if spec is not None else None, res,
+                                            _ptr(d, C.c_double), _ptr(ds, C.c_double), _stream(stream))
+        if not (st == capi.GADEP_E_DEVICE and not raise_device_errors):
+            check(st)
         return [result_dict(r) for r in res], spec, d, ds

@@ -136,7 +136,7 @@ def load(build_if_missing: bool = True):
         "gadep_plan_shape": (st, [vp, P(C.c_int32), P(C.c_int32), P(C.c_int32)]),
         "gadep_plan_destroy": (None, [vp]),
         "gadep_count_work": (st, [vp, P(gadep_materials), C.c_int32, P(gadep_instance), P(gadep_opts),
-                                  P(gadep_result), P(C.c_uint64), P(C.c_uint64), vp]),
+                                  P(gadep_result), P(C.c_uint64), P(C.c_uint64), P(C.c_uint64), vp]),
         "gadep_philox_words": (st, [C.c_uint64, C.c_uint64, C.c_uint32, C.c_int32, vp, vp]),
         "gadep_run_noalloc": (st, [vp, P(gadep_materials), P(gadep_source), C.c_float, C.c_uint64, C.c_uint32,
                                    P(gadep_opts), vp, P(gadep_result), vp]),

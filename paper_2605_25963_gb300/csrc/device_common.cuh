@@ -127,7 +127,7 @@ __device__ __forceinline__ void tri_test(const float4 *__restrict__ tris, int i,
     }
 }
 
-struct TravStats { uint32_t nodes, tris; };
+struct TravStats { uint32_t nodes, tris, relocated; };
 
 // Child word of a node: >= 0 inner node index; < 0 leaf ~(first << 3 | count).
 constexpr int kSentinel = 0x7fffffff;

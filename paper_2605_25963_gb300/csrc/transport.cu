@@ -85,6 +85,7 @@ struct Params {
     float e_cut, fep_delta, e_max, bin_scale;
     int n_bins, step_cap, n_group, chunk;
     float root_lo[3], root_hi[3];       // bounds of every triangle (padded)
+    int root_all;                       // tree over every triangle
 };
 
 // Slab test of the ray (t >= 0) against an axis-aligned box.
@@ -348,8 +349,19 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsig
                 // region record: material slot, active | (group + 1) << 1, parent, tree root
                 const int4 R = s_reg[region];
                 const int group = (R.y >> 1) - 1;
-                const int hit = traverse<COUNT>(P.nodes, P.tris, R.w, ox, oy, oz, dx, dy, dz, t_cur, last_tri,
-                                                t_hit, entering, herr, ts);
+                int hit = traverse<COUNT>(P.nodes, P.tris, R.w, ox, oy, oz, dx, dy, dz, t_cur, last_tri,
+                                          t_hit, entering, herr, ts);
+                if (hit < 0 && region != 0 && !(herr & ERR_STACK)) {
+                    // Inside a solid every ray meets that solid's boundary, so the
+                    // photon actually sits a rounding error past it (an interaction
+                    // point computed in FP32 right at a surface).  Relocate by the
+                    // nearest surface of the whole mesh and the nesting-tree rule;
+                    // with no surface ahead it is outside every solid.
+                    hit = traverse<COUNT>(P.nodes, P.tris, P.root_all, ox, oy, oz, dx, dy, dz, t_cur, last_tri,
+                                          t_hit, entering, herr, ts);
+                    if (COUNT) ts.relocated++;
+                    if (hit < 0) region = 0;
+                }
                 float pe = 0.0f, co = 0.0f, pa = 0.0f;
                 if (R.x >= 0) mu_at(s_xs + (size_t)R.x * P.n_grid, P.n_grid, P.lnE_min, P.inv_dlnE, E, pe, co, pa);
                 const float mu_unit = pe + co + pa;
@@ -498,6 +510,7 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsig
     if (COUNT) {
         atomicAdd(&counters[0], (unsigned long long)ts.nodes);
         atomicAdd(&counters[1], (unsigned long long)ts.tris);
+        if (ts.relocated) atomicAdd(&counters[2], (unsigned long long)ts.relocated);
     }
 }
 
@@ -944,6 +957,7 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
     P.step_cap = opts->step_cap;
     P.n_group = opts->n_group;
     P.chunk = opts->chunk > 0 ? opts->chunk : 256;
+    P.root_all = b->root_all;
     // scene bounds seen from the world = union of the world tree's root child boxes
     for (int k = 0; k < 3; ++k) { P.root_lo[k] = 0.0f; P.root_hi[k] = -1.0f; }
     if (b->regions[3] >= 0) {
@@ -1138,7 +1152,7 @@ extern "C" gadep_status gadep_grad(const gadep_bvh *b, const gadep_materials *ma
 extern "C" gadep_status gadep_count_work(const gadep_bvh *b, const gadep_materials *mat, int32_t n_inst,
                                          const gadep_instance *inst, const gadep_opts *opts,
                                          gadep_result *results, uint64_t *nodes_visited,
-                                         uint64_t *tris_tested, void *stream)
+                                         uint64_t *tris_tested, uint64_t *relocated, void *stream)
 {
     gadep::clear_error();
     if (!results || !nodes_visited || !tris_tested) return fail(GADEP_E_INVAL, "gadep_count_work: NULL output");
@@ -1147,6 +1161,7 @@ extern "C" gadep_status gadep_count_work(const gadep_bvh *b, const gadep_materia
                                 c, true, (cudaStream_t)stream);
     *nodes_visited = c[0];
     *tris_tested = c[1];
+    if (relocated) *relocated = c[2];
     return st;
 }
 
@@ -1373,6 +1388,7 @@ extern "C" gadep_status gadep_run_noalloc(const gadep_bvh *b, const gadep_materi
     P.step_cap = opts->step_cap;
     P.n_group = opts->n_group;
     P.chunk = opts->chunk > 0 ? opts->chunk : 256;
+    P.root_all = b->root_all;
     for (int k = 0; k < 3; ++k) { P.root_lo[k] = 0.0f; P.root_hi[k] = -1.0f; }
     if (b->regions[3] >= 0) {
         const float *f = b->nodes.data() + (size_t)b->regions[3] * 16;
