@@ -160,10 +160,11 @@ def measure_forms(dev, scale=1.0):
     histories (hence the same FEPE sigma) on the same GPU.
 
     batched: bare-cylinder detector with a water prism, 40 energies x 3 sources,
-    log-uniform 1e6-5e7 histories per instance (1.5e9 in all): 120 plain
-    launches vs one autotuned persistent launch replayed from a CUDA graph.
+    log-uniform 1e6-5e7 histories per instance (1.5e9 in all): 120 per-instance
+    runs (each in the form AUTO picks) vs one batched run in the autotuned form
+    (the megakernel replayed from a CUDA graph, or the wavefront kernels).
     gradient: coax detector + water prism volume source, 4 energies x 5e7
-    histories: plain launches vs the score-accumulating kernel (dFEPE/ds for 4
+    histories: plain runs vs the score-accumulating kernels (dFEPE/ds for 4
     density groups); also against central finite differences (1 + 2 x 4 runs).
     """
     import torch
@@ -176,22 +177,33 @@ def measure_forms(dev, scale=1.0):
     items = [(E, W.BATCH_SOURCES[s], max(1, int(n * scale)), i, [1, 1, 1, sm])
              for i, (E, s, n, sm) in enumerate(W.batch_instances())]
     total = sum(it[2] for it in items)
-    t_plain, plans = batch.time_plain(b3, mats, items)
-    del plans
+    t_plain, _ = batch.time_plain(b3, mats, items)
     kw, table = batch.autotune(b3, mats, items)
-    g = batch.GraphBatch(b3, mats, items, kw)
-    g.replay()
-    torch.cuda.synchronize()
     a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    g.replay()
-    e.record()
-    torch.cuda.synchronize()
+    if kw.get("variant") == batch.WAVEFRONT:
+        runner = api.Plan(b3, mats, api.make_instances(items), api.make_opts(**kw))
+        runner.launch()
+        torch.cuda.synchronize()
+        a.record()
+        runner.launch()
+        e.record()
+        torch.cuda.synchronize()
+        res, _, _, _ = runner.results(want_spectra=False)
+        how = "wavefront plan"
+    else:
+        g = batch.GraphBatch(b3, mats, items, kw)
+        g.replay()
+        torch.cuda.synchronize()
+        a.record()
+        g.replay()
+        e.record()
+        torch.cuda.synchronize()
+        res, _, _, _ = g.results(want_spectra=False)
+        how = "megakernel replayed from a CUDA graph"
     t_batch = a.elapsed_time(e) / 1e3
-    res, _, _, _ = g.results(want_spectra=False)
     out["batched"] = {"instances": len(items), "histories": total, "plain_s": t_plain, "batched_s": t_batch,
                       "plain_hist_per_s": total / t_plain, "batched_hist_per_s": total / t_batch,
-                      "batched_vs_plain": t_plain / t_batch, "autotuned": kw,
+                      "batched_vs_plain": t_plain / t_batch, "autotuned": kw, "batched_form": how,
                       "autotune_ms": [[k, round(v, 3)] for k, v in table],
                       "fepe_first": res[0]["fepe"], "n_err": sum(r["n_err"] for r in res)}
     # ---- gradient ----
@@ -200,10 +212,9 @@ def measure_forms(dev, scale=1.0):
     n4 = max(1, int(W.GRAD_HISTORIES * scale))
     items4 = [(E, W.GRAD_SOURCE, n4, i, [1, 1, 1, 1]) for i, E in enumerate(W.GRAD_ENERGIES)]
     t_p, _ = batch.time_plain(b4, mats, items4)
-    t_g, gplans = batch.time_plain(b4, mats, items4, opts_kw=dict(n_group=4), grad=True)
+    t_g, gres = batch.time_plain(b4, mats, items4, opts_kw=dict(n_group=4), grad=True, keep_results=True)
     grads = []
-    for p in gplans:
-        res, _, d, ds = p.results(want_spectra=False)
+    for res, _, d, ds in gres:
         grads.append({"fepe": res[0]["fepe"], "dfepe": [float(x) for x in d[0]],
                       "dsigma": [float(x) for x in ds[0]]})
     out["gradient"] = {"histories": n4 * len(items4), "plain_s": t_p, "grad_s": t_g,
@@ -237,6 +248,8 @@ def main():
     ap.add_argument("--hist", type=int, default=0, help="histories per energy (default: the workload's)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--variant", default="auto", choices=["auto", "mega", "wavefront"])
+    ap.add_argument("--wf-slots", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / gradient comparison")
@@ -272,7 +285,8 @@ def main():
     n = cfg["n_hist"]
     from paper_2605_25963_gb300 import dist as shard
     offset = shard.history_offset(rank, n)   # disjoint history ids per rank
-    opts = api.make_opts(history_offset=offset, block=args.block, chunk=args.chunk)
+    opts = api.make_opts(history_offset=offset, block=args.block, chunk=args.chunk,
+                         variant={"auto": 0, "mega": 1, "wavefront": 2}[args.variant], wf_slots=args.wf_slots)
     plans = [api.Plan(bvh, mats, api.make_instances([(E, cfg["src"], n, i, [])]), opts)
              for i, E in enumerate(cfg["energies"])]
     stream = torch.cuda.current_stream()

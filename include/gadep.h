@@ -227,6 +227,7 @@ typedef struct {
     int32_t  blocks_per_sm;   /* persistent grid = SMs x this (0 = occupancy maximum) */
     int32_t  n_group;         /* density groups scored by gadep_grad (<= 4) */
     float    group_scale[GADEP_MAX_GROUPS];  /* density scale per group (default 1) */
+    int32_t  wf_slots;        /* wavefront variant: photon slots in device memory (0 = 2^20) */
 } gadep_opts;
 
 /* Fill *o with the defaults above (seed 1, offset 0, variant AUTO, scales 1). */

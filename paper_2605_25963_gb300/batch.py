@@ -1,29 +1,33 @@
-"""Batched runs: many (energy, source, history count) instances in one persistent
-launch, captured in a CUDA graph, with an autotuned launch shape.
+"""Batched runs: many (energy, source, history count) instances in one launch.
 
-The device side is the plan of libgadep (``gadep_plan_*``): one work counter over
-the flattened history range of all instances feeds every warp, so instances with
-uneven history counts share the GPU without per-instance launch tails.  This
-module captures the plan's launch (tally clearing + kernel) once and replays it,
-and picks block size, histories per warp fetch and blocks per SM by timing
-candidates on a scaled-down copy of the batch.
+The device side is a libgadep plan (``gadep_plan_*``): one work counter over the
+flattened history range of all instances feeds every warp, so instances with
+uneven history counts share the GPU without per-instance launch tails.  Two
+forms exist: the persistent megakernel (one kernel launch, which this module can
+capture in a CUDA graph and replay) and the wavefront kernels (photon slots in
+device memory, birth / trace / physics per iteration, driven from the host).
+``autotune`` times both forms and the megakernel's launch shapes on a
+scaled-down copy of the batch and keeps the fastest.
 """
 from __future__ import annotations
 
 import itertools
-import time
 
 from . import api
 
+MEGA, WAVEFRONT = 1, 2
+
 
 class GraphBatch:
-    """A plan whose launch is captured in a CUDA graph and replayed."""
+    """A megakernel plan whose launch is captured in a CUDA graph and replayed."""
 
     def __init__(self, bvh, mats, items, opts_kw=None, grad=False):
         import torch
         self.torch = torch
+        kw = dict(opts_kw or {})
+        kw["variant"] = MEGA
         self.items = list(items)
-        self.opts = api.make_opts(**(opts_kw or {}))
+        self.opts = api.make_opts(**kw)
         self.plan = api.Plan(bvh, mats, api.make_instances(self.items), self.opts, grad=grad)
         self.graph = torch.cuda.CUDAGraph()
         s = torch.cuda.Stream()
@@ -50,46 +54,62 @@ def _scaled(items, total):
     return [(E, s, max(1, int(c * f)), i, sc) for E, s, c, i, sc in items]
 
 
-def autotune(bvh, mats, items, grad=False, sample_histories=4_000_000, candidates=None, repeats=2):
-    """Time each launch shape on a scaled copy of the batch; return (best opts, table)."""
+def default_candidates():
+    cands = [dict(variant=MEGA, block=b, chunk=c, blocks_per_sm=0)
+             for b, c in itertools.product((128, 256), (64, 256, 1024))]
+    cands.append(dict(variant=WAVEFRONT))
+    return cands
+
+
+def _time_plan(plan, repeats):
     import torch
-    cands = candidates or [dict(block=b, chunk=c, blocks_per_sm=0)
-                           for b, c in itertools.product((128, 256), (64, 256, 1024))]
+    plan.launch()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(repeats):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        plan.launch()
+        b.record()
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+def autotune(bvh, mats, items, grad=False, sample_histories=20_000_000, candidates=None, repeats=2):
+    """Time each launch form / shape on a scaled copy of the batch; return (best opts, table)."""
+    cands = candidates or default_candidates()
     sample = api.make_instances(_scaled(items, sample_histories))
     table = []
     for kw in cands:
         plan = api.Plan(bvh, mats, sample, api.make_opts(**kw), grad=grad)
-        plan.launch()
-        torch.cuda.synchronize()
-        best = float("inf")
-        for _ in range(repeats):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            plan.launch()
-            b.record()
-            torch.cuda.synchronize()
-            best = min(best, a.elapsed_time(b))
-        table.append((kw, best))
+        table.append((kw, _time_plan(plan, repeats)))
         del plan
     kw, _ = min(table, key=lambda x: x[1])
     return kw, table
 
 
-def time_plain(bvh, mats, items, opts_kw=None, grad=False):
-    """Per-instance launches (one plan each, created before timing); seconds."""
+def time_plain(bvh, mats, items, opts_kw=None, grad=False, keep_results=False):
+    """Per-instance runs, one plan each, in turn; seconds of device time summed over
+    the launches (plan creation is outside the timed spans).  Returns (seconds,
+    [results per instance] if keep_results)."""
     import torch
-    plans = [api.Plan(bvh, mats, api.make_instances([it]), api.make_opts(**(opts_kw or {})), grad=grad)
-             for it in items]
-    for p in plans[:2]:
-        p.launch()
+    total = 0.0
+    out = []
+    warm = api.Plan(bvh, mats, api.make_instances([items[0]]), api.make_opts(**(opts_kw or {})), grad=grad)
+    warm.launch()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record()
-    for p in plans:
+    del warm
+    for it in items:
+        p = api.Plan(bvh, mats, api.make_instances([it]), api.make_opts(**(opts_kw or {})), grad=grad)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
         p.launch()
-    b.record()
-    torch.cuda.synchronize()
-    del t0
-    return a.elapsed_time(b) / 1e3, plans
+        b.record()
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b) / 1e3
+        if keep_results:
+            out.append(p.results(want_spectra=False))
+        del p
+    return total, out

@@ -23,7 +23,7 @@ LIB = os.path.join(OUT_DIR, "libgadep.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CXX_SOURCES = ["detmesh.cpp", "geometry.cpp", "xs.cpp", "bvh.cpp"]
-CU_SOURCES = ["transport.cu"]
+CU_SOURCES = ["transport.cu", "wavefront.cu"]
 
 
 def _cuda_home() -> str:
@@ -77,6 +77,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         r = subprocess.run(cmd, capture_output=True, text=True)
         return cmd, r
 
+    logs = []
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
         for cmd, r in ex.map(run, jobs):
             if r.returncode != 0:
@@ -84,8 +85,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if verbose and (r.stdout or r.stderr):
                 print(r.stdout + r.stderr, file=sys.stderr)
             if "-Xptxas" in cmd:
-                with open(os.path.join(OUT_DIR, "ptxas.log"), "w") as f:
-                    f.write(r.stdout + r.stderr)
+                logs.append(r.stdout + r.stderr)
+    with open(os.path.join(OUT_DIR, "ptxas.log"), "w") as f:
+        f.write("\n".join(logs))
     tmp = LIB + ".tmp.%d" % os.getpid()
     link = [nvcc, "-shared"] + ARCH + objs + ["-o", tmp, "-lcudart_static", "-lpthread", "-ldl", "-lrt"]
     r = subprocess.run(link, capture_output=True, text=True)

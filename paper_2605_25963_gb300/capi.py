@@ -68,7 +68,7 @@ class gadep_opts(C.Structure):
                 ("fep_delta_keV", C.c_float), ("e_max_keV", C.c_float), ("n_bins", C.c_int32),
                 ("step_cap", C.c_int32), ("variant", C.c_int32), ("block", C.c_int32),
                 ("chunk", C.c_int32), ("blocks_per_sm", C.c_int32), ("n_group", C.c_int32),
-                ("group_scale", C.c_float * MAX_GROUPS)]
+                ("group_scale", C.c_float * MAX_GROUPS), ("wf_slots", C.c_int32)]
 
 
 class gadep_result(C.Structure):

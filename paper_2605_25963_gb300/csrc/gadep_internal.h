@@ -1,12 +1,15 @@
 // gadep_internal.h -- host-side structures shared by the library's translation units.
 #pragma once
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "gadep.h"
 
 namespace gadep {
+
+struct WavefrontBuffers;
 
 // Error reporting: every failing C-ABI call records a thread-local message.
 gadep_status fail(gadep_status s, const char *fmt, ...);
@@ -63,6 +66,12 @@ struct gadep_bvh {
     std::vector<int32_t> regions;        // 4 ints per region: material, active | (group + 1) << 1,
                                          // parent region, root node of the region's tree (-1 = none)
     int32_t root_all = -1;               // tree over every triangle
+    // Photon-slot buffers of the wavefront transport, kept for reuse by the next
+    // run on this mesh (allocating gigabytes per call would dominate short runs).
+    std::mutex wf_mutex;
+    gadep::WavefrontBuffers *wf_cache = nullptr;
+    int wf_cache_slots = 0;
+    bool wf_cache_busy = false;
     gadep_bvh_stats stats{};
     void *d_nodes = nullptr, *d_tris = nullptr, *d_tri_orig = nullptr, *d_regions = nullptr;
 };

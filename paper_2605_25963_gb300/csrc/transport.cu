@@ -24,9 +24,9 @@
 //                spectrum (warp-aggregated atomics), full-energy-peak count,
 //                FP64 sums; with GRAD, density-perturbation scores
 //                score_p = n_coll,p / s_p - sum_p mu_unit * length per history.
-// Cross-section tables (float4 per grid point) and the region table are staged
-// in shared memory per block.  Arithmetic is FP32; counts are integers; sums of
-// scores are FP64.
+// Cross-section tables (float4 per grid point) are read through L1 from global
+// memory; the region table is staged in shared memory per block.  Arithmetic is
+// FP32; counts are integers; sums of scores are FP64.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -38,208 +38,25 @@
 
 #include "device_common.cuh"
 #include "gadep_internal.h"
+#include "transport_common.cuh"
 
 namespace gadep {
 
 gadep_status build_bvh_host(const detmesh_mesh *m, gadep_bvh *out);
 
 namespace dev {
-
-struct InstDev {
-    float E0;
-    int32_t src_kind;
-    float px, py, pz;
-    float dx, dy, dz;
-    float radius, height;
-    int32_t n_sides;
-    int32_t birth_region;
-    uint32_t inst_id;
-    uint32_t pad0;
-    unsigned long long hist_offset;
-    float scale[GADEP_MAX_GROUPS];
-};
-
-struct TallyDev {
-    unsigned long long n_hist, n_fep, n_zero, n_over, n_err, n_segments, n_interactions;
-    unsigned long long err_bits;
-    double sum_dep_active, sum_dep_all, sum_esc;
-    double fep_score[GADEP_MAX_GROUPS], fep_score_sq[GADEP_MAX_GROUPS];
-};
-
-struct Params {
-    const float4 *nodes;
-    const float4 *tris;
-    const float4 *xs;                 // [n_mat][n_grid] (pe, compton, pair, 0), mm^-1
-    const int4 *regions;              // (material slot or -1, active, group, parent)
-    const InstDev *inst;
-    const unsigned long long *inst_end;  // inclusive prefix sums of n_hist
-    TallyDev *tally;
-    uint32_t *spectra;
-    unsigned long long *work;
-    float *edep_trace;
-    unsigned long long n_trace;
-    unsigned long long total;
-    int n_mat, n_grid, n_region, n_inst;
-    float lnE_min, inv_dlnE;
-    uint32_t key0, key1;
-    float e_cut, fep_delta, e_max, bin_scale;
-    int n_bins, step_cap, n_group, chunk;
-    float root_lo[3], root_hi[3];       // bounds of every triangle (padded)
-    int root_all;                       // tree over every triangle
-};
-
-// Slab test of the ray (t >= 0) against an axis-aligned box.
-__device__ __forceinline__ bool ray_hits_box(const float lo[3], const float hi[3], float ox, float oy, float oz,
-                                             float dx, float dy, float dz)
-{
-    float t0 = 0.0f, t1 = INFINITY;
-    const float o[3] = { ox, oy, oz }, d[3] = { dx, dy, dz };
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float inv = 1.0f / (fabsf(d[k]) > 1e-30f ? d[k] : copysignf(1e-30f, d[k]));
-        float a = (lo[k] - o[k]) * inv, b = (hi[k] - o[k]) * inv;
-        t0 = fmaxf(t0, fminf(a, b));
-        t1 = fminf(t1, fmaxf(a, b));
-    }
-    return t0 <= t1;
-}
-
-// Per-lane partial tallies of one instance, flushed on instance change and at exit.
-template <bool GRAD>
-struct Acc {
-    int inst;
-    uint32_t hist, fep, zero, over, err, seg, inter, errbits;
-    float dep, dep_all, esc;
-    double score[GRAD ? 4 : 1], score2[GRAD ? 4 : 1];
-    __device__ void reset(int i)
-    {
-        inst = i; hist = fep = zero = over = err = seg = inter = errbits = 0u;
-        dep = dep_all = esc = 0.0f;
-#pragma unroll
-        for (int g = 0; g < (GRAD ? 4 : 1); ++g) { score[g] = 0.0; score2[g] = 0.0; }
-    }
-    __device__ void flush_lane(TallyDev *T) const
-    {
-        if (inst < 0 || hist == 0) return;
-        TallyDev &t = T[inst];
-        atomicAdd(&t.n_hist, (unsigned long long)hist);
-        if (fep) atomicAdd(&t.n_fep, (unsigned long long)fep);
-        if (zero) atomicAdd(&t.n_zero, (unsigned long long)zero);
-        if (over) atomicAdd(&t.n_over, (unsigned long long)over);
-        if (err) { atomicAdd(&t.n_err, (unsigned long long)err); atomicOr(&t.err_bits, (unsigned long long)errbits); }
-        atomicAdd(&t.n_segments, (unsigned long long)seg);
-        atomicAdd(&t.n_interactions, (unsigned long long)inter);
-        atomicAdd(&t.sum_dep_active, (double)dep);
-        atomicAdd(&t.sum_dep_all, (double)dep_all);
-        atomicAdd(&t.sum_esc, (double)esc);
-        if (GRAD) {
-#pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                atomicAdd(&t.fep_score[g], score[g]);
-                atomicAdd(&t.fep_score_sq[g], score2[g]);
-            }
-        }
-    }
-};
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-template <bool GRAD>
-__device__ void flush_warp(const Acc<GRAD> &a, TallyDev *T)
-{
-    int same = 0;
-    __match_all_sync(0xffffffffu, a.inst, &same);
-    if (!same || a.inst < 0) { a.flush_lane(T); return; }
-    const int lane = threadIdx.x & 31;
-    const uint32_t hist = __reduce_add_sync(0xffffffffu, a.hist);
-    const uint32_t fep = __reduce_add_sync(0xffffffffu, a.fep);
-    const uint32_t zero = __reduce_add_sync(0xffffffffu, a.zero);
-    const uint32_t over = __reduce_add_sync(0xffffffffu, a.over);
-    const uint32_t err = __reduce_add_sync(0xffffffffu, a.err);
-    const uint32_t errbits = __reduce_or_sync(0xffffffffu, a.errbits);
-    const uint32_t seg = __reduce_add_sync(0xffffffffu, a.seg);
-    const uint32_t inter = __reduce_add_sync(0xffffffffu, a.inter);
-    const double dep = warp_sum((double)a.dep), dep_all = warp_sum((double)a.dep_all),
-                 esc = warp_sum((double)a.esc);
-    double sc[4] = { 0, 0, 0, 0 }, sc2[4] = { 0, 0, 0, 0 };
-    if (GRAD) {
-#pragma unroll
-        for (int g = 0; g < 4; ++g) { sc[g] = warp_sum(a.score[g]); sc2[g] = warp_sum(a.score2[g]); }
-    }
-    if (lane == 0 && hist) {
-        TallyDev &t = T[a.inst];
-        atomicAdd(&t.n_hist, (unsigned long long)hist);
-        if (fep) atomicAdd(&t.n_fep, (unsigned long long)fep);
-        if (zero) atomicAdd(&t.n_zero, (unsigned long long)zero);
-        if (over) atomicAdd(&t.n_over, (unsigned long long)over);
-        if (err) { atomicAdd(&t.n_err, (unsigned long long)err); atomicOr(&t.err_bits, (unsigned long long)errbits); }
-        atomicAdd(&t.n_segments, (unsigned long long)seg);
-        atomicAdd(&t.n_interactions, (unsigned long long)inter);
-        atomicAdd(&t.sum_dep_active, dep);
-        atomicAdd(&t.sum_dep_all, dep_all);
-        atomicAdd(&t.sum_esc, esc);
-        if (GRAD) {
-#pragma unroll
-            for (int g = 0; g < 4; ++g) { atomicAdd(&t.fep_score[g], sc[g]); atomicAdd(&t.fep_score_sq[g], sc2[g]); }
-        }
-    }
-}
-
-__device__ __forceinline__ void rotate(float &dx, float &dy, float &dz, float c, float sphi, float cphi)
-{
-    const float s = sqrtf(fmaxf(0.0f, 1.0f - c * c));
-    const float r = sqrtf(dx * dx + dy * dy);
-    float nx, ny, nz;
-    if (r < 1e-9f) {
-        nx = s * cphi; ny = s * sphi; nz = dz > 0.0f ? c : -c;
-    } else {
-        const float ir = 1.0f / r;
-        nx = dx * c + s * (dx * dz * cphi - dy * sphi) * ir;
-        ny = dy * c + s * (dy * dz * cphi + dx * sphi) * ir;
-        nz = dz * c - s * r * cphi;
-    }
-    const float inv = rsqrtf(nx * nx + ny * ny + nz * nz);
-    dx = nx * inv; dy = ny * inv; dz = nz * inv;
-}
-
-__device__ __forceinline__ void iso_dir(Stream &rng, uint32_t k0, uint32_t k1, float &dx, float &dy, float &dz)
-{
-    const float c = 2.0f * rng.u01(k0, k1) - 1.0f;
-    float sp, cp;
-    sincospif(2.0f * rng.u01(k0, k1), &sp, &cp);
-    const float s = sqrtf(fmaxf(0.0f, 1.0f - c * c));
-    dx = s * cp; dy = s * sp; dz = c;
-}
-
-// Interpolated attenuation (pe, compton, pair) of a staged material at energy E.
-__device__ __forceinline__ void mu_at(const float4 *tab, int n_grid, float lnE_min, float inv_dl,
-                                      float E, float &pe, float &co, float &pa)
-{
-    const float g = (logf(E) - lnE_min) * inv_dl;
-    int k = (int)floorf(g);
-    k = min(max(k, 0), n_grid - 2);
-    const float f = fminf(fmaxf(g - (float)k, 0.0f), 1.0f);
-    const float4 a = tab[k], b = tab[k + 1];
-    pe = fmaf(f, b.x - a.x, a.x);
-    co = fmaf(f, b.y - a.y, a.y);
-    pa = E > kTwoMeC2 ? fmaf(f, b.z - a.z, a.z) : 0.0f;
-}
-
 template <bool GRAD, bool COUNT>
 // 4 blocks of 256 threads per SM (64 registers): measured faster than 2 or 3
 // blocks despite the register spills, as the traversal is latency bound.
 __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsigned long long *counters)
 {
+    // Shared memory holds the region table and the instance prefix sums.  The
+    // attenuation tables stay in global memory and are read through L1: staging a
+    // copy per block (16 KB per material) took L1 capacity away from the BVH
+    // nodes and measured 16 % slower.
     extern __shared__ float4 smem[];
-    float4 *s_xs = smem;
-    int4 *s_reg = reinterpret_cast<int4 *>(smem + (size_t)P.n_mat * P.n_grid);
+    int4 *s_reg = reinterpret_cast<int4 *>(smem);
     unsigned long long *s_end = reinterpret_cast<unsigned long long *>(s_reg + P.n_region);
-    for (int i = threadIdx.x; i < P.n_mat * P.n_grid; i += blockDim.x) s_xs[i] = P.xs[i];
     for (int i = threadIdx.x; i < P.n_region; i += blockDim.x) s_reg[i] = P.regions[i];
     for (int i = threadIdx.x; i < P.n_inst; i += blockDim.x) s_end[i] = P.inst_end[i];
     __syncthreads();
@@ -287,7 +104,7 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsig
             if (!busy && rank < take) {
                 g_hist = pool_next + rank;
                 while (g_hist >= s_end[inst]) ++inst;
-                if (acc.inst != inst) { acc.flush_lane(P.tally); acc.reset(inst); }
+                if (acc.inst != inst) { acc.flush_lane(block_tally(P)); acc.reset(inst); }
                 const InstDev &I = P.inst[inst];
                 const unsigned long long local = g_hist - (inst ? s_end[inst - 1] : 0ull);
                 rng.init(I.hist_offset + local, I.inst_id);
@@ -363,7 +180,7 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsig
                     if (hit < 0) region = 0;
                 }
                 float pe = 0.0f, co = 0.0f, pa = 0.0f;
-                if (R.x >= 0) mu_at(s_xs + (size_t)R.x * P.n_grid, P.n_grid, P.lnE_min, P.inv_dlnE, E, pe, co, pa);
+                if (R.x >= 0) mu_at(P.xs + (size_t)R.x * P.n_grid, P.n_grid, P.lnE_min, P.inv_dlnE, E, pe, co, pa);
                 const float mu_unit = pe + co + pa;
                 const float sc = group >= 0 ? P.inst[inst].scale[group] : 1.0f;
                 const float mu = mu_unit * sc;
@@ -506,7 +323,7 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsig
             busy = false;
         }
     }
-    flush_warp<GRAD>(acc, P.tally);
+    flush_warp<GRAD>(acc, block_tally(P));
     if (COUNT) {
         atomicAdd(&counters[0], (unsigned long long)ts.nodes);
         atomicAdd(&counters[1], (unsigned long long)ts.tris);
@@ -626,6 +443,8 @@ void free_bvh_device(gadep_bvh *b)
 {
     if (!b->d_nodes && !b->d_tris && !b->d_regions) return;
     DeviceGuard g(b->device);
+    wavefront_destroy(b->wf_cache);
+    b->wf_cache = nullptr;
     cudaFree(b->d_nodes);
     cudaFree(b->d_tris);
     cudaFree(b->d_regions);
@@ -656,8 +475,11 @@ struct gadep_plan {
     unsigned long long *d_counters = nullptr;
     gadep::dev::Params P{};
     int grid = 0, block = 256, smem = 0;
+    int n_stripes = 1;                        // tally copies per instance
     bool count = false;
     uint32_t *last_spectra = nullptr;
+    gadep::WavefrontBuffers *wf = nullptr;   // set when the plan runs the wavefront form
+    bool wf_cached = false;                  // wf borrowed from the BVH's cache
 };
 
 namespace {
@@ -784,6 +606,13 @@ extern "C" void gadep_plan_destroy(gadep_plan *p)
         cudaFree(p->d_spectra);
         cudaFree(p->d_work);
         cudaFree(p->d_counters);
+        if (p->wf_cached) {
+            gadep_bvh *bm = const_cast<gadep_bvh *>(p->bvh);
+            std::lock_guard<std::mutex> lock(bm->wf_mutex);
+            bm->wf_cache_busy = false;
+        } else {
+            gadep::wavefront_destroy(p->wf);
+        }
     }
     delete p;
 }
@@ -890,7 +719,7 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
     }
     // launch shape
     p->block = opts->block ? opts->block : 256;
-    const size_t smem = xs.size() * sizeof(float4) + regions.size() * 4 + (size_t)n_inst * 8;
+    const size_t smem = regions.size() * 4 + (size_t)n_inst * 8;
     p->smem = (int)smem;
     DeviceGuard g(p->device);
     if (!g.ok) { gadep_plan_destroy(p); return fail(GADEP_E_CUDA, "plan: cannot select device %d", p->device); }
@@ -909,12 +738,55 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
     if (e != cudaSuccess || bps < 1) { gadep_plan_destroy(p); return fail(GADEP_E_CUDA, "plan: kernel does not fit on the device"); }
     if (opts->blocks_per_sm > 0) bps = std::min(bps, opts->blocks_per_sm);
     p->grid = n_sm * bps;
+    // form of the transport: AUTO takes the wavefront kernels for large runs
+    // (measured faster from a few million histories on) and the megakernel otherwise
+    int variant = opts->variant;
+    if (variant == GADEP_VARIANT_AUTO)
+        variant = (total >= (1ull << 23) && n_inst <= kWavefrontMaxInstances) ? GADEP_VARIANT_WAVEFRONT
+                                                                              : GADEP_VARIANT_MEGA;
+    if (variant == GADEP_VARIANT_WAVEFRONT && n_inst > kWavefrontMaxInstances) {
+        gadep_plan_destroy(p);
+        return fail(GADEP_E_INVAL, "plan: the wavefront form takes at most %d instances", kWavefrontMaxInstances);
+    }
+    if (variant == GADEP_VARIANT_WAVEFRONT) {
+        int slots = opts->wf_slots;
+        if (slots <= 0) {
+            slots = 1 << 20;
+            while (slots < (1 << 24) && (unsigned long long)slots * 8 <= total) slots <<= 1;
+        }
+        gadep_bvh *bm = const_cast<gadep_bvh *>(b);
+        {
+            std::lock_guard<std::mutex> lock(bm->wf_mutex);
+            if (!bm->wf_cache_busy) {
+                // keep the largest buffers seen: a run may use more slots than it asked for
+                if (bm->wf_cache && bm->wf_cache_slots < slots) {
+                    wavefront_destroy(bm->wf_cache);
+                    bm->wf_cache = nullptr;
+                }
+                if (!bm->wf_cache) {
+                    st = wavefront_create(p->device, slots, grad, &bm->wf_cache);
+                    if (st == GADEP_OK) bm->wf_cache_slots = slots;
+                }
+                if (bm->wf_cache) {
+                    p->wf = bm->wf_cache;
+                    p->wf_cached = true;
+                    bm->wf_cache_busy = true;
+                }
+            }
+        }
+        if (!p->wf && (st = wavefront_create(p->device, slots, grad, &p->wf)) != GADEP_OK) {
+            gadep_plan_destroy(p);
+            return st;
+        }
+        p->grid = wavefront_trace_grid(p->wf);
+    }
     // device buffers
     if ((st = dalloc(&p->d_xs, std::max<size_t>(xs.size(), 1), "plan tables")) != GADEP_OK ||
         (st = dalloc((int32_t **)&p->d_regions, regions.size(), "plan regions")) != GADEP_OK ||
         (st = dalloc(&p->d_inst, (size_t)n_inst, "plan instances")) != GADEP_OK ||
         (st = dalloc(&p->d_end, (size_t)n_inst, "plan prefix")) != GADEP_OK ||
-        (st = dalloc(&p->d_tally, (size_t)n_inst, "plan tallies")) != GADEP_OK ||
+        (st = dalloc(&p->d_tally, (size_t)n_inst * (p->n_stripes = std::max(1, std::min(256, 65536 / n_inst))),
+                     "plan tallies")) != GADEP_OK ||
         (st = dalloc(&p->d_spectra, (size_t)n_inst * p->n_bins, "plan spectra")) != GADEP_OK ||
         (st = dalloc(&p->d_work, 1, "plan work counter")) != GADEP_OK ||
         (st = dalloc(&p->d_counters, 4, "plan counters")) != GADEP_OK) {
@@ -957,6 +829,7 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
     P.step_cap = opts->step_cap;
     P.n_group = opts->n_group;
     P.chunk = opts->chunk > 0 ? opts->chunk : 256;
+    P.n_stripes = p->n_stripes;
     P.root_all = b->root_all;
     // scene bounds seen from the world = union of the world tree's root child boxes
     for (int k = 0; k < 3; ++k) { P.root_lo[k] = 0.0f; P.root_hi[k] = -1.0f; }
@@ -989,12 +862,13 @@ gadep_status plan_launch(gadep_plan *p, uint32_t *spectra_dev, float *edep_trace
     P.n_trace = edep_trace ? n_trace : 0;
     p->last_spectra = P.spectra;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(p->d_tally, 0, sizeof(dev::TallyDev) * p->n_inst, s)) != cudaSuccess ||
+    if ((e = cudaMemsetAsync(p->d_tally, 0, sizeof(dev::TallyDev) * p->n_inst * p->n_stripes, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(P.spectra, 0, sizeof(uint32_t) * (size_t)p->n_inst * p->n_bins, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->d_work, 0, sizeof(unsigned long long), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->d_counters, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
         return cuda_fail(e, "plan launch: memset");
     if (P.total == 0) return GADEP_OK;
+    if (p->wf) return wavefront_run(p->wf, P, p->grad, p->count, p->d_counters, s);
     if (p->grad) {
         if (p->count) dev::transport_kernel<true, true><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
         else dev::transport_kernel<true, false><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
@@ -1010,8 +884,10 @@ gadep_status plan_results(gadep_plan *p, uint32_t *spectra_host, gadep_result *r
                           double *dsigma, unsigned long long *counters, cudaStream_t s)
 {
     DeviceGuard g(p->device);
-    std::vector<dev::TallyDev> T(p->n_inst);
-    cudaError_t e = cudaMemcpyAsync(T.data(), p->d_tally, sizeof(dev::TallyDev) * p->n_inst, cudaMemcpyDeviceToHost, s);
+    const size_t n_copies = (size_t)p->n_inst * p->n_stripes;
+    std::vector<dev::TallyDev> stripes(n_copies);
+    cudaError_t e = cudaMemcpyAsync(stripes.data(), p->d_tally, sizeof(dev::TallyDev) * n_copies,
+                                    cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && spectra_host)
         e = cudaMemcpyAsync(spectra_host, p->last_spectra ? p->last_spectra : p->d_spectra,
                             sizeof(uint32_t) * (size_t)p->n_inst * p->n_bins, cudaMemcpyDeviceToHost, s);
@@ -1020,6 +896,23 @@ gadep_status plan_results(gadep_plan *p, uint32_t *spectra_host, gadep_result *r
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "plan results");
     if (counters) std::memcpy(counters, cnt, sizeof(cnt));
+    // sum the per-block tally copies (integer counts exactly, FP64 sums in stripe order)
+    std::vector<dev::TallyDev> T(p->n_inst);
+    std::memset(T.data(), 0, sizeof(dev::TallyDev) * T.size());
+    for (int k = 0; k < p->n_stripes; ++k) {
+        for (int i = 0; i < p->n_inst; ++i) {
+            const dev::TallyDev &a = stripes[(size_t)k * p->n_inst + i];
+            dev::TallyDev &t = T[i];
+            t.n_hist += a.n_hist; t.n_fep += a.n_fep; t.n_zero += a.n_zero; t.n_over += a.n_over;
+            t.n_err += a.n_err; t.n_segments += a.n_segments; t.n_interactions += a.n_interactions;
+            t.err_bits |= a.err_bits;
+            t.sum_dep_active += a.sum_dep_active; t.sum_dep_all += a.sum_dep_all; t.sum_esc += a.sum_esc;
+            for (int g2 = 0; g2 < GADEP_MAX_GROUPS; ++g2) {
+                t.fep_score[g2] += a.fep_score[g2];
+                t.fep_score_sq[g2] += a.fep_score_sq[g2];
+            }
+        }
+    }
     bool dev_err = false;
     for (int i = 0; i < p->n_inst; ++i) {
         const dev::TallyDev &t = T[i];
@@ -1335,7 +1228,7 @@ extern "C" gadep_status gadep_run_noalloc(const gadep_bvh *b, const gadep_materi
 
     // launch shape (same kernel and shape rule as gadep_run)
     const int block = opts->block ? opts->block : 256;
-    const size_t smem = (size_t)n_used * ng * sizeof(float4) + (size_t)n_region * sizeof(int4) + 8;
+    const size_t smem = (size_t)n_region * sizeof(int4) + 8;
     int dev_smem = 0, n_sm = 0, bps = 0;
     cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, b->device);
@@ -1388,6 +1281,7 @@ extern "C" gadep_status gadep_run_noalloc(const gadep_bvh *b, const gadep_materi
     P.step_cap = opts->step_cap;
     P.n_group = opts->n_group;
     P.chunk = opts->chunk > 0 ? opts->chunk : 256;
+    P.n_stripes = 1;                       // the one tally record of the scratch array
     P.root_all = b->root_all;
     for (int k = 0; k < 3; ++k) { P.root_lo[k] = 0.0f; P.root_hi[k] = -1.0f; }
     if (b->regions[3] >= 0) {
