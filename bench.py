@@ -60,13 +60,15 @@ def workload_config(name, n_hist):
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("transport.cu", "device_common.cuh"):
+    for f in ("transport.cu", "wavefront.cu", "transport_common.cuh", "device_common.cuh"):
         with open(os.path.join(ROOT, "paper_2605_25963_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload):
+def recorded_traffic(workload, kind):
+    """DRAM bytes per launch of kernel `kind` from the committed ncu launch list,
+    or None when the kernels changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
@@ -75,7 +77,7 @@ def recorded_traffic(workload):
     e = d.get(workload)
     if not e or e.get("kernel_hash") != kernel_hash():
         return None
-    return e.get("dram_bytes_per_launch")
+    return e.get("dram_bytes_per_launch", {}).get(kind)
 
 
 def measured_peaks():
@@ -305,6 +307,10 @@ def main():
         flush.fill_(1.0)
         step()
     torch.cuda.synchronize()
+    # per-kernel CUDA events on the launching stream over the timed steps
+    for p in plans:
+        p.set_timing(True)
+        p.kernel_stats(reset=True)
 
     sampler = ClockSampler(dev)
     if dist is not None:
@@ -350,8 +356,21 @@ def main():
         tris += nt
         relocated += nr
     flops_per_step = FLOP_PER_NODE * nodes + FLOP_PER_TRI * tris
-    kernel_s = sum(sum(x) for x in launch_ms) / 1e3 / args.steps     # per step, all four launches
-    achieved_tflops = flops_per_step / kernel_s / 1e12
+    # launches and device time per kernel kind over the timed steps
+    kstats = {}
+    for p in plans:
+        for k, (nl, ms) in p.kernel_stats(reset=True).items():
+            a = kstats.setdefault(k, [0, 0.0])
+            a[0] += nl
+            a[1] += ms
+        p.set_timing(False)
+    ktot = sum(ms for _, ms in kstats.values()) or 1.0
+    kernels = {k: {"launches": nl, "ms_per_step": ms / args.steps, "share": ms / ktot}
+               for k, (nl, ms) in kstats.items() if nl}
+    # the traversal (all node and triangle work) runs in the megakernel or in the trace kernel
+    dom = "trace" if kstats.get("trace", (0, 0.0))[0] else "mega"
+    dom_launches, dom_ms = kstats[dom]
+    achieved_tflops = flops_per_step * args.steps / (dom_ms / 1e3) / 1e12
     sm_max = (clocks or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     segs = sum(f["segments"] for f in fepe)
@@ -398,8 +417,11 @@ def main():
                        "seed": 1, "triangles": bvh.stats()["n_tri"], "grid": g, "block": blk,
                        "smem_bytes": smem, "l2": "flushed between steps (512 MB write)",
                        "mesh_build_s": round(t_mesh, 4), "bvh_build_s": round(t_bvh, 4)},
-            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / peak_tflops, "traffic": recorded_traffic(args.workload),
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved_tflops, "peak": peak_tflops,
+                         "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
+                         "traffic": recorded_traffic(args.workload, dom),
+                         "launches": dom_launches, "avg_launch_ms": dom_ms / max(dom_launches, 1),
+                         "flop_per_launch": flops_per_step * args.steps / max(dom_launches, 1),
                          "peak_note": "FP32 non-tensor: %d SMs x %d lanes x 2 x %.0f MHz (derived)" % (
                              SM_COUNT, FP32_LANES_PER_SM, sm_max),
                          "per_query": {"nodes": nodes / max(segs, 1), "tris": tris / max(segs, 1),
@@ -407,7 +429,8 @@ def main():
                          "queries_per_step": segs},
             "cpu_baseline": cb,
             "e2e": e2e,
-            "gpu_launches": args.steps * len(plans),
+            "gpu_launches": sum(nl for nl, _ in kstats.values()),
+            "kernels": kernels,
             "clocks": clocks,
             "fepe": fepe,
             "forms": forms,

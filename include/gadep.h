@@ -324,6 +324,24 @@ gadep_status gadep_plan_shape(const gadep_plan *p, int32_t *grid, int32_t *block
                               int32_t *smem_bytes);
 void gadep_plan_destroy(gadep_plan *p);
 
+/* Kernel launches of a plan since the last reset, per kind: the persistent
+ * megakernel, or the six kernels of each wavefront iteration plus the slot-list
+ * initialisation.  With timing on, gadep_plan_launch records a CUDA event pair
+ * on the launching stream around every launch and ms[] sums their elapsed
+ * times (device time of the kernels alone, without host gaps). */
+enum { GADEP_KERNEL_MEGA = 0, GADEP_KERNEL_SPAWN = 1, GADEP_KERNEL_TRACE = 2, GADEP_KERNEL_PHYSICS = 3,
+       GADEP_KERNEL_GEN = 4, GADEP_KERNEL_CTRL = 5, GADEP_KERNEL_INIT = 6, GADEP_KERNEL_SORT = 7,
+       GADEP_N_KERNEL_KINDS = 8 };
+typedef struct {
+    uint64_t launches[8];     /* [GADEP_KERNEL_*] */
+    double   ms[8];           /* [GADEP_KERNEL_*], 0 unless timing was on */
+} gadep_kernel_stats;
+/* on != 0 turns per-launch event timing on for later launches of the plan. */
+gadep_status gadep_plan_set_timing(gadep_plan *p, int32_t on);
+/* Waits for the timed launches (host synchronisation on their events), writes
+ * the statistics to *out (host) and, when reset != 0, clears them. */
+gadep_status gadep_plan_kernel_stats(gadep_plan *p, gadep_kernel_stats *out, int32_t reset);
+
 /* Work counters of the traversal for one batch (same histories as gadep_run_batch):
  * BVH nodes visited and triangles tested, summed over all segment queries, and the
  * number of queries that found no surface in their region's tree and were

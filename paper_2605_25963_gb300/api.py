@@ -333,6 +333,16 @@ class Plan:
         check(capi.load().gadep_plan_launch(self._h, spectra.data_ptr() if spectra is not None else None,
                                             _stream(stream)))
 
+    def set_timing(self, on=True):
+        """Record a CUDA event pair around every kernel of later launches."""
+        check(capi.load().gadep_plan_set_timing(self._h, 1 if on else 0))
+
+    def kernel_stats(self, reset=False):
+        """{kind: (launches, ms)} since the last reset; ms is 0 unless timing was on."""
+        ks = capi.gadep_kernel_stats()
+        check(capi.load().gadep_plan_kernel_stats(self._h, C.byref(ks), 1 if reset else 0))
+        return {k: (int(ks.launches[i]), float(ks.ms[i])) for i, k in enumerate(capi.KERNEL_KINDS)}
+
     def results(self, want_spectra=True, stream=None, raise_device_errors=True):
         """Tallies of the last launch.  With raise_device_errors=False a set device
         error word is reported through each result's n_err / dev_err instead."""

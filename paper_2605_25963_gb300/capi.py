@@ -23,8 +23,11 @@ EXPORTS = (
     "gadep_bvh_get_stats", "gadep_bvh_validate", "gadep_bvh_destroy", "gadep_nearest_hit",
     "gadep_opts_default", "gadep_run", "gadep_run_batch", "gadep_grad", "gadep_plan_create",
     "gadep_plan_launch", "gadep_plan_results", "gadep_plan_shape", "gadep_plan_destroy",
-    "gadep_count_work", "gadep_philox_words", "gadep_run_noalloc",
+    "gadep_count_work", "gadep_philox_words", "gadep_run_noalloc", "gadep_plan_set_timing",
+    "gadep_plan_kernel_stats",
 )
+# kernel kinds of gadep_kernel_stats
+KERNEL_KINDS = ("mega", "spawn", "trace", "physics", "gen", "ctrl", "init", "sort")
 
 
 class GadepError(RuntimeError):
@@ -77,6 +80,10 @@ class gadep_result(C.Structure):
                 ("n_interactions", C.c_uint64), ("fepe", C.c_double), ("sigma", C.c_double),
                 ("sum_dep_active", C.c_double), ("sum_dep_all", C.c_double), ("sum_esc", C.c_double),
                 ("dev_err", C.c_uint32)]
+
+
+class gadep_kernel_stats(C.Structure):
+    _fields_ = [("launches", C.c_uint64 * 8), ("ms", C.c_double * 8)]
 
 
 class gadep_instance(C.Structure):
@@ -135,6 +142,8 @@ def load(build_if_missing: bool = True):
         "gadep_plan_results": (st, [vp, vp, P(gadep_result), P(C.c_double), P(C.c_double), vp]),
         "gadep_plan_shape": (st, [vp, P(C.c_int32), P(C.c_int32), P(C.c_int32)]),
         "gadep_plan_destroy": (None, [vp]),
+        "gadep_plan_set_timing": (st, [vp, C.c_int32]),
+        "gadep_plan_kernel_stats": (st, [vp, P(gadep_kernel_stats), C.c_int32]),
         "gadep_count_work": (st, [vp, P(gadep_materials), C.c_int32, P(gadep_instance), P(gadep_opts),
                                   P(gadep_result), P(C.c_uint64), P(C.c_uint64), P(C.c_uint64), vp]),
         "gadep_philox_words": (st, [C.c_uint64, C.c_uint64, C.c_uint32, C.c_int32, vp, vp]),

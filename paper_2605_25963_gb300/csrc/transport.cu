@@ -164,8 +164,7 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsig
                 float t_hit = INFINITY;
                 bool entering = false;
                 // region record: material slot, active | (group + 1) << 1, parent, tree root
-                const int4 R = s_reg[region];
-                const int group = (R.y >> 1) - 1;
+                int4 R = s_reg[region];
                 int hit = traverse<COUNT>(P.nodes, P.tris, R.w, ox, oy, oz, dx, dy, dz, t_cur, last_tri,
                                           t_hit, entering, herr, ts);
                 if (hit < 0 && region != 0 && !(herr & ERR_STACK)) {
@@ -177,8 +176,12 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsig
                     hit = traverse<COUNT>(P.nodes, P.tris, P.root_all, ox, oy, oz, dx, dy, dz, t_cur, last_tri,
                                           t_hit, entering, herr, ts);
                     if (COUNT) ts.relocated++;
-                    if (hit < 0) region = 0;
+                    if (hit < 0) {
+                        region = 0;
+                        R = s_reg[0];       // the segment runs in the world
+                    }
                 }
+                const int group = (R.y >> 1) - 1;
                 float pe = 0.0f, co = 0.0f, pa = 0.0f;
                 if (R.x >= 0) mu_at(P.xs + (size_t)R.x * P.n_grid, P.n_grid, P.lnE_min, P.inv_dlnE, E, pe, co, pa);
                 const float mu_unit = pe + co + pa;
@@ -480,6 +483,7 @@ struct gadep_plan {
     uint32_t *last_spectra = nullptr;
     gadep::WavefrontBuffers *wf = nullptr;   // set when the plan runs the wavefront form
     bool wf_cached = false;                  // wf borrowed from the BVH's cache
+    gadep::KernelTimer timer;                // launch counts and optional event timing
 };
 
 namespace {
@@ -606,6 +610,7 @@ extern "C" void gadep_plan_destroy(gadep_plan *p)
         cudaFree(p->d_spectra);
         cudaFree(p->d_work);
         cudaFree(p->d_counters);
+        p->timer.release();
         if (p->wf_cached) {
             gadep_bvh *bm = const_cast<gadep_bvh *>(p->bvh);
             std::lock_guard<std::mutex> lock(bm->wf_mutex);
@@ -741,12 +746,14 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
     // form of the transport: AUTO takes the wavefront kernels for large runs
     // (measured faster from a few million histories on) and the megakernel otherwise
     int variant = opts->variant;
+    const bool wf_ok = n_inst <= kWavefrontMaxInstances &&
+                       wavefront_supports((int)(regions.size() / 4), (long long)b->geo.n_tri());
     if (variant == GADEP_VARIANT_AUTO)
-        variant = (total >= (1ull << 23) && n_inst <= kWavefrontMaxInstances) ? GADEP_VARIANT_WAVEFRONT
-                                                                              : GADEP_VARIANT_MEGA;
-    if (variant == GADEP_VARIANT_WAVEFRONT && n_inst > kWavefrontMaxInstances) {
+        variant = (total >= (1ull << 23) && wf_ok) ? GADEP_VARIANT_WAVEFRONT : GADEP_VARIANT_MEGA;
+    if (variant == GADEP_VARIANT_WAVEFRONT && !wf_ok) {
         gadep_plan_destroy(p);
-        return fail(GADEP_E_INVAL, "plan: the wavefront form takes at most %d instances", kWavefrontMaxInstances);
+        return fail(GADEP_E_INVAL, "plan: the wavefront form takes at most %d instances, 256 regions and "
+                                   "2^23 - 1 triangles", kWavefrontMaxInstances);
     }
     if (variant == GADEP_VARIANT_WAVEFRONT) {
         int slots = opts->wf_slots;
@@ -868,7 +875,8 @@ gadep_status plan_launch(gadep_plan *p, uint32_t *spectra_dev, float *edep_trace
         (e = cudaMemsetAsync(p->d_counters, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
         return cuda_fail(e, "plan launch: memset");
     if (P.total == 0) return GADEP_OK;
-    if (p->wf) return wavefront_run(p->wf, P, p->grad, p->count, p->d_counters, s);
+    if (p->wf) return wavefront_run(p->wf, P, p->grad, p->count, p->d_counters, &p->timer, s);
+    p->timer.before(s);
     if (p->grad) {
         if (p->count) dev::transport_kernel<true, true><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
         else dev::transport_kernel<true, false><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
@@ -876,6 +884,7 @@ gadep_status plan_launch(gadep_plan *p, uint32_t *spectra_dev, float *edep_trace
         if (p->count) dev::transport_kernel<false, true><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
         else dev::transport_kernel<false, false><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
     }
+    p->timer.after(KK_MEGA, s);
     e = cudaGetLastError();
     return e == cudaSuccess ? GADEP_OK : cuda_fail(e, "plan launch: kernel");
 }
@@ -965,6 +974,29 @@ extern "C" gadep_status gadep_plan_results(gadep_plan *p, uint32_t *spectra_host
     gadep::clear_error();
     if (!p) return fail(GADEP_E_INVAL, "gadep_plan_results: NULL plan");
     return gadep::plan_results(p, spectra_host, results, dfepe, dsigma, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" gadep_status gadep_plan_set_timing(gadep_plan *p, int32_t on)
+{
+    gadep::clear_error();
+    if (!p) return fail(GADEP_E_INVAL, "gadep_plan_set_timing: NULL plan");
+    p->timer.timing = on != 0;
+    return GADEP_OK;
+}
+
+extern "C" gadep_status gadep_plan_kernel_stats(gadep_plan *p, gadep_kernel_stats *out, int32_t reset)
+{
+    gadep::clear_error();
+    if (!p || !out) return fail(GADEP_E_INVAL, "gadep_plan_kernel_stats: NULL argument");
+    DeviceGuard g(p->device);
+    const cudaError_t e = p->timer.resolve();
+    std::memset(out, 0, sizeof(*out));
+    for (int k = 0; k < gadep::KK_N && k < 8; ++k) {
+        out->launches[k] = p->timer.launches[k];
+        out->ms[k] = p->timer.ms[k];
+    }
+    if (reset) p->timer.reset();
+    return e == cudaSuccess ? GADEP_OK : gadep::cuda_fail(e, "gadep_plan_kernel_stats: event");
 }
 
 extern "C" gadep_status gadep_plan_shape(const gadep_plan *p, int32_t *grid, int32_t *block, int32_t *smem_bytes)

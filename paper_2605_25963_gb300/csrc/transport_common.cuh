@@ -2,6 +2,7 @@
 // kernels (persistent megakernel and wavefront kernels).
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -205,14 +206,78 @@ __device__ __forceinline__ void mu_at(const float4 *tab, int n_grid, float lnE_m
 
 }  // namespace dev
 
+// Kernel launches of a plan, counted per kind, and optionally timed with CUDA
+// events recorded on the launching stream around every launch.
+enum KernelKind { KK_MEGA = 0, KK_SPAWN, KK_TRACE, KK_PHYSICS, KK_GEN, KK_CTRL, KK_INIT, KK_SORT, KK_N };
+struct KernelTimer {
+    bool timing = false;
+    unsigned long long launches[KK_N] = {};
+    double ms[KK_N] = {};
+    struct Pair { int kind; cudaEvent_t a, b; };
+    std::vector<Pair> pending;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t open = nullptr;
+    cudaEvent_t take()
+    {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        return e;
+    }
+    void before(cudaStream_t s)
+    {
+        if (!timing) return;
+        open = take();
+        if (open && cudaEventRecord(open, s) != cudaSuccess) { cudaGetLastError(); pool.push_back(open); open = nullptr; }
+    }
+    void after(int kind, cudaStream_t s)
+    {
+        ++launches[kind];
+        if (!timing || !open) return;
+        cudaEvent_t b = take();
+        if (b && cudaEventRecord(b, s) == cudaSuccess) pending.push_back(Pair{ kind, open, b });
+        else { cudaGetLastError(); pool.push_back(open); if (b) pool.push_back(b); }
+        open = nullptr;
+    }
+    // Wait for the recorded launches and add their durations.
+    cudaError_t resolve()
+    {
+        cudaError_t err = cudaSuccess;
+        for (const Pair &p : pending) {
+            float t = 0.0f;
+            cudaError_t e = cudaEventSynchronize(p.b);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, p.a, p.b);
+            if (e == cudaSuccess) ms[p.kind] += t;
+            else if (err == cudaSuccess) err = e;
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        pending.clear();
+        return err;
+    }
+    void reset()
+    {
+        for (int k = 0; k < KK_N; ++k) { launches[k] = 0; ms[k] = 0.0; }
+    }
+    void release()
+    {
+        resolve();
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+        pool.clear();
+    }
+};
+
 // Wavefront form of the transport (wavefront.cu): photon slots in device memory,
-// birth / trace / physics kernels per iteration.
+// spawn / sort / trace / physics / gen / ctrl kernels per iteration.
 struct WavefrontBuffers;
 constexpr int kWavefrontMaxInstances = 1024;   // block tallies live in shared memory
 gadep_status wavefront_create(int device, int slots, bool grad, WavefrontBuffers **out);
 void wavefront_destroy(WavefrontBuffers *w);
 gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P, bool grad, bool count,
-                           unsigned long long *counters, cudaStream_t s);
+                           unsigned long long *counters, KernelTimer *timer, cudaStream_t s);
 int wavefront_trace_grid(const WavefrontBuffers *w);
+// Whether the wavefront records can address the mesh (region and triangle ids
+// share one 32-bit word).
+bool wavefront_supports(int n_region, long long n_mesh_tri);
 
 }  // namespace gadep

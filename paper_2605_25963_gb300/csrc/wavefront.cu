@@ -1,20 +1,28 @@
 // wavefront.cu -- wavefront form of the photon transport (same physics, same
 // Philox streams and same tallies as the persistent megakernel in transport.cu).
 //
-// Photons live in S device-memory slots.  One iteration runs three kernels:
-//   birth    every slot on the dead list takes the next history from the work
-//            counter (histories born in the world whose first ray misses the
-//            scene box end here with nothing deposited) and joins the trace queue;
-//   trace    lean persistent traversal: warps take slots from the queue, lanes
-//            that finish a query take the next one as soon as too few lanes of
+// Photons live in device-memory slots.  One iteration runs five kernels on the
+// stream, with no host round trip between them:
+//   spawn    free slots take births from the pending ring (an index map: the
+//            i-th free slot gets the i-th pending history) and join the trace
+//            queue after the survivors of the previous iteration;
+//   sort     counting sort of the queue by (region, direction octant), from the
+//            key histogram that physics and spawn accumulate, so that a warp
+//            traverses one region's tree with rays of similar direction;
+//   trace    lean persistent traversal: warps claim chunks of the queue, lanes
+//            that finish a query take the next entry as soon as too few lanes of
 //            the warp are still traversing (dynamic fetch), so the warp is not
-//            held by its longest ray;
-//   physics  one thread per queued slot applies the segment: free flight,
+//            held by its longest ray; the hit is stored by queue position;
+//   physics  one thread per queued photon applies the segment: free flight,
 //            boundary crossing (nesting-tree rule), interaction or escape, and the
 //            end-of-history tally; survivors go to the next trace queue, finished
-//            slots to the next dead list.
+//            slots to the next free list (one global atomic per list, block and pass);
+//   gen      history ids in chunks: source point and direction of each id;
+//            histories born in the world whose first ray misses the scene box end
+//            here with nothing deposited, the others join the pending ring;
+//   ctrl     one thread: advances the counters and plans the next iteration.
 // The host issues iterations and reads the control block every few iterations
-// to stop when the work counter is exhausted and no photon is alive.
+// to stop once the history supply, the ring and the queue are all empty.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -31,40 +39,80 @@ namespace wf {
 
 using namespace gadep::dev;
 
-struct __align__(16) Ray {      // read by trace, written by birth and physics
-    float ox, oy, oz, t_cur;
-    float dx, dy, dz;
-    int last_tri;               // mesh triangle id to skip (-1 none)
-    int root;                   // tree of the photon's region
-    int pad[3];
+// Slot records of 32 bytes (one DRAM sector each).
+struct __align__(32) Ray {      // read by trace and physics, written by spawn and physics
+    float4 o;                   // origin, w = t_cur (distance already travelled from o)
+    float4 d;                   // direction, w = tag bits (last mesh triangle + 1) << 8 | region
 };
-struct __align__(16) Hit {      // written by trace
+struct __align__(32) Phot {
+    float4 f;                   // E, lam (mean free paths left), edep (active), dep_all
+    uint4 u;                    // Philox words used, history index within the instance,
+                                // instance | error bits << 16 | flags << 24, segments so far
+};
+struct __align__(16) Hit {      // by queue position, written by trace
     float t;
     int tri;                    // mesh triangle id, -1 = nothing ahead
-    int region;                 // region id of the triangle's solid
+    int region;                 // region of the triangle's solid
     int entering;               // 1 entering, 0 leaving, -2 traversal stack overflow
 };
-struct __align__(16) Phot {
-    float E, lam;
-    int region, steps;
-    float E0, edep, dep_all, esc;
+struct __align__(32) Sec {      // second annihilation photon, waiting for the first
+    float4 p;                   // position
+    float4 d;                   // direction, w = region bits
 };
-struct __align__(16) Rng {
-    uint32_t block, idx, c1, c2;
+
+constexpr int kKeysPerRegion = 8;   // sort key: region * 8 + direction octant
+constexpr int kMaxKeys = 2048;      // regions * kKeysPerRegion at most
+constexpr uint32_t kFlagSec = 1u;   // a second annihilation photon is waiting
+constexpr uint32_t kFlagEsc = 2u;   // esc[slot] holds energy this history let escape
+constexpr int kTagShift = 8;        // at most 256 regions
+constexpr int kMaxTriId = (1 << 23) - 2;
+
+__device__ __forceinline__ uint32_t ray_tag(int last_tri, int region)
+{
+    return ((uint32_t)(last_tri + 1) << kTagShift) | (uint32_t)region;
+}
+
+__device__ __forceinline__ uint32_t sort_key(int region, float px, float py, float pz, float dx, float dy, float dz)
+{
+    (void)px; (void)py; (void)pz;
+    return (uint32_t)region * kKeysPerRegion + (dx < 0.0f ? 1u : 0u) + (dy < 0.0f ? 2u : 0u) + (dz < 0.0f ? 4u : 0u);
+}
+
+// Adds key k to a shared-memory histogram, one atomic per distinct key of the warp.
+__device__ __forceinline__ void warp_hist_add(bool want, uint32_t k, unsigned int *h)
+{
+    const uint32_t peers = __match_any_sync(0xffffffffu, want ? k : 0xffffffffu);
+    if (want && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[k], (unsigned int)__popc(peers));
+}
+
+// Philox stream resumed from the count of words already used: word k of a
+// history is component k mod 4 of block k / 4 (the counter layout of the
+// megakernel's Stream, so both forms draw the same numbers).
+struct Words {
+    uint32_t w, c1, c2, c3;
     uint4 buf;
-};
-struct __align__(16) Hist {
-    unsigned long long g_hist;
-    int inst;
-    uint32_t herr;
-    int sec;                    // region of a waiting annihilation photon, -1 = none
-    uint32_t n_inter;           // interactions of this history so far
-    float sox, soy;
+    bool have;
+    __device__ __forceinline__ void init(uint32_t used, unsigned long long hid, uint32_t inst)
+    {
+        w = used; c1 = (uint32_t)hid; c2 = (uint32_t)(hid >> 32); c3 = inst; have = false;
+    }
+    __device__ __forceinline__ float u01(uint32_t k0, uint32_t k1)
+    {
+        if (!have) {
+            buf = philox4x32_10(make_uint4(w >> 2, c1, c2, c3), k0, k1);
+            have = true;
+        }
+        const uint32_t i = w & 3u;
+        const uint32_t x = i == 0 ? buf.x : (i == 1 ? buf.y : (i == 2 ? buf.z : buf.w));
+        ++w;
+        if ((w & 3u) == 0) have = false;
+        return __uint2float_rn(2u * (x >> 9) + 1u) * 5.9604644775390625e-8f;
+    }
 };
 
 // Per-block tallies in shared memory, one record per instance, flushed once per
 // launch into the block's tally copy: finished histories of many instances mix
-// in every kernel launch, so per-thread accumulators would flush constantly.
+// in every launch, so per-thread accumulators would flush constantly.
 struct STally {
     unsigned int hist, fep, zero, over, err, seg, inter, errbits;
     float dep, dep_all, esc, pad;
@@ -84,13 +132,12 @@ struct BlockTally {
         if (GRAD)
             for (int i = threadIdx.x; i < 8 * n_inst; i += blockDim.x) sc[i] = 0.0;
     }
-    __device__ void history(int inst, uint32_t segs, uint32_t inter, uint32_t herr, bool fep, float edep,
-                            float dep_all, float esc, float e_max, const float *score)
+    __device__ void history(int inst, uint32_t segs, uint32_t herr, bool fep, float edep, float dep_all, float esc,
+                            float e_max, const float *score)
     {
         STally &s = t[inst];
         atomicAdd(&s.hist, 1u);
         atomicAdd(&s.seg, segs);
-        if (inter) atomicAdd(&s.inter, inter);
         if (herr) {
             atomicAdd(&s.err, 1u);
             atomicOr(&s.errbits, herr);
@@ -108,15 +155,15 @@ struct BlockTally {
         if (edep == 0.0f) atomicAdd(&s.zero, 1u);
         else if (edep >= e_max) atomicAdd(&s.over, 1u);
         if (edep != 0.0f) atomicAdd(&s.dep, edep);
-        atomicAdd(&s.dep_all, dep_all);
-        atomicAdd(&s.esc, esc);
+        if (dep_all != 0.0f) atomicAdd(&s.dep_all, dep_all);
+        if (esc != 0.0f) atomicAdd(&s.esc, esc);
     }
     __device__ void flush(TallyDev *T)
     {
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const STally &s = t[i];
-            if (!s.hist && !s.seg) continue;
+            if (!s.hist && !s.seg && !s.inter) continue;
             TallyDev &d = T[i];
             if (s.hist) atomicAdd(&d.n_hist, (unsigned long long)s.hist);
             if (s.fep) atomicAdd(&d.n_fep, (unsigned long long)s.fep);
@@ -144,224 +191,407 @@ __host__ __device__ constexpr size_t block_tally_bytes(int n_inst)
 }
 
 struct Ctrl {
-    unsigned int q_count[2];     // trace queue sizes, by iteration parity
-    unsigned int dead_count[2];  // dead lists, by iteration parity
-    unsigned int trace_head;     // dynamic-fetch cursor of the trace kernel
-    unsigned int pad;
-    unsigned long long work;     // next global history index
+    // counters
+    unsigned int q_count[2];       // trace queue sizes, by iteration parity
+    unsigned int dead_count[2];    // free-slot lists, by iteration parity
+    unsigned int trace_head;       // chunk cursor of the trace kernel
+    unsigned int iter;
+    unsigned long long work;       // next history index handed to gen (may run past the total)
+    unsigned long long pend_add;   // births appended by the running gen launch
+    unsigned long long pend_head;  // births consumed so far
+    unsigned long long pend_tail;  // births produced so far
+    // plan of the next spawn and gen, written by ctrl only
+    unsigned int sp_n_dead, sp_filled, sp_q0, done;   // done: 1 finished, 2 iteration bound reached
+    unsigned long long sp_head;
+    unsigned long long gen_live;   // ring entries left once the next spawn has run
+    unsigned long long max_iter;
 };
 
 struct State {
     Ray *ray;
-    Hit *hit;
     Phot *phot;
-    Rng *rng;
-    Hist *hist;
-    float4 *sec;                 // secondary photon: (z, -direction)
-    float4 *score;               // GRAD only
+    Sec *sec;
+    float *esc;
+    float4 *score;                 // GRAD only
+    Hit *hit;                      // by queue position
     unsigned int *queue[2];
+    unsigned int *qkey[2];         // sort key of each queue entry
+    unsigned int *hist[2];         // key histogram of queue[parity]
+    unsigned int *fill;            // bucket cursors of the sort
+    unsigned int *qsort;           // the queue in key order: what trace and physics walk
     unsigned int *dead[2];
+    unsigned long long *pend;      // ring of global history indices waiting for a slot
+    unsigned long long pend_mask;  // ring size - 1 (a power of two)
+    unsigned long long gen_target; // ring fill at which gen stops claiming ids
     Ctrl *ctrl;
     int slots;
 };
 
-__device__ __forceinline__ float rng_u01(Rng &r, uint32_t c3, uint32_t k0, uint32_t k1)
+constexpr int kGenChunk = 2048;    // history ids per gen claim (8 per thread)
+constexpr int kTraceChunk = 64;    // queue entries per trace claim
+
+// Instance of global history index g (inst_end: inclusive prefix sums of the
+// history counts); `inst` is a guess tried first.
+__device__ __forceinline__ int find_inst(const Params &P, unsigned long long g, int inst)
 {
-    if (r.idx == 4) {
-        r.buf = philox4x32_10(make_uint4(r.block, r.c1, r.c2, c3), k0, k1);
-        ++r.block;
-        r.idx = 0;
+    if (g < P.inst_end[inst] && (inst == 0 || g >= P.inst_end[inst - 1])) return inst;
+    int lo = 0, hi = P.n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (g < P.inst_end[mid]) hi = mid; else lo = mid + 1;
     }
-    const uint32_t x = r.idx == 0 ? r.buf.x : (r.idx == 1 ? r.buf.y : (r.idx == 2 ? r.buf.z : r.buf.w));
-    ++r.idx;
-    return __uint2float_rn(2u * (x >> 9) + 1u) * 5.9604644775390625e-8f;
+    return lo;
 }
 
-// Warp-aggregated append of `slot` to list (count at *cnt).
-__device__ __forceinline__ void warp_append(bool want, unsigned int slot, unsigned int *list, unsigned int *cnt)
+// Source point and direction of a history (the megakernel's draw order).
+__device__ __forceinline__ void sample_birth(const InstDev &I, Words &r, uint32_t k0, uint32_t k1, float &ox,
+                                             float &oy, float &oz, float &dx, float &dy, float &dz)
 {
-    const unsigned mask = __ballot_sync(0xffffffffu, want);
-    if (!mask) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(mask) - 1;
-    unsigned int base = 0;
-    if (lane == leader) base = atomicAdd(cnt, (unsigned int)__popc(mask));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (want) list[base + __popc(mask & ((1u << lane) - 1u))] = slot;
+    ox = I.px; oy = I.py; oz = I.pz;
+    if (I.src_kind == GADEP_SRC_DISK) {
+        const float rr = I.radius * sqrtf(r.u01(k0, k1));
+        float sp, cp;
+        sincospif(2.0f * r.u01(k0, k1), &sp, &cp);
+        ox = fmaf(rr, cp, ox); oy = fmaf(rr, sp, oy);
+    } else if (I.src_kind == GADEP_SRC_PRISM) {
+        const int N = I.n_sides;
+        int kk = (int)((float)N * r.u01(k0, k1));
+        kk = min(kk, N - 1);
+        const float s1 = sqrtf(r.u01(k0, k1)), u3 = r.u01(k0, k1);
+        float sa, ca, sb, cb;
+        sincospif(2.0f * (float)kk / (float)N, &sa, &ca);
+        sincospif(2.0f * (float)((kk + 1) % N) / (float)N, &sb, &cb);
+        const float wa = s1 * (1.0f - u3), wb = s1 * u3;
+        ox += I.radius * (wa * ca + wb * cb);
+        oy += I.radius * (wa * sa + wb * sb);
+        oz = fmaf(I.height, r.u01(k0, k1), oz);
+    }
+    if (I.src_kind == GADEP_SRC_PENCIL) {
+        dx = I.dx; dy = I.dy; dz = I.dz;
+    } else {
+        const float c = 2.0f * r.u01(k0, k1) - 1.0f;
+        float sp, cp;
+        sincospif(2.0f * r.u01(k0, k1), &sp, &cp);
+        const float s = sqrtf(fmaxf(0.0f, 1.0f - c * c));
+        dx = s * cp; dy = s * sp; dz = c;
+    }
 }
 
-__global__ void init_kernel(State S)
+__global__ void init_kernel(State S, unsigned long long max_iter)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < S.slots) S.dead[0][i] = (unsigned int)i;
+    for (int k = i; k < kMaxKeys; k += gridDim.x * blockDim.x) {
+        S.hist[0][k] = 0u;
+        S.hist[1][k] = 0u;
+        S.fill[k] = 0u;
+    }
     if (i == 0) {
-        S.ctrl->q_count[0] = S.ctrl->q_count[1] = 0;
-        S.ctrl->dead_count[0] = (unsigned int)S.slots;
-        S.ctrl->dead_count[1] = 0;
-        S.ctrl->trace_head = 0;
-        S.ctrl->work = 0;
+        Ctrl &c = *S.ctrl;
+        c.q_count[0] = c.q_count[1] = 0;
+        c.dead_count[0] = (unsigned int)S.slots;
+        c.dead_count[1] = 0;
+        c.trace_head = 0;
+        c.iter = 0;
+        c.work = 0;
+        c.pend_add = c.pend_head = c.pend_tail = 0;
+        c.sp_n_dead = c.sp_filled = c.sp_q0 = c.done = 0;
+        c.sp_head = 0;
+        c.gen_live = 0;
+        c.max_iter = max_iter;
     }
 }
 
-// ---------------------------------------------------------------- birth
-template <bool GRAD>
-__global__ void __launch_bounds__(256) birth_kernel(const Params P, State S, int cur)
+// ---------------------------------------------------------------- ctrl
+// Close iteration `cur` (spawn, trace, physics and gen have run) and plan the next.
+__global__ void ctrl_kernel(State S, int cur, unsigned long long total)
+{
+    for (int k = threadIdx.x; k < kMaxKeys; k += blockDim.x) {
+        S.hist[cur][k] = 0u;        // the sort of iteration `cur` is done with it
+        S.fill[k] = 0u;
+    }
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    Ctrl &c = *S.ctrl;
+    if (c.done) return;
+    const int nxt = cur ^ 1;
+    c.pend_tail += c.pend_add;
+    c.pend_add = 0;
+    c.pend_head += c.sp_filled;
+    const unsigned long long work = c.work < total ? c.work : total;
+    c.work = work;
+    const unsigned int n_alive = c.q_count[nxt], n_dead = c.dead_count[nxt];
+    const unsigned long long avail = c.pend_tail - c.pend_head;
+    const unsigned int filled = (unsigned int)(avail < n_dead ? avail : n_dead);
+    c.sp_n_dead = n_dead;
+    c.sp_filled = filled;
+    c.sp_q0 = n_alive;
+    c.sp_head = c.pend_head;
+    c.q_count[nxt] = n_alive + filled;
+    c.q_count[cur] = 0;
+    c.dead_count[cur] = n_dead - filled;
+    c.trace_head = 0;
+    c.gen_live = avail - filled;
+    c.iter++;
+    if (work >= total && avail == 0 && n_alive == 0) c.done = 1;
+    else if (c.iter >= c.max_iter) c.done = 2;
+}
+
+// ---------------------------------------------------------------- gen
+// Blocks claim chunks of history ids while the ring holds fewer than gen_target
+// births; each block has at most one chunk in flight, so the fill stays below
+// gen_target + blocks x chunk, which the ring size covers.
+__global__ void __launch_bounds__(256) gen_kernel(const Params P, State S)
 {
     const uint32_t FULL = 0xffffffffu;
-    const int nxt = cur ^ 1;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        S.ctrl->q_count[nxt] = 0;
-        S.ctrl->dead_count[nxt] = 0;
-        S.ctrl->trace_head = 0;
-    }
-    extern __shared__ double4 smem_birth[];
+    Ctrl &c = *S.ctrl;
+    if (c.done) return;
+    extern __shared__ double4 smem_gen[];
+    __shared__ unsigned long long s_chunk, s_base;
+    __shared__ unsigned int s_cnt;
     BlockTally<false> bt;               // culled histories carry no score
-    bt.init(smem_birth, P.n_inst);
-    __syncthreads();
-    const unsigned int n_dead = S.ctrl->dead_count[cur];
+    bt.init(smem_gen, P.n_inst);
+    if (threadIdx.x == 0) s_cnt = 0;
+    const unsigned long long live0 = c.gen_live, tail0 = c.pend_tail;
     const int lane = threadIdx.x & 31;
     const uint32_t k0 = P.key0, k1 = P.key1;
     int inst = 0;
-    // warp-uniform loop over the dead list
-    const unsigned int stride = gridDim.x * blockDim.x;
-    for (unsigned int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n_dead; base += stride) {
-        const unsigned int j = base + lane;
-        const bool mine = j < n_dead;
-        const unsigned int slot = mine ? S.dead[cur][j] : 0u;
-        bool need = mine, placed = false;
-        // draw histories until the slot holds one that reaches the scene; the warp
-        // takes exactly as many history ids as it has lanes in need, so no id is lost
-        while (true) {
-            const uint32_t needm = __ballot_sync(FULL, need);
-            if (!needm) break;
-            unsigned long long b = 0;
-            if (lane == 0) b = atomicAdd(&S.ctrl->work, (unsigned long long)__popc(needm));
-            b = __shfl_sync(FULL, b, 0);
-            if (b >= P.total) break;
-            const uint32_t rank = __popc(needm & ((1u << lane) - 1u));
-            if (need && b + rank < P.total) {
-                const unsigned long long g = b + rank;
-                if (g >= P.inst_end[inst]) {
-                    // first instance whose end exceeds g (binary search over the prefix sums)
-                    int lo = inst + 1, hi = P.n_inst - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (g < P.inst_end[mid]) hi = mid; else lo = mid + 1;
-                    }
-                    inst = lo;
-                }
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned long long added = atomicAdd(&c.pend_add, 0ull);
+            s_chunk = live0 + added < S.gen_target ? atomicAdd(&c.work, (unsigned long long)kGenChunk) : ~0ull;
+        }
+        __syncthreads();
+        const unsigned long long chunk = s_chunk;
+        if (chunk >= P.total) break;
+#pragma unroll 1
+        for (int k = 0; k < kGenChunk / 256; ++k) {
+            const unsigned long long g = chunk + (unsigned long long)(k * 256 + threadIdx.x);
+            bool keep = false;
+            if (g < P.total) {
+                inst = find_inst(P, g, inst);
                 const InstDev &I = P.inst[inst];
                 const unsigned long long local = g - (inst ? P.inst_end[inst - 1] : 0ull);
-                const unsigned long long hid = I.hist_offset + local;
-                Rng r;
-                r.block = 0u; r.c1 = (uint32_t)hid; r.c2 = (uint32_t)(hid >> 32); r.idx = 4;
-                const uint32_t c3 = I.inst_id;
-                float ox = I.px, oy = I.py, oz = I.pz, dx, dy, dz;
-                if (I.src_kind == GADEP_SRC_DISK) {
-                    const float rr = I.radius * sqrtf(rng_u01(r, c3, k0, k1));
-                    float sp, cp;
-                    sincospif(2.0f * rng_u01(r, c3, k0, k1), &sp, &cp);
-                    ox = fmaf(rr, cp, ox); oy = fmaf(rr, sp, oy);
-                } else if (I.src_kind == GADEP_SRC_PRISM) {
-                    const int N = I.n_sides;
-                    int kk = (int)((float)N * rng_u01(r, c3, k0, k1));
-                    kk = min(kk, N - 1);
-                    const float s1 = sqrtf(rng_u01(r, c3, k0, k1)), u3 = rng_u01(r, c3, k0, k1);
-                    float sa, ca, sb, cb;
-                    sincospif(2.0f * (float)kk / (float)N, &sa, &ca);
-                    sincospif(2.0f * (float)((kk + 1) % N) / (float)N, &sb, &cb);
-                    const float wa = s1 * (1.0f - u3), wb = s1 * u3;
-                    ox += I.radius * (wa * ca + wb * cb);
-                    oy += I.radius * (wa * sa + wb * sb);
-                    oz = fmaf(I.height, rng_u01(r, c3, k0, k1), oz);
-                }
-                if (I.src_kind == GADEP_SRC_PENCIL) {
-                    dx = I.dx; dy = I.dy; dz = I.dz;
-                } else {
-                    const float c = 2.0f * rng_u01(r, c3, k0, k1) - 1.0f;
-                    float sp, cp;
-                    sincospif(2.0f * rng_u01(r, c3, k0, k1), &sp, &cp);
-                    const float s = sqrtf(fmaxf(0.0f, 1.0f - c * c));
-                    dx = s * cp; dy = s * sp; dz = c;
-                }
-                const int region = I.birth_region;
-                if (region == 0 && !ray_hits_box(P.root_lo, P.root_hi, ox, oy, oz, dx, dy, dz)) {
-                    bt.history(inst, 1u, 0u, 0u, false, 0.0f, 0.0f, I.E0, P.e_max, nullptr);
+                Words r;
+                r.init(0u, I.hist_offset + local, I.inst_id);
+                float ox, oy, oz, dx, dy, dz;
+                sample_birth(I, r, k0, k1, ox, oy, oz, dx, dy, dz);
+                if (I.birth_region == 0 && !ray_hits_box(P.root_lo, P.root_hi, ox, oy, oz, dx, dy, dz)) {
+                    bt.history(inst, 1u, 0u, false, 0.0f, 0.0f, I.E0, P.e_max, nullptr);
                     if (g < P.n_trace) P.edep_trace[g] = 0.0f;
                 } else {
-                    const float lam = -logf(rng_u01(r, c3, k0, k1));
-                    Ray ry;
-                    ry.ox = ox; ry.oy = oy; ry.oz = oz; ry.t_cur = 0.0f;
-                    ry.dx = dx; ry.dy = dy; ry.dz = dz; ry.last_tri = -1;
-                    ry.root = P.regions[region].w;
-                    ry.pad[0] = ry.pad[1] = ry.pad[2] = 0;
-                    S.ray[slot] = ry;
-                    Phot ph;
-                    ph.E = I.E0; ph.lam = lam; ph.region = region; ph.steps = 0;
-                    ph.E0 = I.E0; ph.edep = 0.0f; ph.dep_all = 0.0f; ph.esc = 0.0f;
-                    S.phot[slot] = ph;
-                    S.rng[slot] = r;
-                    Hist h;
-                    h.g_hist = g; h.inst = inst; h.herr = 0u; h.sec = -1; h.n_inter = 0u; h.sox = 0.0f; h.soy = 0.0f;
-                    S.hist[slot] = h;
-                    if (GRAD) S.score[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                    need = false;
-                    placed = true;
+                    keep = true;
                 }
             }
-            if (b + __popc(needm) >= P.total) break;
+            const uint32_t m = __ballot_sync(FULL, keep);
+            unsigned int off = 0;
+            if (lane == 0 && m) off = atomicAdd(&s_cnt, (unsigned int)__popc(m));
+            off = __shfl_sync(FULL, off, 0) + __popc(m & ((1u << lane) - 1u));
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_base = s_cnt ? atomicAdd(&c.pend_add, (unsigned long long)s_cnt) : 0ull;
+                s_cnt = 0;
+            }
+            __syncthreads();
+            if (keep) S.pend[(tail0 + s_base + off) & S.pend_mask] = g;
         }
-        warp_append(placed, slot, S.queue[cur], &S.ctrl->q_count[cur]);
     }
     bt.flush(block_tally(P));
+}
+
+// ---------------------------------------------------------------- spawn
+// Places history g into `slot` at queue position qpos; returns its sort key.
+template <bool GRAD>
+__device__ __forceinline__ uint32_t spawn_one(const Params &P, const State &S, int cur, unsigned int slot,
+                                              unsigned long long g, unsigned int qpos, uint32_t k0, uint32_t k1,
+                                              int &inst)
+{
+    inst = find_inst(P, g, inst);
+    const InstDev &I = P.inst[inst];
+    const unsigned long long local = g - (inst ? P.inst_end[inst - 1] : 0ull);
+    Words r;
+    r.init(0u, I.hist_offset + local, I.inst_id);
+    float ox, oy, oz, dx, dy, dz;
+    sample_birth(I, r, k0, k1, ox, oy, oz, dx, dy, dz);
+    const float lam = -logf(r.u01(k0, k1));
+    Ray ry;
+    ry.o = make_float4(ox, oy, oz, 0.0f);
+    ry.d = make_float4(dx, dy, dz, __uint_as_float(ray_tag(-1, I.birth_region)));
+    S.ray[slot] = ry;
+    Phot ph;
+    ph.f = make_float4(I.E0, lam, 0.0f, 0.0f);
+    ph.u = make_uint4(r.w, (uint32_t)local, (uint32_t)inst, 0u);
+    S.phot[slot] = ph;
+    if (GRAD) S.score[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    const uint32_t key = sort_key(I.birth_region, ox, oy, oz, dx, dy, dz);
+    S.queue[cur][qpos] = slot;
+    S.qkey[cur][qpos] = key;
+    return key;
+}
+
+template <bool GRAD>
+__global__ void __launch_bounds__(256) spawn_kernel(const Params P, State S, int cur)
+{
+    const Ctrl &c = *S.ctrl;
+    const unsigned int n_dead = c.sp_n_dead, filled = c.sp_filled, q0 = c.sp_q0;
+    if (n_dead == 0) return;
+    const unsigned long long head = c.sp_head;
+    const uint32_t k0 = P.key0, k1 = P.key1;
+    const int n_keys = P.n_region * kKeysPerRegion;
+    __shared__ unsigned int s_hist[kMaxKeys];
+    for (int k = threadIdx.x; k < n_keys; k += blockDim.x) s_hist[k] = 0u;
+    __syncthreads();
+    int inst = 0;
+    const unsigned int stride = gridDim.x * blockDim.x;
+    for (unsigned int base = blockIdx.x * blockDim.x; base < n_dead; base += stride) {   // warp-uniform
+        const unsigned int i = base + threadIdx.x;
+        bool born = false;
+        uint32_t key = 0;
+        if (i < n_dead) {
+            const unsigned int slot = S.dead[cur][i];
+            if (i >= filled) {
+                S.dead[cur ^ 1][i - filled] = slot;
+            } else {
+                key = spawn_one<GRAD>(P, S, cur, slot, S.pend[(head + i) & S.pend_mask], q0 + i, k0, k1, inst);
+                born = true;
+            }
+        }
+        warp_hist_add(born, key, s_hist);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_keys; k += blockDim.x)
+        if (s_hist[k]) atomicAdd(&S.hist[cur][k], s_hist[k]);
+}
+
+// ---------------------------------------------------------------- sort
+constexpr int kSortPerThread = 16;
+
+// Counting sort of queue[cur] into qsort: each block takes a contiguous range,
+// finds its keys' bucket starts from the exclusive prefix of the histogram,
+// reserves room in every bucket with one atomic per key and scatters.
+__global__ void __launch_bounds__(256) sort_kernel(State S, int cur, int n_keys)
+{
+    const uint32_t FULL = 0xffffffffu;
+    __shared__ unsigned int s_base[kMaxKeys], s_cnt[kMaxKeys], s_warp[8];
+    const unsigned int n = S.ctrl->q_count[cur];
+    const unsigned int begin = blockIdx.x * (256u * kSortPerThread);
+    if (begin >= n) return;
+    const unsigned int end = min(begin + 256u * kSortPerThread, n);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // exclusive prefix of the histogram: thread t owns keys kpt t .. kpt t + kpt - 1
+    constexpr int kpt = kMaxKeys / 256;
+    unsigned int loc[kpt], sum = 0;
+#pragma unroll
+    for (int q = 0; q < kpt; ++q) {
+        const int k = threadIdx.x * kpt + q;
+        loc[q] = k < n_keys ? S.hist[cur][k] : 0u;
+        sum += loc[q];
+    }
+    unsigned int inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int v = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    unsigned int pre = inc - sum;
+    for (int w = 0; w < warp; ++w) pre += s_warp[w];
+#pragma unroll
+    for (int q = 0; q < kpt; ++q) {
+        const int k = threadIdx.x * kpt + q;
+        s_base[k] = pre;
+        s_cnt[k] = 0u;
+        pre += loc[q];
+    }
+    __syncthreads();
+    for (unsigned int i = begin + threadIdx.x; i < end; i += 256u) atomicAdd(&s_cnt[S.qkey[cur][i]], 1u);
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_keys; k += 256)
+        if (s_cnt[k]) {
+            s_base[k] += atomicAdd(&S.fill[k], s_cnt[k]);
+            s_cnt[k] = 0u;
+        }
+    __syncthreads();
+    for (unsigned int b = begin; b < end; b += 256u) {   // warp-uniform
+        const unsigned int i = b + threadIdx.x;
+        const bool valid = i < end;
+        const uint32_t key = valid ? S.qkey[cur][i] : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(FULL, key);
+        const int leader = __ffs(peers) - 1;
+        unsigned int off = 0;
+        if (valid && lane == leader) off = atomicAdd(&s_cnt[key], (unsigned int)__popc(peers));
+        off = __shfl_sync(FULL, off, leader) + __popc(peers & ((1u << lane) - 1u));
+        if (valid) S.qsort[s_base[key] + off] = S.queue[cur][i];
+    }
 }
 
 // ---------------------------------------------------------------- trace
 constexpr int kFetchThreshold = 20;   // refill lanes when fewer are still traversing (8, 12, 20 measured)
 
 template <bool COUNT>
-__global__ void __launch_bounds__(256) trace_kernel(const float4 *__restrict__ nodes,
-                                                    const float4 *__restrict__ tris, State S, int cur,
-                                                    unsigned long long *counters)
+__global__ void __launch_bounds__(256, 5) trace_kernel(const float4 *__restrict__ nodes,
+                                                    const float4 *__restrict__ tris,
+                                                    const int4 *__restrict__ regions, int n_region, State S,
+                                                    int cur, unsigned long long *counters)
 {
     const uint32_t FULL = 0xffffffffu;
+    __shared__ int s_root[256];
+    for (int i = threadIdx.x; i < n_region; i += blockDim.x) s_root[i] = regions[i].w;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const unsigned int n = S.ctrl->q_count[cur];
-    const unsigned int *queue = S.queue[cur];
+    const unsigned int *queue = S.qsort;
     bool has = false;
-    unsigned int slot = 0;
+    unsigned int qidx = 0;
     float ox = 0, oy = 0, oz = 0, t_min = 0, ix = 0, iy = 0, iz = 0, oix = 0, oiy = 0, oiz = 0, t_best = 0;
     int exclude = -1, node = kSentinel, leaf = 0, sp = 0, best = -1;
     bool ent = false;
     Shear sh{ 0, 1, 2, 0.0f, 0.0f, 1.0f };
     int stack[kStack];
     uint32_t nn = 0, nt = 0, err = 0;
-    bool drained = false;
+    // warp-uniform private range [wb, we) of the queue, refilled a chunk at a time
+    unsigned int wb = 0, we = 0;
+    bool global_done = false, drained = false;
     while (true) {
         // ---- dynamic fetch: lanes without a ray take the next queue entries ----
         const uint32_t need = __ballot_sync(FULL, !has);
         if (need && !drained) {
-            unsigned int base = 0;
-            if (lane == 0) base = atomicAdd(&S.ctrl->trace_head, (unsigned int)__popc(need));
-            base = __shfl_sync(FULL, base, 0);
-            if (base >= n) drained = true;
-            const unsigned int idx = base + __popc(need & ((1u << lane) - 1u));
-            if (!has && idx < n) {
-                slot = queue[idx];
-                const Ray r = S.ray[slot];
-                ox = r.ox; oy = r.oy; oz = r.oz; t_min = r.t_cur;
-                exclude = r.last_tri;
-                sh = make_shear(r.dx, r.dy, r.dz);
-                ix = 1.0f / (fabsf(r.dx) > 1e-30f ? r.dx : copysignf(1e-30f, r.dx));
-                iy = 1.0f / (fabsf(r.dy) > 1e-30f ? r.dy : copysignf(1e-30f, r.dy));
-                iz = 1.0f / (fabsf(r.dz) > 1e-30f ? r.dz : copysignf(1e-30f, r.dz));
+            const unsigned int k = __popc(need);
+            const unsigned int avail = we - wb;
+            unsigned int nb = 0, ne = 0;
+            if (avail < k && !global_done) {
+                if (lane == 0) nb = atomicAdd(&S.ctrl->trace_head, (unsigned int)kTraceChunk);
+                nb = __shfl_sync(FULL, nb, 0);
+                if (nb >= n) { global_done = true; nb = ne = n; }
+                else ne = min(nb + (unsigned int)kTraceChunk, n);
+            }
+            const unsigned int rank = __popc(need & ((1u << lane) - 1u));
+            unsigned int idx = 0xffffffffu;
+            if (rank < avail) idx = wb + rank;
+            else if (nb + (rank - avail) < ne) idx = nb + (rank - avail);
+            if (avail >= k) wb += k;
+            else if (ne > nb) { wb = min(nb + (k - avail), ne); we = ne; }
+            else wb = we;
+            drained = global_done && wb >= we;
+            if (!has && idx != 0xffffffffu) {
+                qidx = idx;
+                const Ray r = S.ray[queue[idx]];
+                const uint32_t tag = __float_as_uint(r.d.w);
+                ox = r.o.x; oy = r.o.y; oz = r.o.z; t_min = r.o.w;
+                exclude = (int)(tag >> kTagShift) - 1;
+                sh = make_shear(r.d.x, r.d.y, r.d.z);
+                ix = 1.0f / (fabsf(r.d.x) > 1e-30f ? r.d.x : copysignf(1e-30f, r.d.x));
+                iy = 1.0f / (fabsf(r.d.y) > 1e-30f ? r.d.y : copysignf(1e-30f, r.d.y));
+                iz = 1.0f / (fabsf(r.d.z) > 1e-30f ? r.d.z : copysignf(1e-30f, r.d.z));
                 oix = ox * ix; oiy = oy * iy; oiz = oz * iz;
                 t_best = INFINITY;
                 best = -1;
                 ent = false;
                 stack[0] = kSentinel;
                 sp = 0;
-                node = r.root < 0 ? kSentinel : r.root;
+                const int root = s_root[tag & 255u];
+                node = root < 0 ? kSentinel : root;
                 leaf = 0;
                 has = true;
             }
@@ -413,7 +643,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const float4 *__restrict__ n
                 h.tri = best >= 0 ? __float_as_int(__ldg(&tris[3 * best + 1].w)) : -1;
                 h.region = best >= 0 ? __float_as_int(__ldg(&tris[3 * best].w)) : 0;
                 h.entering = best >= 0 ? (ent ? 1 : 0) : ((err & ERR_STACK) ? -2 : 0);
-                S.hit[slot] = h;
+                S.hit[qidx] = h;
                 err = 0;
                 has = false;
             }
@@ -435,54 +665,69 @@ __global__ void __launch_bounds__(256) physics_kernel(const Params P, State S, i
     const int nxt = cur ^ 1;
     // shared: region table (material slot, flags, parent, root), then block tallies
     extern __shared__ int4 s_reg[];
+    __shared__ unsigned int s_cnt[2], s_base[2];
     for (int i = threadIdx.x; i < P.n_region; i += blockDim.x) s_reg[i] = P.regions[i];
     BlockTally<GRAD> bt;
     bt.init(s_reg + P.n_region, P.n_inst);
+    // key histogram of the next queue, after the block tallies
+    unsigned int *s_hist = reinterpret_cast<unsigned int *>(
+        reinterpret_cast<char *>(s_reg + P.n_region) + block_tally_bytes<GRAD>(P.n_inst));
+    const int n_keys = P.n_region * kKeysPerRegion;
+    for (int k = threadIdx.x; k < n_keys; k += blockDim.x) s_hist[k] = 0u;
+    if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     const unsigned int n = S.ctrl->q_count[cur];
     const int lane = threadIdx.x & 31;
     const uint32_t k0 = P.key0, k1 = P.key1;
     TravStats ts{ 0u, 0u, 0u };
+    uint32_t inter_acc = 0;             // interactions of instance inter_inst not yet tallied
+    int inter_inst = 0;
     const unsigned int stride = gridDim.x * blockDim.x;
-    for (unsigned int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
-        const unsigned int j = base + lane;
+    for (unsigned int base = blockIdx.x * blockDim.x; base < n; base += stride) {   // block-uniform
+        const unsigned int j = base + threadIdx.x;
         const bool mine = j < n;
-        const unsigned int slot = mine ? S.queue[cur][j] : 0u;
+        const unsigned int slot = mine ? S.qsort[j] : 0u;
         bool alive_slot = false, finished = false;
+        uint32_t key = 0;
         int inst = 0;
-        float edep_out = 0.0f, E0_out = 0.0f;
-        unsigned long long g_hist = 0;
+        float edep_out = 0.0f;
         uint32_t herr_out = 0;
         if (mine) {
+            const Hit ht = S.hit[j];
             Ray ry = S.ray[slot];
-            Hit ht = S.hit[slot];
             Phot ph = S.phot[slot];
-            Hist hs = S.hist[slot];
-            inst = hs.inst;
-            g_hist = hs.g_hist;
-            uint32_t herr = hs.herr;
-            float4 sc4 = GRAD ? S.score[slot] : make_float4(0, 0, 0, 0);
+            float E = ph.f.x, lam = ph.f.y, edep = ph.f.z, dep_all = ph.f.w;
+            const uint32_t local = ph.u.y;
+            inst = (int)(ph.u.z & 0xffffu);
+            uint32_t herr = (ph.u.z >> 16) & 0xffu, flags = ph.u.z >> 24, steps = ph.u.w;
+            const uint32_t tag = __float_as_uint(ry.d.w);
+            int region = (int)(tag & 255u);
+            int last_tri = (int)(tag >> kTagShift) - 1;
+            const float4 sc4 = GRAD ? S.score[slot] : make_float4(0, 0, 0, 0);
             float score[4] = { sc4.x, sc4.y, sc4.z, sc4.w };
-            bool rng_loaded = false;
-            Rng r;
             const InstDev &I = P.inst[inst];
-            const uint32_t c3 = I.inst_id;
-            bool ray_dirty = false;
+            Words r;
+            r.init(ph.u.x, I.hist_offset + local, I.inst_id);
+            float esc_now = 0.0f;       // energy escaping in this segment
+            if (inst != inter_inst) {
+                if (inter_acc) atomicAdd(&bt.t[inter_inst].inter, inter_acc);
+                inter_acc = 0;
+                inter_inst = inst;
+            }
             if (ht.entering == -2) herr |= ERR_STACK;
-            if (++ph.steps > P.step_cap) herr |= ERR_STEPCAP;
+            if (++steps > (uint32_t)P.step_cap) herr |= ERR_STEPCAP;
             if (herr) {
                 finished = true;
             } else {
-                int region = ph.region;
-                const int4 R = s_reg[region];
-                const int group = (R.y >> 1) - 1;
                 float t_hit = ht.t;
                 int hit_tri = ht.tri, hit_region = ht.region;
                 bool entering = ht.entering == 1;
                 if (hit_tri < 0 && region != 0) {
-                    // not inside the region it carries: relocate through every triangle
-                    const int k = traverse<COUNT>(P.nodes, P.tris, P.root_all, ry.ox, ry.oy, ry.oz, ry.dx, ry.dy,
-                                                  ry.dz, ry.t_cur, ry.last_tri, t_hit, entering, herr, ts);
+                    // Inside a solid every ray meets its boundary, so the photon sits a
+                    // rounding error past it: relocate by the nearest surface of the
+                    // whole mesh; with none ahead it is outside every solid.
+                    const int k = traverse<COUNT>(P.nodes, P.tris, P.root_all, ry.o.x, ry.o.y, ry.o.z, ry.d.x,
+                                                  ry.d.y, ry.d.z, ry.o.w, last_tri, t_hit, entering, herr, ts);
                     if (COUNT) ts.relocated++;
                     if (k < 0) {
                         region = 0;
@@ -491,27 +736,27 @@ __global__ void __launch_bounds__(256) physics_kernel(const Params P, State S, i
                         hit_region = __float_as_int(__ldg(&P.tris[3 * k].w));
                     }
                 }
-                const int hit = hit_tri;
+                // region record: material slot, active | (group + 1) << 1, parent, tree root
+                const int4 R = s_reg[region];
+                const int group = (R.y >> 1) - 1;
                 float pe = 0.0f, co = 0.0f, pa = 0.0f;
-                if (R.x >= 0) mu_at(P.xs + (size_t)R.x * P.n_grid, P.n_grid, P.lnE_min, P.inv_dlnE, ph.E, pe, co, pa);
+                if (R.x >= 0) mu_at(P.xs + (size_t)R.x * P.n_grid, P.n_grid, P.lnE_min, P.inv_dlnE, E, pe, co, pa);
                 const float mu_unit = pe + co + pa;
                 const float scl = group >= 0 ? I.scale[group] : 1.0f;
                 const float mu = mu_unit * scl;
-                const float d_int = mu > 0.0f ? ph.lam / mu : INFINITY;
+                const float d_int = mu > 0.0f ? lam / mu : INFINITY;
                 bool photon_done = false;
                 if (herr) {
                     finished = true;
-                } else if (d_int < t_hit - ry.t_cur) {
+                } else if (d_int < t_hit - ry.o.w) {
                     // ---- interaction ----
-                    hs.n_inter++;
-                    r = S.rng[slot];
-                    rng_loaded = true;
+                    ++inter_acc;
                     if (GRAD && group >= 0 && group < 4) score[group] += 1.0f / scl - mu_unit * d_int;
-                    const float tt = ry.t_cur + d_int;
-                    const float px = fmaf(tt, ry.dx, ry.ox), py = fmaf(tt, ry.dy, ry.oy), pz = fmaf(tt, ry.dz, ry.oz);
-                    const float u = rng_u01(r, c3, k0, k1) * mu_unit;
+                    const float tt = ry.o.w + d_int;
+                    const float px = fmaf(tt, ry.d.x, ry.o.x), py = fmaf(tt, ry.d.y, ry.o.y),
+                                pz = fmaf(tt, ry.d.z, ry.o.z);
+                    const float u = r.u01(k0, k1) * mu_unit;
                     float dep;
-                    float E = ph.E;
                     if (u < pe) {
                         dep = E; E = 0.0f; photon_done = true;
                     } else if (u < pe + co || pa == 0.0f) {
@@ -521,8 +766,7 @@ __global__ void __launch_bounds__(256) physics_kernel(const Params P, State S, i
                         float x = 1.0f;
                         bool ok = false;
                         for (int trial = 0; trial < 1000; ++trial) {
-                            const float r1 = rng_u01(r, c3, k0, k1), r2 = rng_u01(r, c3, k0, k1),
-                                        r3 = rng_u01(r, c3, k0, k1);
+                            const float r1 = r.u01(k0, k1), r2 = r.u01(k0, k1), r3 = r.u01(k0, k1);
                             if (r1 <= br) {
                                 x = 1.0f + 2.0f * k * r2;
                                 if (r3 <= 4.0f * (1.0f / x - 1.0f / (x * x))) { ok = true; break; }
@@ -539,106 +783,131 @@ __global__ void __launch_bounds__(256) physics_kernel(const Params P, State S, i
                         } else {
                             const float c = 1.0f - (x - 1.0f) / k;
                             float sp, cp;
-                            sincospif(2.0f * rng_u01(r, c3, k0, k1), &sp, &cp);
+                            sincospif(2.0f * r.u01(k0, k1), &sp, &cp);
                             const float Ep = E / x;
                             dep = E - Ep;
-                            rotate(ry.dx, ry.dy, ry.dz, c, sp, cp);
+                            rotate(ry.d.x, ry.d.y, ry.d.z, c, sp, cp);
                             E = Ep;
                             if (E < P.e_cut) { dep += E; E = 0.0f; photon_done = true; }
                         }
                     } else {
                         dep = E - kTwoMeC2;
-                        float nx, ny, nz;
-                        const float c = 2.0f * rng_u01(r, c3, k0, k1) - 1.0f;
+                        const float c = 2.0f * r.u01(k0, k1) - 1.0f;
                         float sp, cp;
-                        sincospif(2.0f * rng_u01(r, c3, k0, k1), &sp, &cp);
+                        sincospif(2.0f * r.u01(k0, k1), &sp, &cp);
                         const float s = sqrtf(fmaxf(0.0f, 1.0f - c * c));
-                        nx = s * cp; ny = s * sp; nz = c;
+                        const float nx = s * cp, ny = s * sp, nz = c;
                         E = kMeC2;
-                        ry.dx = nx; ry.dy = ny; ry.dz = nz;
-                        hs.sec = region;
-                        hs.sox = px; hs.soy = py;
-                        S.sec[slot] = make_float4(pz, -nx, -ny, -nz);
+                        ry.d.x = nx; ry.d.y = ny; ry.d.z = nz;
+                        flags |= kFlagSec;
+                        Sec sc;
+                        sc.p = make_float4(px, py, pz, 0.0f);
+                        sc.d = make_float4(-nx, -ny, -nz, __int_as_float(region));
+                        S.sec[slot] = sc;
                     }
-                    if (R.y & 1) ph.edep += dep;
-                    ph.dep_all += dep;
-                    ph.E = E;
-                    ry.ox = px; ry.oy = py; ry.oz = pz;
-                    ry.t_cur = 0.0f; ry.last_tri = -1;
-                    ray_dirty = true;
+                    if (R.y & 1) edep += dep;
+                    dep_all += dep;
+                    ry.o = make_float4(px, py, pz, 0.0f);
+                    last_tri = -1;
                     if (herr) finished = true;
-                    else if (!photon_done) ph.lam = -logf(rng_u01(r, c3, k0, k1));
-                } else if (hit < 0) {
+                    else if (!photon_done) lam = -logf(r.u01(k0, k1));
+                } else if (hit_tri < 0) {
                     if (region != 0) herr |= ERR_LOST;
-                    ph.esc += ph.E;
-                    ph.E = 0.0f;
+                    esc_now = E;
+                    E = 0.0f;
                     photon_done = true;
                     if (herr) finished = true;
                 } else {
                     // ---- boundary crossing ----
-                    const float len = t_hit - ry.t_cur;
-                    ph.lam -= mu * len;
+                    const float len = t_hit - ry.o.w;
+                    lam -= mu * len;
                     if (GRAD && group >= 0 && group < 4) score[group] -= mu_unit * len;
-                    ry.t_cur = t_hit;
-                    ry.last_tri = hit_tri;
+                    ry.o.w = t_hit;
+                    last_tri = hit_tri;
                     region = entering ? hit_region : s_reg[hit_region].z;
-                    ry.root = s_reg[region].w;
-                    ph.region = region;
-                    ray_dirty = true;
+                }
+                if (esc_now != 0.0f) {
+                    // escaped energy of this history so far (at most two photons escape)
+                    if (flags & kFlagEsc) esc_now += S.esc[slot];
+                    flags |= kFlagEsc;
+                    if (!finished && (flags & kFlagSec)) S.esc[slot] = esc_now;
                 }
                 if (photon_done && !finished) {
-                    if (hs.sec >= 0) {
-                        if (!rng_loaded) { r = S.rng[slot]; rng_loaded = true; }
-                        const float4 s4 = S.sec[slot];
-                        const int sreg = hs.sec;
-                        hs.sec = -1;
-                        ry.ox = hs.sox; ry.oy = hs.soy; ry.oz = s4.x;
-                        ry.dx = s4.y; ry.dy = s4.z; ry.dz = s4.w;
-                        ry.t_cur = 0.0f; ry.last_tri = -1;
-                        ph.E = kMeC2;
-                        ph.region = sreg;
-                        ry.root = s_reg[sreg].w;
-                        ph.lam = -logf(rng_u01(r, c3, k0, k1));
-                        ray_dirty = true;
+                    if (flags & kFlagSec) {
+                        const Sec sc = S.sec[slot];
+                        flags &= ~kFlagSec;
+                        region = __float_as_int(sc.d.w);
+                        ry.o = make_float4(sc.p.x, sc.p.y, sc.p.z, 0.0f);
+                        ry.d.x = sc.d.x; ry.d.y = sc.d.y; ry.d.z = sc.d.z;
+                        last_tri = -1;
+                        E = kMeC2;
+                        lam = -logf(r.u01(k0, k1));
                     } else {
                         finished = true;
                     }
                 }
-                if (!finished && !(isfinite(ry.dx) && isfinite(ph.E) && isfinite(ph.lam))) {
+                if (!finished && !(isfinite(ry.d.x) && isfinite(E) && isfinite(lam))) {
                     herr |= ERR_NONFINITE;
                     finished = true;
                 }
             }
-            hs.herr = herr;
             herr_out = herr;
-            edep_out = ph.edep;
-            E0_out = ph.E0;
+            edep_out = edep;
             if (!finished) {
-                if (ray_dirty) S.ray[slot] = ry;
+                ry.d.w = __uint_as_float(ray_tag(last_tri, region));
+                S.ray[slot] = ry;
+                ph.f = make_float4(E, lam, edep, dep_all);
+                ph.u = make_uint4(r.w, local, (uint32_t)inst | (herr << 16) | (flags << 24), steps);
                 S.phot[slot] = ph;
-                if (rng_loaded) S.rng[slot] = r;
-                S.hist[slot] = hs;
                 if (GRAD) S.score[slot] = make_float4(score[0], score[1], score[2], score[3]);
+                key = sort_key(region, fmaf(ry.o.w, ry.d.x, ry.o.x), fmaf(ry.o.w, ry.d.y, ry.o.y),
+                               fmaf(ry.o.w, ry.d.z, ry.o.z), ry.d.x, ry.d.y, ry.d.z);
                 alive_slot = true;
             } else {
-                const bool fep = !herr && (E0_out - edep_out) <= P.fep_delta;
-                bt.history(inst, (uint32_t)ph.steps, hs.n_inter, herr, fep, edep_out, ph.dep_all, ph.esc, P.e_max,
-                           score);
-                if (g_hist < P.n_trace) P.edep_trace[g_hist] = herr ? -1.0f : edep_out;
+                float esc = 0.0f;
+                if (flags & kFlagEsc) esc = esc_now != 0.0f ? esc_now : S.esc[slot];
+                const bool fep = !herr && (I.E0 - edep) <= P.fep_delta;
+                bt.history(inst, steps, herr, fep, edep, dep_all, esc, P.e_max, score);
+                const unsigned long long g = (inst ? P.inst_end[inst - 1] : 0ull) + local;
+                if (g < P.n_trace) P.edep_trace[g] = herr ? -1.0f : edep;
             }
         }
-        // ---- warp-converged: spectrum atomics, queue / dead-list appends ----
+        // ---- spectrum atomics (warp-aggregated per bin) ----
         const bool binned = finished && herr_out == 0u && edep_out > 0.0f && edep_out < P.e_max;
         int bin = 0;
         if (binned) bin = min((int)(edep_out * P.bin_scale), P.n_bins - 1);
-        const uint32_t key = binned ? (uint32_t)(inst * P.n_bins + bin) : 0xffffffffu;
-        const uint32_t peers = __match_any_sync(FULL, key);
+        const uint32_t bkey = binned ? (uint32_t)(inst * P.n_bins + bin) : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(FULL, bkey);
         if (binned && lane == __ffs(peers) - 1)
             atomicAdd(&P.spectra[(size_t)inst * P.n_bins + bin], (uint32_t)__popc(peers));
-        warp_append(alive_slot, slot, S.queue[nxt], &S.ctrl->q_count[nxt]);
-        warp_append(finished, slot, S.dead[nxt], &S.ctrl->dead_count[nxt]);
+        // ---- queue / free-list appends: one global atomic per list, block and pass ----
+        const uint32_t ma = __ballot_sync(FULL, alive_slot), mf = __ballot_sync(FULL, finished);
+        unsigned int oa = 0, of = 0;
+        if (lane == 0) {
+            if (ma) oa = atomicAdd(&s_cnt[0], (unsigned int)__popc(ma));
+            if (mf) of = atomicAdd(&s_cnt[1], (unsigned int)__popc(mf));
+        }
+        const uint32_t below = (1u << lane) - 1u;
+        oa = __shfl_sync(FULL, oa, 0) + __popc(ma & below);
+        of = __shfl_sync(FULL, of, 0) + __popc(mf & below);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_base[0] = s_cnt[0] ? atomicAdd(&S.ctrl->q_count[nxt], s_cnt[0]) : 0u;
+            s_base[1] = s_cnt[1] ? atomicAdd(&S.ctrl->dead_count[nxt], s_cnt[1]) : 0u;
+            s_cnt[0] = s_cnt[1] = 0;
+        }
+        __syncthreads();
+        if (alive_slot) {
+            S.queue[nxt][s_base[0] + oa] = slot;
+            S.qkey[nxt][s_base[0] + oa] = key;
+        }
+        if (finished) S.dead[nxt][s_base[1] + of] = slot;
+        warp_hist_add(alive_slot, key, s_hist);
     }
-    bt.flush(block_tally(P));
+    if (inter_acc) atomicAdd(&bt.t[inter_inst].inter, inter_acc);
+    bt.flush(block_tally(P));     // starts with a barrier
+    for (int k = threadIdx.x; k < n_keys; k += blockDim.x)
+        if (s_hist[k]) atomicAdd(&S.hist[nxt][k], s_hist[k]);
     if (COUNT) {
         if (ts.nodes) atomicAdd(&counters[0], (unsigned long long)ts.nodes);
         if (ts.tris) atomicAdd(&counters[1], (unsigned long long)ts.tris);
@@ -659,6 +928,12 @@ struct WavefrontBuffers {
 
 int wavefront_trace_grid(const WavefrontBuffers *w) { return w ? w->trace_grid : 0; }
 
+bool wavefront_supports(int n_region, long long n_mesh_tri)
+{
+    return n_region >= 1 && n_region <= 256 && n_region * wf::kKeysPerRegion <= wf::kMaxKeys &&
+           n_mesh_tri <= wf::kMaxTriId;
+}
+
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 gadep_status wavefront_create(int device, int slots, bool grad, WavefrontBuffers **out)
@@ -667,20 +942,35 @@ gadep_status wavefront_create(int device, int slots, bool grad, WavefrontBuffers
     if (slots < 1024 || slots > (1 << 24)) return fail(GADEP_E_INVAL, "wavefront: slots must be in [1024, 2^24]");
     WavefrontBuffers *w = new (std::nothrow) WavefrontBuffers();
     if (!w) return fail(GADEP_E_NOMEM, "wavefront: out of host memory");
+    int n_sm = 0, bps = 0;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (void *)wf::trace_kernel<false>, 256, 0);
+    w->trace_grid = n_sm * std::max(bps, 1);
+    w->work_grid = n_sm * 8;
+    // ring of pending births: gen stops claiming once it holds `slots` (the most a
+    // spawn can take); every gen block may complete one more chunk after that
+    const unsigned long long target = (unsigned long long)slots;
+    const unsigned long long need = 2 * target + (unsigned long long)w->work_grid * wf::kGenChunk;
+    unsigned long long ring = 1;
+    while (ring < need) ring <<= 1;
     const size_t n = (size_t)slots;
     size_t off = 0;
     size_t o_ray = off; off = align_up(off + n * sizeof(wf::Ray));
-    size_t o_hit = off; off = align_up(off + n * sizeof(wf::Hit));
     size_t o_phot = off; off = align_up(off + n * sizeof(wf::Phot));
-    size_t o_rng = off; off = align_up(off + n * sizeof(wf::Rng));
-    size_t o_hist = off; off = align_up(off + n * sizeof(wf::Hist));
-    size_t o_sec = off; off = align_up(off + n * sizeof(float4));
+    size_t o_sec = off; off = align_up(off + n * sizeof(wf::Sec));
+    size_t o_esc = off; off = align_up(off + n * sizeof(float));
     size_t o_score = off; off = align_up(off + n * sizeof(float4));   // always: buffers serve both forms
     (void)grad;
+    size_t o_hit = off; off = align_up(off + n * sizeof(wf::Hit));
     size_t o_q0 = off; off = align_up(off + n * 4);
     size_t o_q1 = off; off = align_up(off + n * 4);
+    size_t o_k0 = off; off = align_up(off + n * 4);
+    size_t o_k1 = off; off = align_up(off + n * 4);
+    size_t o_qs = off; off = align_up(off + n * 4);
+    size_t o_h = off; off = align_up(off + 3 * wf::kMaxKeys * 4);
     size_t o_d0 = off; off = align_up(off + n * 4);
     size_t o_d1 = off; off = align_up(off + n * 4);
+    size_t o_pend = off; off = align_up(off + ring * sizeof(unsigned long long));
     size_t o_ctrl = off; off = align_up(off + sizeof(wf::Ctrl));
     cudaError_t e = cudaMalloc(&w->block, off);
     if (e != cudaSuccess) {
@@ -696,23 +986,26 @@ gadep_status wavefront_create(int device, int slots, bool grad, WavefrontBuffers
     }
     char *b = (char *)w->block;
     w->S.ray = (wf::Ray *)(b + o_ray);
-    w->S.hit = (wf::Hit *)(b + o_hit);
     w->S.phot = (wf::Phot *)(b + o_phot);
-    w->S.rng = (wf::Rng *)(b + o_rng);
-    w->S.hist = (wf::Hist *)(b + o_hist);
-    w->S.sec = (float4 *)(b + o_sec);
+    w->S.sec = (wf::Sec *)(b + o_sec);
+    w->S.esc = (float *)(b + o_esc);
     w->S.score = (float4 *)(b + o_score);
+    w->S.hit = (wf::Hit *)(b + o_hit);
     w->S.queue[0] = (unsigned int *)(b + o_q0);
     w->S.queue[1] = (unsigned int *)(b + o_q1);
+    w->S.qkey[0] = (unsigned int *)(b + o_k0);
+    w->S.qkey[1] = (unsigned int *)(b + o_k1);
+    w->S.qsort = (unsigned int *)(b + o_qs);
+    w->S.hist[0] = (unsigned int *)(b + o_h);
+    w->S.hist[1] = w->S.hist[0] + wf::kMaxKeys;
+    w->S.fill = w->S.hist[1] + wf::kMaxKeys;
     w->S.dead[0] = (unsigned int *)(b + o_d0);
     w->S.dead[1] = (unsigned int *)(b + o_d1);
+    w->S.pend = (unsigned long long *)(b + o_pend);
+    w->S.pend_mask = ring - 1;
+    w->S.gen_target = target;
     w->S.ctrl = (wf::Ctrl *)(b + o_ctrl);
     w->S.slots = slots;
-    int n_sm = 0, bps = 0;
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (void *)wf::trace_kernel<false>, 256, 0);
-    w->trace_grid = n_sm * std::max(bps, 1);
-    w->work_grid = n_sm * 8;
     *out = w;
     return GADEP_OK;
 }
@@ -727,41 +1020,62 @@ void wavefront_destroy(WavefrontBuffers *w)
 
 // Run every history of the plan's Params through the wavefront kernels on `s`.
 gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P, bool grad, bool count,
-                           unsigned long long *counters, cudaStream_t s)
+                           unsigned long long *counters, KernelTimer *timer, cudaStream_t s)
 {
     wf::State S = w->S;
     if (P.n_inst > kWavefrontMaxInstances)
         return fail(GADEP_E_INVAL, "wavefront: at most %d instances per run", kWavefrontMaxInstances);
-    // dynamic shared memory: block tallies (birth); region table + block tallies (physics)
-    const size_t bsm = wf::block_tally_bytes<false>(P.n_inst);
+    if (!wavefront_supports(P.n_region, 0)) return fail(GADEP_E_INVAL, "wavefront: too many regions");
+    // dynamic shared memory: block tallies (gen); region table + block tallies (physics)
+    const size_t gsm = wf::block_tally_bytes<false>(P.n_inst);
     const size_t rsm = (size_t)P.n_region * sizeof(int4) +
-                       (grad ? wf::block_tally_bytes<true>(P.n_inst) : wf::block_tally_bytes<false>(P.n_inst));
+                       (grad ? wf::block_tally_bytes<true>(P.n_inst) : wf::block_tally_bytes<false>(P.n_inst)) +
+                       (size_t)P.n_region * wf::kKeysPerRegion * sizeof(unsigned int);
     {
         cudaError_t e = cudaSuccess;
         auto set = [&](const void *f, size_t b) {
-            if (e == cudaSuccess && b > 48 * 1024)
+            if (e == cudaSuccess && b > 40 * 1024)
                 e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
         };
-        set((const void *)wf::birth_kernel<true>, bsm);
-        set((const void *)wf::birth_kernel<false>, bsm);
+        set((const void *)wf::gen_kernel, gsm);
         set((const void *)wf::physics_kernel<true, true>, rsm);
         set((const void *)wf::physics_kernel<true, false>, rsm);
         set((const void *)wf::physics_kernel<false, true>, rsm);
         set((const void *)wf::physics_kernel<false, false>, rsm);
         if (e != cudaSuccess) return fail(GADEP_E_CUDA, "wavefront: shared memory: %s", cudaGetErrorString(e));
     }
-    wf::init_kernel<<<(S.slots + 255) / 256, 256, 0, s>>>(S);
+    const unsigned long long max_iter = (unsigned long long)P.step_cap * 4 + P.total / 1024 + 1000000ull;
+    KernelTimer none;
+    KernelTimer &T = timer ? *timer : none;
+    T.before(s);
+    wf::init_kernel<<<(S.slots + 255) / 256, 256, 0, s>>>(S, max_iter);
+    T.after(KK_INIT, s);
+    T.before(s);
+    wf::gen_kernel<<<w->work_grid, 256, gsm, s>>>(P, S);
+    T.after(KK_GEN, s);
+    T.before(s);
+    wf::ctrl_kernel<<<1, 256, 0, s>>>(S, 1, P.total);
+    T.after(KK_CTRL, s);
+    const int sort_grid = (S.slots + 256 * wf::kSortPerThread - 1) / (256 * wf::kSortPerThread);
     const int check_every = 16;
-    const long long max_iter = (long long)P.step_cap * 4 + (long long)(P.total / 1024) + 1000000;
-    for (long long it = 0; it < max_iter; ++it) {
+    for (unsigned long long it = 0;; ++it) {
         const int cur = (int)(it & 1);
-        if (grad) {
-            wf::birth_kernel<true><<<w->work_grid, 256, bsm, s>>>(P, S, cur);
-        } else {
-            wf::birth_kernel<false><<<w->work_grid, 256, bsm, s>>>(P, S, cur);
-        }
-        if (count) wf::trace_kernel<true><<<w->trace_grid, 256, 0, s>>>(P.nodes, P.tris, S, cur, counters);
-        else wf::trace_kernel<false><<<w->trace_grid, 256, 0, s>>>(P.nodes, P.tris, S, cur, counters);
+        T.before(s);
+        if (grad) wf::spawn_kernel<true><<<w->work_grid, 256, 0, s>>>(P, S, cur);
+        else wf::spawn_kernel<false><<<w->work_grid, 256, 0, s>>>(P, S, cur);
+        T.after(KK_SPAWN, s);
+        T.before(s);
+        wf::sort_kernel<<<sort_grid, 256, 0, s>>>(S, cur, P.n_region * wf::kKeysPerRegion);
+        T.after(KK_SORT, s);
+        T.before(s);
+        if (count)
+            wf::trace_kernel<true><<<w->trace_grid, 256, 0, s>>>(P.nodes, P.tris, P.regions, P.n_region, S, cur,
+                                                                  counters);
+        else
+            wf::trace_kernel<false><<<w->trace_grid, 256, 0, s>>>(P.nodes, P.tris, P.regions, P.n_region, S, cur,
+                                                                   counters);
+        T.after(KK_TRACE, s);
+        T.before(s);
         if (grad) {
             if (count) wf::physics_kernel<true, true><<<w->work_grid, 256, rsm, s>>>(P, S, cur, counters);
             else wf::physics_kernel<true, false><<<w->work_grid, 256, rsm, s>>>(P, S, cur, counters);
@@ -769,17 +1083,24 @@ gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P, bool grad,
             if (count) wf::physics_kernel<false, true><<<w->work_grid, 256, rsm, s>>>(P, S, cur, counters);
             else wf::physics_kernel<false, false><<<w->work_grid, 256, rsm, s>>>(P, S, cur, counters);
         }
+        T.after(KK_PHYSICS, s);
+        T.before(s);
+        wf::gen_kernel<<<w->work_grid, 256, gsm, s>>>(P, S);
+        T.after(KK_GEN, s);
+        T.before(s);
+        wf::ctrl_kernel<<<1, 256, 0, s>>>(S, cur, P.total);
+        T.after(KK_CTRL, s);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(GADEP_E_CUDA, "wavefront: launch: %s", cudaGetErrorString(e));
         if (it % check_every == check_every - 1) {
             e = cudaMemcpyAsync(w->host_ctrl, S.ctrl, sizeof(wf::Ctrl), cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return fail(GADEP_E_CUDA, "wavefront: control read: %s", cudaGetErrorString(e));
-            const int nxt = cur ^ 1;
-            if (w->host_ctrl->work >= P.total && w->host_ctrl->q_count[nxt] == 0) return GADEP_OK;
+            if (w->host_ctrl->done == 1) return GADEP_OK;
+            if (w->host_ctrl->done == 2)
+                return fail(GADEP_E_TIMEOUT, "wavefront: iteration bound reached with photons still alive");
         }
     }
-    return fail(GADEP_E_TIMEOUT, "wavefront: iteration bound reached with photons still alive");
 }
 
 }  // namespace gadep
