@@ -127,6 +127,89 @@ __device__ __forceinline__ void tri_test(const float4 *__restrict__ tris, int i,
     }
 }
 
+// Shear of a ray for the fixed-permutation test below: kz = dominant axis,
+// kx = kz + 1 and ky = kx + 1 (mod 3), never swapped; flip = d[kz] < 0.
+struct ShearK {
+    int kz;
+    bool flip;
+    float sx, sy, sz;
+};
+
+__device__ __forceinline__ ShearK make_shear_k(float dx, float dy, float dz)
+{
+    const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
+    ShearK s;
+    s.kz = (ax > ay) ? ((ax > az) ? 0 : 2) : ((ay > az) ? 1 : 2);
+    const int kx = s.kz == 2 ? 0 : s.kz + 1;
+    const int ky = kx == 2 ? 0 : kx + 1;
+    const float dkz = pick(dx, dy, dz, s.kz);
+    s.flip = dkz < 0.0f;
+    s.sx = pick(dx, dy, dz, kx) / dkz;
+    s.sy = pick(dx, dy, dz, ky) / dkz;
+    s.sz = 1.0f / dkz;
+    return s;
+}
+
+template <int K>
+__device__ __forceinline__ float comp(float x, float y, float z)
+{
+    return K == 0 ? x : (K == 1 ? y : z);
+}
+
+// tri_test with the axis permutation fixed at compile time (KZ = dominant axis).
+// make_shear swaps kx and ky when d[kz] < 0 to keep the winding; that swap
+// negates U, V, W, det and T exactly, so t and the hit decision are the same
+// and only the sign of det turns, which `flip` undoes for `entering`.
+template <int KZ>
+__device__ __forceinline__ void tri_test_k(const float4 *__restrict__ tris, int i, int exclude, float ox,
+                                           float oy, float oz, const ShearK &sh, float t_min, float &t_best,
+                                           int &best, bool &entering)
+{
+    constexpr int KX = (KZ + 1) % 3, KY = (KX + 1) % 3;
+    const float4 a = __ldg(tris + 3 * i), b = __ldg(tris + 3 * i + 1), c = __ldg(tris + 3 * i + 2);
+    if (__float_as_int(b.w) == exclude) return;
+    const float Akz = comp<KZ>(a.x, a.y, a.z) - comp<KZ>(ox, oy, oz);
+    const float Bkz = comp<KZ>(b.x, b.y, b.z) - comp<KZ>(ox, oy, oz);
+    const float Ckz = comp<KZ>(c.x, c.y, c.z) - comp<KZ>(ox, oy, oz);
+    const float Ax = fmaf(-sh.sx, Akz, comp<KX>(a.x, a.y, a.z) - comp<KX>(ox, oy, oz));
+    const float Ay = fmaf(-sh.sy, Akz, comp<KY>(a.x, a.y, a.z) - comp<KY>(ox, oy, oz));
+    const float Bx = fmaf(-sh.sx, Bkz, comp<KX>(b.x, b.y, b.z) - comp<KX>(ox, oy, oz));
+    const float By = fmaf(-sh.sy, Bkz, comp<KY>(b.x, b.y, b.z) - comp<KY>(ox, oy, oz));
+    const float Cx = fmaf(-sh.sx, Ckz, comp<KX>(c.x, c.y, c.z) - comp<KX>(ox, oy, oz));
+    const float Cy = fmaf(-sh.sy, Ckz, comp<KY>(c.x, c.y, c.z) - comp<KY>(ox, oy, oz));
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        U = (float)__dsub_rn(__dmul_rn((double)Cx, (double)By), __dmul_rn((double)Cy, (double)Bx));
+        V = (float)__dsub_rn(__dmul_rn((double)Ax, (double)Cy), __dmul_rn((double)Ay, (double)Cx));
+        W = (float)__dsub_rn(__dmul_rn((double)Bx, (double)Ay), __dmul_rn((double)By, (double)Ax));
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return;
+    const float det = U + V + W;
+    if (det == 0.0f) return;
+    const float T = U * (sh.sz * Akz) + V * (sh.sz * Bkz) + W * (sh.sz * Ckz);
+    const float t = T / det;
+    if (t > t_min && t < t_best) {
+        t_best = t;
+        best = i;
+        entering = (det > 0.0f) != sh.flip;
+    }
+}
+
+template <int KZ>
+__device__ __forceinline__ void leaf_test_k(const float4 *__restrict__ tris, int ref, int exclude, float ox,
+                                            float oy, float oz, const ShearK &sh, float t_min, float &t_best,
+                                            int &best, bool &ent, uint32_t &ntested)
+{
+    const int code = ~ref;
+    const int first = code >> 3, count = code & 7;
+    for (int i = first; i < first + count; ++i) {
+        ++ntested;
+        tri_test_k<KZ>(tris, i, exclude, ox, oy, oz, sh, t_min, t_best, best, ent);
+    }
+}
+
 struct TravStats { uint32_t nodes, tris, relocated; };
 
 // Child word of a node: >= 0 inner node index; < 0 leaf ~(first << 3 | count).

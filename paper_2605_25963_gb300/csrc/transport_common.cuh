@@ -53,6 +53,7 @@ struct Params {
     int n_stripes;                      // tally copies [n_stripes][n_inst], summed on the host
     float root_lo[3], root_hi[3];       // bounds of every triangle (padded)
     int root_all;                       // tree over every triangle
+    int face_bins, n_keys;              // wavefront queue sort: direction cells, key count
 };
 
 // Slab test of the ray (t >= 0) against an axis-aligned box.

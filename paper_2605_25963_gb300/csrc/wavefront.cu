@@ -6,7 +6,7 @@
 //   spawn    free slots take births from the pending ring (an index map: the
 //            i-th free slot gets the i-th pending history) and join the trace
 //            queue after the survivors of the previous iteration;
-//   sort     counting sort of the queue by (region, direction octant), from the
+//   sort     counting sort of the queue by (region, direction class), from the
 //            key histogram that physics and spawn accumulate, so that a warp
 //            traverses one region's tree with rays of similar direction;
 //   trace    lean persistent traversal: warps claim chunks of the queue, lanes
@@ -60,8 +60,17 @@ struct __align__(32) Sec {      // second annihilation photon, waiting for the f
     float4 d;                   // direction, w = region bits
 };
 
-constexpr int kKeysPerRegion = 8;   // sort key: region * 8 + direction octant
-constexpr int kMaxKeys = 2048;      // regions * kKeysPerRegion at most
+constexpr int kMaxFaceBins = 10;    // direction cells per cube-map face and axis, at most
+constexpr int kMaxKeys = 8192;      // regions * 6 * face_bins^2 at most
+
+// Face cells per axis for a mesh of n_region regions: the finest that keeps the
+// key space within kMaxKeys (one bin at 256 regions).
+__host__ __device__ constexpr int face_bins_for(int n_region)
+{
+    int b = kMaxFaceBins;
+    while (b > 1 && n_region * 6 * b * b > kMaxKeys) --b;
+    return b;
+}
 constexpr uint32_t kFlagSec = 1u;   // a second annihilation photon is waiting
 constexpr uint32_t kFlagEsc = 2u;   // esc[slot] holds energy this history let escape
 constexpr int kTagShift = 8;        // at most 256 regions
@@ -72,10 +81,21 @@ __device__ __forceinline__ uint32_t ray_tag(int last_tri, int region)
     return ((uint32_t)(last_tri + 1) << kTagShift) | (uint32_t)region;
 }
 
-__device__ __forceinline__ uint32_t sort_key(int region, float px, float py, float pz, float dx, float dy, float dz)
+// Sort key of a ray: its region, then a cube-map cell of its direction -- the
+// face (dominant axis and its sign) and a fb x fb cell of the
+// other two components divided by the dominant one.  Lanes of a warp then share
+// the region's tree and the shear permutation of the triangle test, and descend
+// the tree along similar paths.
+__device__ __forceinline__ uint32_t sort_key(int region, int fb, float dx, float dy, float dz)
 {
-    (void)px; (void)py; (void)pz;
-    return (uint32_t)region * kKeysPerRegion + (dx < 0.0f ? 1u : 0u) + (dy < 0.0f ? 2u : 0u) + (dz < 0.0f ? 4u : 0u);
+    const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
+    const uint32_t kz = (ax > ay) ? ((ax > az) ? 0u : 2u) : ((ay > az) ? 1u : 2u);
+    const float m = kz == 0 ? dx : (kz == 1 ? dy : dz);
+    const float u = kz == 0 ? dy : dx, w = kz == 2 ? dy : dz;
+    const float h = 0.5f * (float)fb / fabsf(m);
+    const uint32_t bu = min((uint32_t)fmaxf(fmaf(u, h, 0.5f * (float)fb), 0.0f), (uint32_t)fb - 1u);
+    const uint32_t bw = min((uint32_t)fmaxf(fmaf(w, h, 0.5f * (float)fb), 0.0f), (uint32_t)fb - 1u);
+    return ((uint32_t)region * 6u + kz * 2u + (m < 0.0f ? 1u : 0u)) * (uint32_t)(fb * fb) + bu * (uint32_t)fb + bw;
 }
 
 // Adds key k to a shared-memory histogram, one atomic per distinct key of the warp.
@@ -158,6 +178,16 @@ struct BlockTally {
         if (dep_all != 0.0f) atomicAdd(&s.dep_all, dep_all);
         if (esc != 0.0f) atomicAdd(&s.esc, esc);
     }
+    // n histories of instance inst that ended at birth: one segment each, nothing
+    // deposited, the source energy escaped
+    __device__ void culled(int inst, uint32_t n, float E0)
+    {
+        STally &s = t[inst];
+        atomicAdd(&s.hist, n);
+        atomicAdd(&s.seg, n);
+        atomicAdd(&s.zero, n);
+        atomicAdd(&s.esc, (float)n * E0);
+    }
     __device__ void flush(TallyDev *T)
     {
         __syncthreads();
@@ -218,6 +248,7 @@ struct State {
     unsigned int *qkey[2];         // sort key of each queue entry
     unsigned int *hist[2];         // key histogram of queue[parity]
     unsigned int *fill;            // bucket cursors of the sort
+    unsigned int *base;            // bucket starts of the sort
     unsigned int *qsort;           // the queue in key order: what trace and physics walk
     unsigned int *dead[2];
     unsigned long long *pend;      // ring of global history indices waiting for a slot
@@ -343,18 +374,21 @@ __global__ void ctrl_kernel(State S, int cur, unsigned long long total)
 __global__ void __launch_bounds__(256) gen_kernel(const Params P, State S)
 {
     const uint32_t FULL = 0xffffffffu;
+    constexpr int kPer = kGenChunk / 256;   // ids per thread and chunk
     Ctrl &c = *S.ctrl;
     if (c.done) return;
     extern __shared__ double4 smem_gen[];
     __shared__ unsigned long long s_chunk, s_base;
-    __shared__ unsigned int s_cnt;
+    __shared__ unsigned int s_warp[8];
     BlockTally<false> bt;               // culled histories carry no score
     bt.init(smem_gen, P.n_inst);
-    if (threadIdx.x == 0) s_cnt = 0;
     const unsigned long long live0 = c.gen_live, tail0 = c.pend_tail;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t k0 = P.key0, k1 = P.key1;
     int inst = 0;
+    // culled histories of instance cull_inst not yet added to the block tally
+    uint32_t cull_n = 0;
+    int cull_inst = 0;
     while (true) {
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -364,38 +398,55 @@ __global__ void __launch_bounds__(256) gen_kernel(const Params P, State S)
         __syncthreads();
         const unsigned long long chunk = s_chunk;
         if (chunk >= P.total) break;
+        uint32_t keep = 0;              // bit k: id chunk + 256 k + threadIdx.x joins the ring
 #pragma unroll 1
-        for (int k = 0; k < kGenChunk / 256; ++k) {
+        for (int k = 0; k < kPer; ++k) {
             const unsigned long long g = chunk + (unsigned long long)(k * 256 + threadIdx.x);
-            bool keep = false;
-            if (g < P.total) {
-                inst = find_inst(P, g, inst);
-                const InstDev &I = P.inst[inst];
-                const unsigned long long local = g - (inst ? P.inst_end[inst - 1] : 0ull);
-                Words r;
-                r.init(0u, I.hist_offset + local, I.inst_id);
-                float ox, oy, oz, dx, dy, dz;
-                sample_birth(I, r, k0, k1, ox, oy, oz, dx, dy, dz);
-                if (I.birth_region == 0 && !ray_hits_box(P.root_lo, P.root_hi, ox, oy, oz, dx, dy, dz)) {
-                    bt.history(inst, 1u, 0u, false, 0.0f, 0.0f, I.E0, P.e_max, nullptr);
-                    if (g < P.n_trace) P.edep_trace[g] = 0.0f;
-                } else {
-                    keep = true;
+            if (g >= P.total) break;
+            inst = find_inst(P, g, inst);
+            const InstDev &I = P.inst[inst];
+            const unsigned long long local = g - (inst ? P.inst_end[inst - 1] : 0ull);
+            Words r;
+            r.init(0u, I.hist_offset + local, I.inst_id);
+            float ox, oy, oz, dx, dy, dz;
+            sample_birth(I, r, k0, k1, ox, oy, oz, dx, dy, dz);
+            if (I.birth_region == 0 && !ray_hits_box(P.root_lo, P.root_hi, ox, oy, oz, dx, dy, dz)) {
+                if (inst != cull_inst && cull_n) {
+                    bt.culled(cull_inst, cull_n, P.inst[cull_inst].E0);
+                    cull_n = 0;
                 }
+                cull_inst = inst;
+                ++cull_n;
+                if (g < P.n_trace) P.edep_trace[g] = 0.0f;
+            } else {
+                keep |= 1u << k;
             }
-            const uint32_t m = __ballot_sync(FULL, keep);
-            unsigned int off = 0;
-            if (lane == 0 && m) off = atomicAdd(&s_cnt, (unsigned int)__popc(m));
-            off = __shfl_sync(FULL, off, 0) + __popc(m & ((1u << lane) - 1u));
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                s_base = s_cnt ? atomicAdd(&c.pend_add, (unsigned long long)s_cnt) : 0ull;
-                s_cnt = 0;
-            }
-            __syncthreads();
-            if (keep) S.pend[(tail0 + s_base + off) & S.pend_mask] = g;
+        }
+        // block-wide exclusive prefix of the kept counts, one ring reservation per chunk
+        const unsigned int cnt = __popc(keep);
+        unsigned int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int v = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += v;
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned int tot = 0;
+            for (int w = 0; w < 8; ++w) { const unsigned int v = s_warp[w]; s_warp[w] = tot; tot += v; }
+            s_base = tot ? atomicAdd(&c.pend_add, (unsigned long long)tot) : 0ull;
+        }
+        __syncthreads();
+        unsigned long long pos = tail0 + s_base + s_warp[warp] + (inc - cnt);
+        while (keep) {
+            const int k = __ffs(keep) - 1;
+            keep &= keep - 1u;
+            S.pend[pos & S.pend_mask] = chunk + (unsigned long long)(k * 256 + threadIdx.x);
+            ++pos;
         }
     }
+    if (cull_n) bt.culled(cull_inst, cull_n, P.inst[cull_inst].E0);
     bt.flush(block_tally(P));
 }
 
@@ -423,7 +474,7 @@ __device__ __forceinline__ uint32_t spawn_one(const Params &P, const State &S, i
     ph.u = make_uint4(r.w, (uint32_t)local, (uint32_t)inst, 0u);
     S.phot[slot] = ph;
     if (GRAD) S.score[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    const uint32_t key = sort_key(I.birth_region, ox, oy, oz, dx, dy, dz);
+    const uint32_t key = sort_key(I.birth_region, P.face_bins, dx, dy, dz);
     S.queue[cur][qpos] = slot;
     S.qkey[cur][qpos] = key;
     return key;
@@ -437,8 +488,8 @@ __global__ void __launch_bounds__(256) spawn_kernel(const Params P, State S, int
     if (n_dead == 0) return;
     const unsigned long long head = c.sp_head;
     const uint32_t k0 = P.key0, k1 = P.key1;
-    const int n_keys = P.n_region * kKeysPerRegion;
-    __shared__ unsigned int s_hist[kMaxKeys];
+    const int n_keys = P.n_keys;
+    extern __shared__ unsigned int s_hist[];
     for (int k = threadIdx.x; k < n_keys; k += blockDim.x) s_hist[k] = 0u;
     __syncthreads();
     int inst = 0;
@@ -464,22 +515,15 @@ __global__ void __launch_bounds__(256) spawn_kernel(const Params P, State S, int
 }
 
 // ---------------------------------------------------------------- sort
-constexpr int kSortPerThread = 16;
+constexpr int kSortPerThread = 32;
 
-// Counting sort of queue[cur] into qsort: each block takes a contiguous range,
-// finds its keys' bucket starts from the exclusive prefix of the histogram,
-// reserves room in every bucket with one atomic per key and scatters.
-__global__ void __launch_bounds__(256) sort_kernel(State S, int cur, int n_keys)
+// Exclusive prefix of the key histogram of queue[cur]: the start of every bucket.
+__global__ void __launch_bounds__(1024) sort_prefix_kernel(State S, int cur, int n_keys)
 {
     const uint32_t FULL = 0xffffffffu;
-    __shared__ unsigned int s_base[kMaxKeys], s_cnt[kMaxKeys], s_warp[8];
-    const unsigned int n = S.ctrl->q_count[cur];
-    const unsigned int begin = blockIdx.x * (256u * kSortPerThread);
-    if (begin >= n) return;
-    const unsigned int end = min(begin + 256u * kSortPerThread, n);
+    __shared__ unsigned int s_warp[32];
+    constexpr int kpt = kMaxKeys / 1024;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // exclusive prefix of the histogram: thread t owns keys kpt t .. kpt t + kpt - 1
-    constexpr int kpt = kMaxKeys / 256;
     unsigned int loc[kpt], sum = 0;
 #pragma unroll
     for (int q = 0; q < kpt; ++q) {
@@ -495,21 +539,46 @@ __global__ void __launch_bounds__(256) sort_kernel(State S, int cur, int n_keys)
     }
     if (lane == 31) s_warp[warp] = inc;
     __syncthreads();
-    unsigned int pre = inc - sum;
-    for (int w = 0; w < warp; ++w) pre += s_warp[w];
+    if (warp == 0) {
+        const unsigned int t = s_warp[lane];
+        unsigned int x = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int v = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += v;
+        }
+        s_warp[lane] = x - t;
+    }
+    __syncthreads();
+    unsigned int pre = s_warp[warp] + inc - sum;
 #pragma unroll
     for (int q = 0; q < kpt; ++q) {
         const int k = threadIdx.x * kpt + q;
-        s_base[k] = pre;
-        s_cnt[k] = 0u;
+        if (k < n_keys) S.base[k] = pre;
         pre += loc[q];
     }
+}
+
+// Counting sort of queue[cur] into qsort: each block takes a contiguous range,
+// counts its keys, reserves room in every bucket it touches with one atomic per
+// key and scatters.  Dynamic shared memory: 2 * n_keys words.
+__global__ void __launch_bounds__(256) sort_kernel(State S, int cur, int n_keys)
+{
+    const uint32_t FULL = 0xffffffffu;
+    extern __shared__ unsigned int s_sort[];
+    unsigned int *s_base = s_sort, *s_cnt = s_sort + n_keys;
+    const unsigned int n = S.ctrl->q_count[cur];
+    const unsigned int begin = blockIdx.x * (256u * kSortPerThread);
+    if (begin >= n) return;
+    const unsigned int end = min(begin + 256u * kSortPerThread, n);
+    const int lane = threadIdx.x & 31;
+    for (int k = threadIdx.x; k < n_keys; k += 256) s_cnt[k] = 0u;
     __syncthreads();
     for (unsigned int i = begin + threadIdx.x; i < end; i += 256u) atomicAdd(&s_cnt[S.qkey[cur][i]], 1u);
     __syncthreads();
     for (int k = threadIdx.x; k < n_keys; k += 256)
         if (s_cnt[k]) {
-            s_base[k] += atomicAdd(&S.fill[k], s_cnt[k]);
+            s_base[k] = S.base[k] + atomicAdd(&S.fill[k], s_cnt[k]);
             s_cnt[k] = 0u;
         }
     __syncthreads();
@@ -547,7 +616,7 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const float4 *__restrict_
     float ox = 0, oy = 0, oz = 0, t_min = 0, ix = 0, iy = 0, iz = 0, oix = 0, oiy = 0, oiz = 0, t_best = 0;
     int exclude = -1, node = kSentinel, leaf = 0, sp = 0, best = -1;
     bool ent = false;
-    Shear sh{ 0, 1, 2, 0.0f, 0.0f, 1.0f };
+    ShearK sh{ 2, false, 0.0f, 0.0f, 1.0f };
     int stack[kStack];
     uint32_t nn = 0, nt = 0, err = 0;
     // warp-uniform private range [wb, we) of the queue, refilled a chunk at a time
@@ -580,7 +649,7 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const float4 *__restrict_
                 const uint32_t tag = __float_as_uint(r.d.w);
                 ox = r.o.x; oy = r.o.y; oz = r.o.z; t_min = r.o.w;
                 exclude = (int)(tag >> kTagShift) - 1;
-                sh = make_shear(r.d.x, r.d.y, r.d.z);
+                sh = make_shear_k(r.d.x, r.d.y, r.d.z);
                 ix = 1.0f / (fabsf(r.d.x) > 1e-30f ? r.d.x : copysignf(1e-30f, r.d.x));
                 iy = 1.0f / (fabsf(r.d.y) > 1e-30f ? r.d.y : copysignf(1e-30f, r.d.y));
                 iz = 1.0f / (fabsf(r.d.z) > 1e-30f ? r.d.z : copysignf(1e-30f, r.d.z));
@@ -632,8 +701,11 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const float4 *__restrict_
                 }
                 if (!__any_sync(__activemask(), leaf >= 0)) break;
             }
+            // the queue is sorted by dominant axis, so lanes of a warp take one branch
             while (leaf < 0) {
-                leaf_test(tris, leaf, exclude, ox, oy, oz, sh, t_min, t_best, best, ent, nt);
+                if (sh.kz == 0) leaf_test_k<0>(tris, leaf, exclude, ox, oy, oz, sh, t_min, t_best, best, ent, nt);
+                else if (sh.kz == 1) leaf_test_k<1>(tris, leaf, exclude, ox, oy, oz, sh, t_min, t_best, best, ent, nt);
+                else leaf_test_k<2>(tris, leaf, exclude, ox, oy, oz, sh, t_min, t_best, best, ent, nt);
                 leaf = node;
                 if (node < 0) node = stack[sp--];
             }
@@ -672,7 +744,7 @@ __global__ void __launch_bounds__(256) physics_kernel(const Params P, State S, i
     // key histogram of the next queue, after the block tallies
     unsigned int *s_hist = reinterpret_cast<unsigned int *>(
         reinterpret_cast<char *>(s_reg + P.n_region) + block_tally_bytes<GRAD>(P.n_inst));
-    const int n_keys = P.n_region * kKeysPerRegion;
+    const int n_keys = P.n_keys;
     for (int k = threadIdx.x; k < n_keys; k += blockDim.x) s_hist[k] = 0u;
     if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
     __syncthreads();
@@ -860,8 +932,7 @@ __global__ void __launch_bounds__(256) physics_kernel(const Params P, State S, i
                 ph.u = make_uint4(r.w, local, (uint32_t)inst | (herr << 16) | (flags << 24), steps);
                 S.phot[slot] = ph;
                 if (GRAD) S.score[slot] = make_float4(score[0], score[1], score[2], score[3]);
-                key = sort_key(region, fmaf(ry.o.w, ry.d.x, ry.o.x), fmaf(ry.o.w, ry.d.y, ry.o.y),
-                               fmaf(ry.o.w, ry.d.z, ry.o.z), ry.d.x, ry.d.y, ry.d.z);
+                key = sort_key(region, P.face_bins, ry.d.x, ry.d.y, ry.d.z);
                 alive_slot = true;
             } else {
                 float esc = 0.0f;
@@ -930,8 +1001,7 @@ int wavefront_trace_grid(const WavefrontBuffers *w) { return w ? w->trace_grid :
 
 bool wavefront_supports(int n_region, long long n_mesh_tri)
 {
-    return n_region >= 1 && n_region <= 256 && n_region * wf::kKeysPerRegion <= wf::kMaxKeys &&
-           n_mesh_tri <= wf::kMaxTriId;
+    return n_region >= 1 && n_region <= 256 && n_mesh_tri <= wf::kMaxTriId;
 }
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -967,7 +1037,7 @@ gadep_status wavefront_create(int device, int slots, bool grad, WavefrontBuffers
     size_t o_k0 = off; off = align_up(off + n * 4);
     size_t o_k1 = off; off = align_up(off + n * 4);
     size_t o_qs = off; off = align_up(off + n * 4);
-    size_t o_h = off; off = align_up(off + 3 * wf::kMaxKeys * 4);
+    size_t o_h = off; off = align_up(off + 4 * wf::kMaxKeys * 4);
     size_t o_d0 = off; off = align_up(off + n * 4);
     size_t o_d1 = off; off = align_up(off + n * 4);
     size_t o_pend = off; off = align_up(off + ring * sizeof(unsigned long long));
@@ -999,6 +1069,7 @@ gadep_status wavefront_create(int device, int slots, bool grad, WavefrontBuffers
     w->S.hist[0] = (unsigned int *)(b + o_h);
     w->S.hist[1] = w->S.hist[0] + wf::kMaxKeys;
     w->S.fill = w->S.hist[1] + wf::kMaxKeys;
+    w->S.base = w->S.fill + wf::kMaxKeys;
     w->S.dead[0] = (unsigned int *)(b + o_d0);
     w->S.dead[1] = (unsigned int *)(b + o_d1);
     w->S.pend = (unsigned long long *)(b + o_pend);
@@ -1019,18 +1090,23 @@ void wavefront_destroy(WavefrontBuffers *w)
 }
 
 // Run every history of the plan's Params through the wavefront kernels on `s`.
-gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P, bool grad, bool count,
+gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P0, bool grad, bool count,
                            unsigned long long *counters, KernelTimer *timer, cudaStream_t s)
 {
     wf::State S = w->S;
+    dev::Params P = P0;
+    P.face_bins = wf::face_bins_for(P.n_region);
+    P.n_keys = P.n_region * 6 * P.face_bins * P.face_bins;
     if (P.n_inst > kWavefrontMaxInstances)
         return fail(GADEP_E_INVAL, "wavefront: at most %d instances per run", kWavefrontMaxInstances);
     if (!wavefront_supports(P.n_region, 0)) return fail(GADEP_E_INVAL, "wavefront: too many regions");
     // dynamic shared memory: block tallies (gen); region table + block tallies (physics)
     const size_t gsm = wf::block_tally_bytes<false>(P.n_inst);
+    const size_t ksm = (size_t)P.n_keys * sizeof(unsigned int);   // key histogram (spawn)
+    const size_t ssm = 2 * ksm;                                    // bucket starts and counts (sort)
     const size_t rsm = (size_t)P.n_region * sizeof(int4) +
                        (grad ? wf::block_tally_bytes<true>(P.n_inst) : wf::block_tally_bytes<false>(P.n_inst)) +
-                       (size_t)P.n_region * wf::kKeysPerRegion * sizeof(unsigned int);
+                       (size_t)P.n_keys * sizeof(unsigned int);
     {
         cudaError_t e = cudaSuccess;
         auto set = [&](const void *f, size_t b) {
@@ -1038,6 +1114,7 @@ gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P, bool grad,
                 e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
         };
         set((const void *)wf::gen_kernel, gsm);
+        set((const void *)wf::sort_kernel, ssm);
         set((const void *)wf::physics_kernel<true, true>, rsm);
         set((const void *)wf::physics_kernel<true, false>, rsm);
         set((const void *)wf::physics_kernel<false, true>, rsm);
@@ -1061,11 +1138,12 @@ gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P, bool grad,
     for (unsigned long long it = 0;; ++it) {
         const int cur = (int)(it & 1);
         T.before(s);
-        if (grad) wf::spawn_kernel<true><<<w->work_grid, 256, 0, s>>>(P, S, cur);
-        else wf::spawn_kernel<false><<<w->work_grid, 256, 0, s>>>(P, S, cur);
+        if (grad) wf::spawn_kernel<true><<<w->work_grid, 256, ksm, s>>>(P, S, cur);
+        else wf::spawn_kernel<false><<<w->work_grid, 256, ksm, s>>>(P, S, cur);
         T.after(KK_SPAWN, s);
         T.before(s);
-        wf::sort_kernel<<<sort_grid, 256, 0, s>>>(S, cur, P.n_region * wf::kKeysPerRegion);
+        wf::sort_prefix_kernel<<<1, 1024, 0, s>>>(S, cur, P.n_keys);
+        wf::sort_kernel<<<sort_grid, 256, ssm, s>>>(S, cur, P.n_keys);
         T.after(KK_SORT, s);
         T.before(s);
         if (count)
