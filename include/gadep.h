@@ -75,7 +75,7 @@ enum { GADEP_MAT_VACUUM = 0, GADEP_MAT_GE = 1, GADEP_MAT_AL = 2, GADEP_MAT_CU = 
  *   BARE_CYLINDER: 0 active Ge crystal (R = D2, L = D1, rounding D3); [1 source]
  *   COAX: 0 endcap Al, 1 endcap vacuum, 2 holder Cu, 3 crystal (dead Ge),
  *         4 active Ge (R_active = D2 - D4, L_active = D1 - D4, Eq. of Sec. 2.3.2),
- *         5 bore contact (dead Ge), 6 bore vacuum, [7 source]
+ *         5 bore contact (dead Ge), 6 bore vacuum, [source], [flange Cu]
  * Density groups: 0 dead layer (COAX solid 3), 1 endcap, 2 active Ge, 3 source
  * matrix; other solids -1. */
 typedef struct {
@@ -88,6 +88,18 @@ typedef struct {
     int32_t has_source_solid;
     double  src_r, src_h, src_z0;
     int32_t src_n_sides;
+    /* Stress features of the coax (0 = absent).  Groove: an annular channel of
+     * width groove_w and depth groove_d centred at radius groove_r, cut into the
+     * crystal's back face; the active volume's back face follows it one
+     * separation step inside.  Flange: a flat Cu ring around the holder, radii
+     * flange_r_in .. flange_r_out, thickness flange_h, top face at z = flange_z_top,
+     * with n_bolt_holes axial through-holes of radius bolt_r (bolt_n_sides-gon
+     * walls) centred on the circle of radius bolt_rc, one per angular sector
+     * (n_theta must be a multiple of n_bolt_holes). */
+    double  groove_r, groove_w, groove_d;
+    double  flange_r_in, flange_r_out, flange_h, flange_z_top;
+    int32_t n_bolt_holes, bolt_n_sides;
+    double  bolt_r, bolt_rc;
 } detmesh_params;
 
 /* Per-solid attributes.  parent: innermost solid containing this one, -1 = world

@@ -91,6 +91,10 @@ def detmesh_build(det: W.Detector) -> Mesh:
     p.cup_rim_drop, p.sep_delta = det.cup_rim_drop, det.sep_delta
     p.has_source_solid = det.has_source_solid
     p.src_r, p.src_h, p.src_z0, p.src_n_sides = det.src_r, det.src_h, det.src_z0, det.src_n_sides
+    p.groove_r, p.groove_w, p.groove_d = det.groove_r, det.groove_w, det.groove_d
+    p.flange_r_in, p.flange_r_out, p.flange_h, p.flange_z_top = (det.flange_r_in, det.flange_r_out,
+                                                                det.flange_h, det.flange_z_top)
+    p.n_bolt_holes, p.bolt_n_sides, p.bolt_r, p.bolt_rc = det.n_bolt_holes, det.bolt_n_sides, det.bolt_r, det.bolt_rc
     h = C.c_void_p()
     check(capi.load().detmesh_build(C.byref(p), C.byref(h)))
     return Mesh(h)

@@ -41,7 +41,11 @@ class detmesh_params(C.Structure):
                 ("n_theta", C.c_int32), ("n_phi", C.c_int32), ("z_slices", C.c_int32),
                 ("cup_rim_drop", C.c_double), ("sep_delta", C.c_double),
                 ("has_source_solid", C.c_int32), ("src_r", C.c_double), ("src_h", C.c_double),
-                ("src_z0", C.c_double), ("src_n_sides", C.c_int32)]
+                ("src_z0", C.c_double), ("src_n_sides", C.c_int32),
+                ("groove_r", C.c_double), ("groove_w", C.c_double), ("groove_d", C.c_double),
+                ("flange_r_in", C.c_double), ("flange_r_out", C.c_double), ("flange_h", C.c_double),
+                ("flange_z_top", C.c_double), ("n_bolt_holes", C.c_int32), ("bolt_n_sides", C.c_int32),
+                ("bolt_r", C.c_double), ("bolt_rc", C.c_double)]
 
 
 class gadep_solid(C.Structure):

@@ -39,15 +39,20 @@ namespace wf {
 
 using namespace gadep::dev;
 
-// Slot records of 32 bytes (one DRAM sector each).
-struct __align__(32) Ray {      // read by trace and physics, written by spawn and physics
+// Per-slot photon record: 64 bytes, the DRAM fetch unit, so the physics visit
+// that needs all of it costs one fetch and the trace query (first half) no more.
+struct Ray {
     float4 o;                   // origin, w = t_cur (distance already travelled from o)
     float4 d;                   // direction, w = tag bits (last mesh triangle + 1) << 8 | region
 };
-struct __align__(32) Phot {
+struct Phot {
     float4 f;                   // E, lam (mean free paths left), edep (active), dep_all
     uint4 u;                    // Philox words used, history index within the instance,
                                 // instance | error bits << 16 | flags << 24, segments so far
+};
+struct __align__(64) Slot {
+    Ray r;                      // read by trace and physics, written by spawn and physics
+    Phot p;                     // read and written by physics, written by spawn
 };
 struct __align__(16) Hit {      // by queue position, written by trace
     float t;
@@ -55,6 +60,7 @@ struct __align__(16) Hit {      // by queue position, written by trace
     int region;                 // region of the triangle's solid
     int entering;               // 1 entering, 0 leaving, -2 traversal stack overflow
 };
+static_assert(sizeof(Slot) == 64, "slot record is one 64-byte DRAM fetch");
 struct __align__(32) Sec {      // second annihilation photon, waiting for the first
     float4 p;                   // position
     float4 d;                   // direction, w = region bits
@@ -238,8 +244,7 @@ struct Ctrl {
 };
 
 struct State {
-    Ray *ray;
-    Phot *phot;
+    Slot *slot;
     Sec *sec;
     float *esc;
     float4 *score;                 // GRAD only
@@ -468,11 +473,10 @@ __device__ __forceinline__ uint32_t spawn_one(const Params &P, const State &S, i
     Ray ry;
     ry.o = make_float4(ox, oy, oz, 0.0f);
     ry.d = make_float4(dx, dy, dz, __uint_as_float(ray_tag(-1, I.birth_region)));
-    S.ray[slot] = ry;
     Phot ph;
     ph.f = make_float4(I.E0, lam, 0.0f, 0.0f);
     ph.u = make_uint4(r.w, (uint32_t)local, (uint32_t)inst, 0u);
-    S.phot[slot] = ph;
+    S.slot[slot] = Slot{ ry, ph };
     if (GRAD) S.score[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     const uint32_t key = sort_key(I.birth_region, P.face_bins, dx, dy, dz);
     S.queue[cur][qpos] = slot;
@@ -645,7 +649,7 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const float4 *__restrict_
             drained = global_done && wb >= we;
             if (!has && idx != 0xffffffffu) {
                 qidx = idx;
-                const Ray r = S.ray[queue[idx]];
+                const Ray r = S.slot[queue[idx]].r;
                 const uint32_t tag = __float_as_uint(r.d.w);
                 ox = r.o.x; oy = r.o.y; oz = r.o.z; t_min = r.o.w;
                 exclude = (int)(tag >> kTagShift) - 1;
@@ -730,7 +734,7 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const float4 *__restrict_
 
 // ---------------------------------------------------------------- physics
 template <bool GRAD, bool COUNT>
-__global__ void __launch_bounds__(256) physics_kernel(const Params P, State S, int cur,
+__global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S, int cur,
                                                       unsigned long long *counters)
 {
     const uint32_t FULL = 0xffffffffu;
@@ -766,8 +770,9 @@ __global__ void __launch_bounds__(256) physics_kernel(const Params P, State S, i
         uint32_t herr_out = 0;
         if (mine) {
             const Hit ht = S.hit[j];
-            Ray ry = S.ray[slot];
-            Phot ph = S.phot[slot];
+            const Slot sl = S.slot[slot];
+            Ray ry = sl.r;
+            Phot ph = sl.p;
             float E = ph.f.x, lam = ph.f.y, edep = ph.f.z, dep_all = ph.f.w;
             const uint32_t local = ph.u.y;
             inst = (int)(ph.u.z & 0xffffu);
@@ -927,10 +932,9 @@ __global__ void __launch_bounds__(256) physics_kernel(const Params P, State S, i
             edep_out = edep;
             if (!finished) {
                 ry.d.w = __uint_as_float(ray_tag(last_tri, region));
-                S.ray[slot] = ry;
                 ph.f = make_float4(E, lam, edep, dep_all);
                 ph.u = make_uint4(r.w, local, (uint32_t)inst | (herr << 16) | (flags << 24), steps);
-                S.phot[slot] = ph;
+                S.slot[slot] = Slot{ ry, ph };
                 if (GRAD) S.score[slot] = make_float4(score[0], score[1], score[2], score[3]);
                 key = sort_key(region, P.face_bins, ry.d.x, ry.d.y, ry.d.z);
                 alive_slot = true;
@@ -1025,8 +1029,7 @@ gadep_status wavefront_create(int device, int slots, bool grad, WavefrontBuffers
     while (ring < need) ring <<= 1;
     const size_t n = (size_t)slots;
     size_t off = 0;
-    size_t o_ray = off; off = align_up(off + n * sizeof(wf::Ray));
-    size_t o_phot = off; off = align_up(off + n * sizeof(wf::Phot));
+    size_t o_slot = off; off = align_up(off + n * sizeof(wf::Slot));
     size_t o_sec = off; off = align_up(off + n * sizeof(wf::Sec));
     size_t o_esc = off; off = align_up(off + n * sizeof(float));
     size_t o_score = off; off = align_up(off + n * sizeof(float4));   // always: buffers serve both forms
@@ -1055,8 +1058,7 @@ gadep_status wavefront_create(int device, int slots, bool grad, WavefrontBuffers
         return fail(GADEP_E_NOMEM, "wavefront: pinned host allocation failed");
     }
     char *b = (char *)w->block;
-    w->S.ray = (wf::Ray *)(b + o_ray);
-    w->S.phot = (wf::Phot *)(b + o_phot);
+    w->S.slot = (wf::Slot *)(b + o_slot);
     w->S.sec = (wf::Sec *)(b + o_sec);
     w->S.esc = (float *)(b + o_esc);
     w->S.score = (float4 *)(b + o_score);

@@ -53,6 +53,18 @@ class Detector:
     src_h: float = 0.0
     src_z0: float = 0.0
     src_n_sides: int = 48
+    # stress features of the coax (0 = absent)
+    groove_r: float = 0.0
+    groove_w: float = 0.0
+    groove_d: float = 0.0
+    flange_r_in: float = 0.0
+    flange_r_out: float = 0.0
+    flange_h: float = 0.0
+    flange_z_top: float = 0.0
+    n_bolt_holes: int = 0
+    bolt_n_sides: int = 0
+    bolt_r: float = 0.0
+    bolt_rc: float = 0.0
 
     def as_dict(self):
         return dict(self.__dict__)
