@@ -76,6 +76,11 @@ typedef struct {
     int    has_source_solid;
     double src_r, src_h, src_z0;
     int    src_n_sides;
+    /* stress features of the coax (0 = absent): back-face groove, bolted flange */
+    double groove_r, groove_w, groove_d;
+    double flange_r_in, flange_r_out, flange_h, flange_z_top;
+    int    n_bolt_holes, bolt_n_sides;
+    double bolt_r, bolt_rc;
 } orc_detparams;
 
 typedef struct {

@@ -44,7 +44,11 @@ class DetParams(C.Structure):
                 ("n_theta", C.c_int), ("n_phi", C.c_int), ("z_slices", C.c_int),
                 ("cup_rim_drop", C.c_double), ("sep_delta", C.c_double),
                 ("has_source_solid", C.c_int), ("src_r", C.c_double), ("src_h", C.c_double),
-                ("src_z0", C.c_double), ("src_n_sides", C.c_int)]
+                ("src_z0", C.c_double), ("src_n_sides", C.c_int),
+                ("groove_r", C.c_double), ("groove_w", C.c_double), ("groove_d", C.c_double),
+                ("flange_r_in", C.c_double), ("flange_r_out", C.c_double), ("flange_h", C.c_double),
+                ("flange_z_top", C.c_double), ("n_bolt_holes", C.c_int), ("bolt_n_sides", C.c_int),
+                ("bolt_r", C.c_double), ("bolt_rc", C.c_double)]
 
 
 class MeshC(C.Structure):
@@ -248,6 +252,17 @@ class Det:
     src_h: float = 0.0
     src_z0: float = 0.0
     src_n_sides: int = 48
+    groove_r: float = 0.0
+    groove_w: float = 0.0
+    groove_d: float = 0.0
+    flange_r_in: float = 0.0
+    flange_r_out: float = 0.0
+    flange_h: float = 0.0
+    flange_z_top: float = 0.0
+    n_bolt_holes: int = 0
+    bolt_n_sides: int = 0
+    bolt_r: float = 0.0
+    bolt_rc: float = 0.0
 
     def c(self):
         p = DetParams()
@@ -260,6 +275,11 @@ class Det:
         p.cup_rim_drop, p.sep_delta = self.cup_rim_drop, self.sep_delta
         p.has_source_solid = self.has_source_solid
         p.src_r, p.src_h, p.src_z0, p.src_n_sides = self.src_r, self.src_h, self.src_z0, self.src_n_sides
+        p.groove_r, p.groove_w, p.groove_d = self.groove_r, self.groove_w, self.groove_d
+        p.flange_r_in, p.flange_r_out, p.flange_h, p.flange_z_top = (self.flange_r_in, self.flange_r_out,
+                                                                    self.flange_h, self.flange_z_top)
+        p.n_bolt_holes, p.bolt_n_sides, p.bolt_r, p.bolt_rc = (self.n_bolt_holes, self.bolt_n_sides, self.bolt_r,
+                                                               self.bolt_rc)
         return p
 
 

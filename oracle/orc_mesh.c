@@ -30,6 +30,12 @@
  *   solid 7  optional source (water prism)
  * The back faces of solids 3..6 coincide; they are separated inside-out
  * (Sec. 2.4.2, Fig. 6): nesting level L is lifted by L * sep_delta.
+ *   stress features (optional): an annular groove cut into the crystal's back
+ *   face (profile notch; the active volume's back face follows it one sep_delta
+ *   inside) and, after the source, a flat Cu flange ring with axial bolt holes.
+ *   The flange faces are planar polygons with holes; the oracle triangulates
+ *   each angular sector (one hole per sector) by ear clipping after bridging the
+ *   hole to the sector boundary.
  *
  * Bare cylinder: solid 0 = active Ge cylinder R = D2, length D1, rounding D3,
  * front face at z = 0; solid 1 = optional source prism.
@@ -109,7 +115,7 @@ static void revolve(builder *b, int solid, const double *rho, const double *z, i
 /* Profile of a cylinder of radius R from z_front down to z_back with a front
    rounding of radius rch (0 <= rch <= R); rch == R gives a hemispherical end. */
 static int rounded_profile(double R, double rch, double z_front, double z_back, int n_phi,
-                           int z_slices, double *rho, double *z)
+                           int z_slices, double g_in, double g_out, double g_depth, double *rho, double *z)
 {
     int n = 0;
     if (rch > 0.0) {
@@ -134,19 +140,154 @@ static int rounded_profile(double R, double rch, double z_front, double z_back, 
         z[n] = (s == z_slices) ? z_back : z_side_top - (z_side_top - z_back) * (double)s / (double)z_slices;
         ++n;
     }
+    if (g_depth > 0.0) {
+        /* annular channel g_in < rho < g_out cut g_depth into the back face */
+        rho[n] = g_out; z[n] = z_back; ++n;
+        rho[n] = g_out; z[n] = z_back + g_depth; ++n;
+        rho[n] = g_in;  z[n] = z_back + g_depth; ++n;
+        rho[n] = g_in;  z[n] = z_back; ++n;
+    }
     rho[n] = 0.0; z[n] = z_back; ++n;
     return n;
+}
+
+static void add_rounded_g(builder *b, int solid, double R, double rch, double z_front, double z_back,
+                          int N, int n_phi, int z_slices, double g_in, double g_out, double g_depth)
+{
+    int cap = n_phi + z_slices + 12;
+    double *rho = (double *)malloc((size_t)cap * sizeof(double));
+    double *z = (double *)malloc((size_t)cap * sizeof(double));
+    int np = rounded_profile(R, rch, z_front, z_back, n_phi, z_slices, g_in, g_out, g_depth, rho, z);
+    revolve(b, solid, rho, z, np, N);
+    free(rho); free(z);
 }
 
 static void add_rounded(builder *b, int solid, double R, double rch, double z_front, double z_back,
                         int N, int n_phi, int z_slices)
 {
-    int cap = n_phi + z_slices + 8;
-    double *rho = (double *)malloc((size_t)cap * sizeof(double));
-    double *z = (double *)malloc((size_t)cap * sizeof(double));
-    int np = rounded_profile(R, rch, z_front, z_back, n_phi, z_slices, rho, z);
-    revolve(b, solid, rho, z, np, N);
-    free(rho); free(z);
+    add_rounded_g(b, solid, R, rch, z_front, z_back, N, n_phi, z_slices, 0.0, 0.0, 0.0);
+}
+
+/* ---- flange: planar faces with holes, triangulated by ear clipping ---- */
+
+typedef struct { double x, y; int id; } pt2;
+
+static double cross3(const pt2 *a, const pt2 *b, const pt2 *c)
+{
+    return (b->x - a->x) * (c->y - a->y) - (b->y - a->y) * (c->x - a->x);
+}
+
+static int same_point(const pt2 *a, const pt2 *b) { return a->x == b->x && a->y == b->y; }
+
+/* p inside or on the closed triangle (a, b, c) given counter-clockwise */
+static int in_triangle(const pt2 *p, const pt2 *a, const pt2 *b, const pt2 *c)
+{
+    return cross3(a, b, p) >= 0.0 && cross3(b, c, p) >= 0.0 && cross3(c, a, p) >= 0.0;
+}
+
+/* Ear clipping of a counter-clockwise (weakly) simple polygon of n points; emits
+   n - 2 counter-clockwise triangles through emit(ids).  Returns 0 on success. */
+static int ear_clip(pt2 *poly, int n, builder *b, int solid, int flip)
+{
+    int *idx = (int *)malloc((size_t)n * sizeof(int));
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    int m = n, guard = 0;
+    while (m > 3) {
+        int found = 0;
+        for (int k = 0; k < m && !found; ++k) {
+            const pt2 *a = &poly[idx[(k + m - 1) % m]], *c0 = &poly[idx[k]], *c = &poly[idx[(k + 1) % m]];
+            if (cross3(a, c0, c) <= 0.0) continue;          /* reflex or degenerate corner */
+            int blocked = 0;
+            for (int q = 0; q < m && !blocked; ++q) {
+                const pt2 *p = &poly[idx[q]];
+                if (same_point(p, a) || same_point(p, c0) || same_point(p, c)) continue;
+                if (in_triangle(p, a, c0, c)) blocked = 1;
+            }
+            if (blocked) continue;
+            if (flip) add_tri(b, a->id, c->id, c0->id, solid);
+            else add_tri(b, a->id, c0->id, c->id, solid);
+            for (int q = k; q + 1 < m; ++q) idx[q] = idx[q + 1];
+            --m;
+            found = 1;
+        }
+        if (!found || ++guard > 4 * n) { free(idx); return -1; }
+    }
+    const pt2 *a = &poly[idx[0]], *c0 = &poly[idx[1]], *c = &poly[idx[2]];
+    if (flip) add_tri(b, a->id, c->id, c0->id, solid);
+    else add_tri(b, a->id, c0->id, c->id, solid);
+    free(idx);
+    return 0;
+}
+
+/* Flat ring r_in..r_out, z in [z_top - h, z_top], with nh axial holes of radius
+   rh (M-gon, M even) centred on radius rc, hole k at angle 2 pi (k + 1/2) / nh.
+   N (a multiple of nh, N / nh even) vertices on each circle. */
+static int add_flange(builder *b, int solid, double r_in, double r_out, double h, double z_top, int nh,
+                      int M, double rh, double rc, int N)
+{
+    if (nh < 1 || N % nh != 0 || (N / nh) % 2 != 0 || M < 4 || M % 2 != 0) return -1;
+    const double zt = z_top, zb = z_top - h;
+    const int m = N / nh;
+    int ring[4];                       /* inner top, outer top, inner bottom, outer bottom */
+    const double rr[4] = { r_in, r_out, r_in, r_out }, zz[4] = { zt, zt, zb, zb };
+    for (int q = 0; q < 4; ++q) {
+        ring[q] = b->n_vert;
+        for (int i = 0; i < N; ++i) {
+            double th = 2.0 * ORC_PI * (double)i / (double)N;
+            add_vertex(b, rr[q] * cos(th), rr[q] * sin(th), zz[q]);
+        }
+    }
+    int *hole = (int *)malloc((size_t)nh * 2 * sizeof(int));
+    for (int k = 0; k < nh; ++k) {
+        double tc = 2.0 * ORC_PI * ((double)k + 0.5) / (double)nh;
+        double cx = rc * cos(tc), cy = rc * sin(tc);
+        for (int f = 0; f < 2; ++f) {
+            hole[2 * k + f] = b->n_vert;
+            for (int j = 0; j < M; ++j) {
+                double a = tc + 2.0 * ORC_PI * (double)j / (double)M;
+                add_vertex(b, cx + rh * cos(a), cy + rh * sin(a), f == 0 ? zt : zb);
+            }
+        }
+    }
+    /* walls: outer faces +r, inner faces toward the axis, hole walls toward the hole axis */
+    for (int i = 0; i < N; ++i) {
+        int i1 = (i + 1) % N;
+        add_tri(b, ring[1] + i, ring[3] + i, ring[3] + i1, solid);
+        add_tri(b, ring[1] + i, ring[3] + i1, ring[1] + i1, solid);
+        add_tri(b, ring[0] + i, ring[2] + i1, ring[2] + i, solid);
+        add_tri(b, ring[0] + i, ring[0] + i1, ring[2] + i1, solid);
+    }
+    for (int k = 0; k < nh; ++k) {
+        int t = hole[2 * k], u = hole[2 * k + 1];
+        for (int j = 0; j < M; ++j) {
+            int j1 = (j + 1) % M;
+            add_tri(b, t + j, t + j1, u + j1, solid);
+            add_tri(b, t + j, u + j1, u + j, solid);
+        }
+    }
+    /* faces: each sector polygon, hole bridged to the inner-arc midpoint */
+    int n_poly = 2 * (m + 1) + M + 3;
+    pt2 *poly = (pt2 *)malloc((size_t)n_poly * sizeof(pt2));
+    int rc_ok = 0;
+    for (int f = 0; f < 2 && rc_ok == 0; ++f) {
+        int in = ring[f == 0 ? 0 : 2], out = ring[f == 0 ? 1 : 3];
+        for (int k = 0; k < nh && rc_ok == 0; ++k) {
+            int n = 0;
+#define ORC_PUSH(vid) do { int v_ = (vid); poly[n].x = b->xyz[3 * v_]; poly[n].y = b->xyz[3 * v_ + 1]; poly[n].id = v_; ++n; } while (0)
+            /* counter-clockwise: outer arc forward, inner arc backward with the bridge */
+            for (int i = 0; i <= m; ++i) ORC_PUSH(out + (k * m + i) % N);
+            for (int i = m; i >= m / 2; --i) ORC_PUSH(in + (k * m + i) % N);
+            int hv = hole[2 * k + f];
+            /* around the hole clockwise, from its vertex facing the axis and back */
+            for (int j = 0; j <= M; ++j) ORC_PUSH(hv + ((M / 2 - j) % M + M) % M);
+            for (int i = m / 2; i >= 0; --i) ORC_PUSH(in + (k * m + i) % N);
+#undef ORC_PUSH
+            rc_ok = ear_clip(poly, n, b, solid, f == 1);
+        }
+    }
+    free(poly);
+    free(hole);
+    return rc_ok;
 }
 
 static void add_cup(builder *b, int solid, double r_in, double r_out, double z_rim,
@@ -210,19 +351,29 @@ int orc_mesh_build(const orc_detparams *p, orc_mesh **out)
     double r_in = D[1] + d[5];
     add_cup(&b, 2, r_in, r_in + d[3], z_front - p->cup_rim_drop, -d[7] + d[9], -d[7], N);
     /* 3 crystal, 4 active (Eq. R_active = D2 - D4, L_active = D1 - D4) */
-    add_rounded(&b, 3, D[1], D[2], z_front, z_back, N, nphi, zs);
+    double gi = p->groove_r - 0.5 * p->groove_w, go = p->groove_r + 0.5 * p->groove_w;
+    double gd = p->groove_d > 0.0 ? p->groove_d : 0.0;
+    add_rounded_g(&b, 3, D[1], D[2], z_front, z_back, N, nphi, zs, gi, go, gd);
     double rch_a = D[2] - D[3] > 0.0 ? D[2] - D[3] : 0.0;
-    add_rounded(&b, 4, D[1] - D[3], rch_a, z_front - D[3], z_back + 1.0 * sep, N, nphi, zs);
+    add_rounded_g(&b, 4, D[1] - D[3], rch_a, z_front - D[3], z_back + 1.0 * sep, N, nphi, zs, gi - sep, go + sep, gd);
     /* 5 bore contact, 6 bore vacuum: blind end toward the front, depth from the back face */
     double rc = D[5] + D[6];
     add_rounded(&b, 5, rc, rc, z_back + D[4] + D[6], z_back + 2.0 * sep, N, nphi, 1);
     add_rounded(&b, 6, D[5], D[5], z_back + D[4], z_back + 3.0 * sep, N, nphi, 1);
-    int n_solid = 7;
+    int n_solid = 7, src_solid = -1, flange_solid = -1;
     if (p->has_source_solid) {
         double rho[4] = { 0.0, p->src_r, p->src_r, 0.0 };
         double z[4] = { p->src_z0 + p->src_h, p->src_z0 + p->src_h, p->src_z0, p->src_z0 };
-        revolve(&b, 7, rho, z, 4, p->src_n_sides);
-        n_solid = 8;
+        src_solid = n_solid++;
+        revolve(&b, src_solid, rho, z, 4, p->src_n_sides);
+    }
+    if (p->flange_h > 0.0) {
+        flange_solid = n_solid++;
+        if (add_flange(&b, flange_solid, p->flange_r_in, p->flange_r_out, p->flange_h, p->flange_z_top,
+                       p->n_bolt_holes, p->bolt_n_sides, p->bolt_r, p->bolt_rc, N) != 0) {
+            free(b.xyz); free(b.tri); free(b.tri_solid);
+            return -1;
+        }
     }
     orc_mesh *m = finish(&b, n_solid);
     set_solid(m, 0, ORC_MAT_AL, 0, 1, -1);
@@ -232,7 +383,8 @@ int orc_mesh_build(const orc_detparams *p, orc_mesh **out)
     set_solid(m, 4, ORC_MAT_GE, 1, 2, 3);
     set_solid(m, 5, ORC_MAT_GE, 0, -1, 4);
     set_solid(m, 6, ORC_MAT_VACUUM, 0, -1, 5);
-    if (n_solid == 8) set_solid(m, 7, ORC_MAT_WATER, 0, 3, -1);
+    if (src_solid >= 0) set_solid(m, src_solid, ORC_MAT_WATER, 0, 3, -1);
+    if (flange_solid >= 0) set_solid(m, flange_solid, ORC_MAT_CU, 0, -1, 1);
     *out = m;
     return 0;
 }

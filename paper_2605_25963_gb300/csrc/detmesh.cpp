@@ -78,10 +78,14 @@ void stitch(Surface &s, const Ring &a, const Ring &b, int n_theta)
 // ChamferedCylinder: cylinder of radius R and length L with a front-edge
 // rounding of radius r_ch (0 <= r_ch <= R).  r_ch == R closes the front with a
 // hemisphere whose apex is a single vertex (the borehole end, Fig. 10).
+// Optionally with an annular groove g_in < rho < g_out cut g_depth deep into the
+// back face (the contact groove of a stress model).
 class ChamferedCylinder : public Geometry {
 public:
-    ChamferedCylinder(double R, double r_ch, double L, int n_theta, int n_phi, int z_slices)
-        : R_(R), rch_(r_ch), L_(L), nt_(n_theta), np_(n_phi), zs_(std::max(1, z_slices)) {}
+    ChamferedCylinder(double R, double r_ch, double L, int n_theta, int n_phi, int z_slices,
+                      double g_in = 0.0, double g_out = 0.0, double g_depth = 0.0)
+        : R_(R), rch_(r_ch), L_(L), nt_(n_theta), np_(n_phi), zs_(std::max(1, z_slices)),
+          gi_(g_in), go_(g_out), gd_(g_depth) {}
     Surface generate() const override
     {
         Surface s;
@@ -105,6 +109,12 @@ public:
             double z = (k == zs_) ? L_ : z0 + (L_ - z0) * k / zs_;
             rings.push_back(make_ring(s, R_, z, nt_));
         }
+        if (gd_ > 0.0) {
+            rings.push_back(make_ring(s, go_, L_, nt_));
+            rings.push_back(make_ring(s, go_, L_ - gd_, nt_));
+            rings.push_back(make_ring(s, gi_, L_ - gd_, nt_));
+            rings.push_back(make_ring(s, gi_, L_, nt_));
+        }
         rings.push_back(make_ring(s, 0.0, L_, nt_));               // back face centre
         for (size_t k = 0; k + 1 < rings.size(); ++k) stitch(s, rings[k], rings[k + 1], nt_);
         return s;
@@ -112,6 +122,7 @@ public:
 private:
     double R_, rch_, L_;
     int nt_, np_, zs_;
+    double gi_, go_, gd_;
 };
 
 // Cup (crystal holder): open-topped hollow cylinder with a flat bottom.  Local
@@ -137,6 +148,118 @@ public:
     }
 private:
     double ri_, w_, h_, b_;
+    int nt_;
+};
+
+// Flange: flat ring r_in..r_out, thickness h (local z in [0, h]), with nh axial
+// bolt holes (M-gon walls of circumradius rh) centred on radius rc, hole k at the
+// middle of angular sector k.  Each face of a sector is a polygon with one hole;
+// it is triangulated by zipping the sector boundary and the hole polygon in the
+// sector's (radius, arc length) coordinates, where the boundary is a rectangle
+// and both loops are star-shaped about the hole centre.  generate() fails (empty
+// surface) if a triangle comes out with non-positive area in the plane.
+class Flange : public Geometry {
+public:
+    Flange(double r_in, double r_out, double h, int nh, int M, double rh, double rc, int n_theta)
+        : ri_(r_in), ro_(r_out), h_(h), nh_(nh), M_(M), rh_(rh), rc_(rc), nt_(n_theta) {}
+    Surface generate() const override
+    {
+        Surface s;
+        const int m = nt_ / nh_;
+        // rings: inner / outer circle at the two faces; hole polygons at the two faces
+        int ring[2][2];                          // [face][inner, outer]
+        for (int f = 0; f < 2; ++f)
+            for (int q = 0; q < 2; ++q) ring[f][q] = make_ring(s, q ? ro_ : ri_, f ? h_ : 0.0, nt_).first;
+        std::vector<int> hole(2 * nh_);
+        for (int k = 0; k < nh_; ++k) {
+            const double tc = 2.0 * kPi * (k + 0.5) / nh_;
+            const double cx = rc_ * std::cos(tc), cy = rc_ * std::sin(tc);
+            for (int f = 0; f < 2; ++f) {
+                hole[2 * k + f] = (int)(s.v.size() / 3);
+                for (int j = 0; j < M_; ++j) {
+                    const double a = tc + 2.0 * kPi * j / M_;
+                    s.add(cx + rh_ * std::cos(a), cy + rh_ * std::sin(a), f ? h_ : 0.0);
+                }
+            }
+        }
+        // side walls, wound with outward normals (outer wall +r, inner wall and
+        // hole walls toward their axes)
+        for (int i = 0; i < nt_; ++i) {
+            const int j = (i + 1) % nt_;
+            s.tri(ring[0][1] + i, ring[0][1] + j, ring[1][1] + j);   // outer wall
+            s.tri(ring[0][1] + i, ring[1][1] + j, ring[1][1] + i);
+            s.tri(ring[0][0] + i, ring[1][0] + j, ring[0][0] + j);   // inner wall
+            s.tri(ring[0][0] + i, ring[1][0] + i, ring[1][0] + j);
+        }
+        for (int k = 0; k < nh_; ++k) {
+            const int t = hole[2 * k], u = hole[2 * k + 1];
+            for (int j = 0; j < M_; ++j) {
+                const int j1 = (j + 1) % M_;
+                s.tri(t + j, u + j1, t + j1);
+                s.tri(t + j, u + j, u + j1);
+            }
+        }
+        // faces
+        for (int f = 0; f < 2; ++f) {
+            for (int k = 0; k < nh_; ++k) {
+                const double tc = 2.0 * kPi * (k + 0.5) / nh_;
+                // sector boundary counter-clockwise in the plane: outer arc forward,
+                // radial edge in, inner arc backward, radial edge out
+                std::vector<int> outer;
+                for (int i = 0; i <= m; ++i) outer.push_back(ring[f][1] + (k * m + i) % nt_);
+                for (int i = m; i >= 0; --i) outer.push_back(ring[f][0] + (k * m + i) % nt_);
+                std::vector<int> inner;                              // hole, counter-clockwise
+                for (int j = 0; j < M_; ++j) inner.push_back(hole[2 * k + f] + j);
+                // polar angle about the hole centre in (radius - rc, rc * (theta - tc))
+                auto ang = [&](int v) {
+                    const double x = s.v[3 * v], y = s.v[3 * v + 1];
+                    double th = std::atan2(y, x) - tc;
+                    th -= 2.0 * kPi * std::floor((th + kPi) / (2.0 * kPi));
+                    return std::atan2(rc_ * th, std::hypot(x, y) - rc_);
+                };
+                const int no = (int)outer.size(), ni = (int)inner.size();
+                std::vector<double> ao(no), ai(ni);
+                for (int i = 0; i < no; ++i) ao[i] = ang(outer[i]);
+                for (int j = 0; j < ni; ++j) ai[j] = ang(inner[j]);
+                const int o0 = (int)(std::min_element(ao.begin(), ao.end()) - ao.begin());
+                const double ref = ao[o0];
+                auto rel = [&](double a) { double d = a - ref; while (d < 0.0) d += 2.0 * kPi; return d; };
+                int i0 = 0;
+                for (int j = 1; j < ni; ++j)
+                    if (rel(ai[j]) < rel(ai[i0])) i0 = j;
+                int io = 0, ii = 0;
+                while (io < no || ii < ni) {
+                    const int oa = outer[(o0 + io) % no], ia = inner[(i0 + ii) % ni];
+                    const double next_o = io + 1 <= no ? (io + 1 == no ? 2.0 * kPi : rel(ao[(o0 + io + 1) % no])) : 1e300;
+                    const double next_i = ii + 1 <= ni ? rel(ai[(i0 + ii + 1) % ni]) + (ii + 1 == ni ? 2.0 * kPi : 0.0) : 1e300;
+                    if (io < no && (ii >= ni || next_o <= next_i)) {
+                        s.tri(oa, outer[(o0 + io + 1) % no], ia);
+                        ++io;
+                    } else {
+                        s.tri(oa, inner[(i0 + ii + 1) % ni], ia);
+                        ++ii;
+                    }
+                }
+            }
+        }
+        // the zipper winds both faces counter-clockwise (normal +z); the face at
+        // z = 0 bounds the solid from below, so its outward windings are reversed
+        const size_t n_face = (size_t)nh_ * (size_t)(2 * m + 2 + M_) * 3;
+        const size_t face0 = s.f.size() - 2 * n_face, face1 = s.f.size() - n_face;
+        for (size_t t = face0; t < face1; t += 3) std::swap(s.f[t + 1], s.f[t + 2]);
+        // every face triangle must have positive area in its face's winding
+        for (size_t t = face0; t < s.f.size(); t += 3) {
+            const double *a = &s.v[3 * s.f[t]], *b = &s.v[3 * s.f[t + 1]], *c = &s.v[3 * s.f[t + 2]];
+            double cz = (b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0]);
+            if (t < face1) cz = -cz;
+            if (!(cz > 0.0)) return Surface{};
+        }
+        return s;
+    }
+private:
+    double ri_, ro_, h_;
+    int nh_, M_;
+    double rh_, rc_;
     int nt_;
 };
 
@@ -244,6 +367,21 @@ public:
               z_rim > -d[7] + d[9] && z_back > -d[7] + d[9] && -d[7] > -d[6] + d[8] &&
               z_front < -d[1] && D[3] < D[0]))
             return gadep::fail(GADEP_E_INVAL, "coax: parameters give overlapping components");
+        if (p.groove_d > 0.0 &&
+            !(p.groove_w > 0.0 && p.groove_r - 0.5 * p.groove_w - sep > D[5] + D[6] + sep &&
+              p.groove_r + 0.5 * p.groove_w + sep < r_act && p.groove_d + 4 * sep < l_act - D[4]))
+            return gadep::fail(GADEP_E_INVAL, "coax: the back-face groove must lie between the bore and the side");
+        if (p.flange_h > 0.0) {
+            const double r_cup_out = r_cup_in + d[3];
+            const int nh = p.n_bolt_holes, M = p.bolt_n_sides;
+            if (!(nh >= 1 && M >= 4 && M % 2 == 0 && p.n_theta % nh == 0 && (p.n_theta / nh) % 2 == 0 &&
+                  p.flange_r_in > r_cup_out && p.flange_r_out < d[0] - d[2] && p.flange_r_in < p.flange_r_out &&
+                  p.bolt_r > 0.0 && p.bolt_rc - p.bolt_r > p.flange_r_in && p.bolt_rc + p.bolt_r < p.flange_r_out &&
+                  2.0 * p.bolt_r < 2.0 * kPi * (p.bolt_rc - p.bolt_r) / nh &&
+                  p.flange_z_top < -d[1] && p.flange_z_top - p.flange_h > -d[6] + d[8]))
+                return gadep::fail(GADEP_E_INVAL, "coax: flange must lie between the holder and the endcap wall, "
+                                                  "n_theta a multiple of 2 n_bolt_holes, even bolt_n_sides");
+        }
         const int nt = p.n_theta, np = p.n_phi;
 
         // endcap and its vacuum: plain cylinders, top face at local z = 0
@@ -253,10 +391,13 @@ public:
         relocate(endvac, -d[1]);
         Surface cup = Cup(r_cup_in, d[3], z_rim + d[7], d[9], nt).generate();
         relocate(cup, z_rim);
-        Surface crystal = ChamferedCylinder(D[1], D[2], D[0], nt, np, p.z_slices).generate();
+        // optional back-face groove; the active volume follows it one delta inside
+        const double gi = p.groove_r - 0.5 * p.groove_w, go = p.groove_r + 0.5 * p.groove_w;
+        const double gd = p.groove_d > 0.0 ? p.groove_d : 0.0;
+        Surface crystal = ChamferedCylinder(D[1], D[2], D[0], nt, np, p.z_slices, gi, go, gd).generate();
         relocate(crystal, z_front);
         // active volume: front shrunk by D4, back face kept and separated by one delta
-        Surface active = ChamferedCylinder(r_act, rch_act, l_act - sep, nt, np, p.z_slices).generate();
+        Surface active = ChamferedCylinder(r_act, rch_act, l_act - sep, nt, np, p.z_slices, gi - sep, go + sep, gd).generate();
         relocate(active, z_front - D[3]);
         // borehole contact and vacuum: hemispherical blind ends toward the front
         const double rc = D[5] + D[6];
@@ -273,6 +414,13 @@ public:
         a.add(std::move(contact), attr(GADEP_MAT_GE, 0, -1));
         a.add(std::move(borevac), attr(GADEP_MAT_VACUUM, 0, -1));
         if (p.has_source_solid) add_source_prism(p, a);
+        if (p.flange_h > 0.0) {
+            Surface fl = Flange(p.flange_r_in, p.flange_r_out, p.flange_h, p.n_bolt_holes, p.bolt_n_sides, p.bolt_r,
+                                p.bolt_rc, nt).generate();
+            if (fl.f.empty()) return gadep::fail(GADEP_E_MESH, "coax: flange face triangulation failed");
+            relocate(fl, p.flange_z_top);
+            a.add(std::move(fl), attr(GADEP_MAT_CU, 0, -1));
+        }
         return GADEP_OK;
     }
 };

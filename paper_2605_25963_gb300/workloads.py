@@ -20,6 +20,9 @@ closed-form synthetic cross sections instead of evaluated data):
                     history counts 1e6-5e7.
   gradient          coax_p + water prism 70 dia x 40 on the endcap; four density
                     groups (dead layer, endcap, active Ge, source matrix).
+  stress            gradient geometry at 1024 segments (~1e6 triangles) with a
+                    back-face contact groove and a bolted Cu flange; 8 energies
+                    59.5-1836 keV, 1.25e8 histories each.
 """
 from __future__ import annotations
 
@@ -139,6 +142,27 @@ GRAD_SOURCE = Source(kind=SRC_PRISM, pos=(0.0, 0.0, 0.01), radius=35.0, height=4
 GRAD_ENERGIES = (59.5, 122.0, 662.0, 1332.0)
 GRAD_HISTORIES = 50_000_000
 GRAD_N_GROUP = 4
+
+# ---------------- stress ----------------
+# The gradient workload's detector and volume source at 1024 segments per circle,
+# with a 2 x 1 mm contact groove on the crystal back face (centred at r = 8 mm)
+# and a 3 mm Cu flange ring around the holder carrying 16 bolt holes (r 1.5 mm,
+# 64-gon walls); z_slices brings the mesh to about 1e6 triangles.  The flange is
+# solid 8 (after the source, solid 7).
+STRESS_FEATURES = dict(groove_r=8.0, groove_w=2.0, groove_d=1.0, flange_r_in=32.0, flange_r_out=36.5,
+                       flange_h=3.0, flange_z_top=-21.0, n_bolt_holes=16, bolt_n_sides=64, bolt_r=1.5,
+                       bolt_rc=34.25)
+STRESS_DET = Detector(kind=DET_COAX, d=COAX_D_EXT, D=COAX_D_INT, n_theta=1024, n_phi=10, z_slices=214,
+                      cup_rim_drop=10.0, sep_delta=1e-4, has_source_solid=1, src_r=35.0, src_h=40.0,
+                      src_z0=0.01, src_n_sides=128, **STRESS_FEATURES)
+# the same features at 64 segments per circle (fast host checks and oracle parity)
+STRESS_SMALL = Detector(kind=DET_COAX, d=COAX_D_EXT, D=COAX_D_INT, n_theta=64, n_phi=10, z_slices=4,
+                        cup_rim_drop=10.0, sep_delta=1e-4, has_source_solid=1, src_r=35.0, src_h=40.0,
+                        src_z0=0.01, src_n_sides=128, **dict(STRESS_FEATURES, bolt_n_sides=16))
+STRESS_SOURCE = GRAD_SOURCE
+STRESS_ENERGIES = tuple(59.5 * (1836.0 / 59.5) ** (j / 7.0) for j in range(8))
+STRESS_HISTORIES = 125_000_000
+STRESS_FLANGE_SOLID = 8
 
 # ---------------- slabs (analytic checks) ----------------
 

@@ -165,3 +165,72 @@ def test_box_mesh_input_generator(orc):
     m = orc.Mesh.from_arrays(xyz, tri, ts, [1], [1], [0], [-1])
     assert m.volume(0) == pytest.approx(48.0, rel=1e-14)
     assert m.euler(0) == 2 and m.open_edges(0) == 0
+
+
+def groove_profile(R, rch, zf, zb, n_phi, g_in, g_out, depth):
+    """rounded_profile with the back-face channel g_in < rho < g_out, depth deep."""
+    pts = rounded_profile(R, rch, zf, zb, n_phi)[:-1]
+    return pts + [(g_out, zb), (g_out, zb + depth), (g_in, zb + depth), (g_in, zb), (0.0, zb)]
+
+
+@pytest.mark.parametrize("name", ["STRESS_SMALL", "STRESS_DET"])
+def test_stress_groove_and_flange(orc, name):
+    """The stress features against closed forms: the grooved crystal and active
+    volume are revolved profiles (exact faceted volumes), the flange ring is an
+    extruded polygon with holes -- volume h x (N-gon annulus - holes x M-gon),
+    genus 17 (the ring's opening plus 16 bolt holes) so chi = 2 - 2 * 17 = -32."""
+    d = getattr(W, name)
+    m = det(orc, d)
+    assert m.n_solid == 9
+    N, nphi = d.n_theta, d.n_phi
+    D, sep = d.D, d.sep_delta
+    zf = -(d.d[1] + d.d[4])
+    zb = zf - D[0]
+    gi, go = d.groove_r - d.groove_w / 2, d.groove_r + d.groove_w / 2
+    crystal = groove_profile(D[1], D[2], zf, zb, nphi, gi, go, d.groove_d)
+    active = groove_profile(D[1] - D[3], D[2] - D[3], zf - D[3], zb + sep, nphi, gi - sep, go + sep, d.groove_d)
+    # the z_slices side bands add vertices on straight segments only (no volume change)
+    assert m.volume(3) == pytest.approx(faceted_volume(crystal, N), rel=1e-10)
+    assert m.volume(4) == pytest.approx(faceted_volume(active, N), rel=1e-10)
+    c = 0.5 * N * math.sin(2 * math.pi / N)
+    assert m.volume(3) == pytest.approx(faceted_volume(rounded_profile(D[1], D[2], zf, zb, nphi), N)
+                                        - d.groove_d * c * (go * go - gi * gi), rel=1e-10)
+    M, nh = d.bolt_n_sides, d.n_bolt_holes
+    ring = c * (d.flange_r_out ** 2 - d.flange_r_in ** 2)
+    holes = nh * 0.5 * M * math.sin(2 * math.pi / M) * d.bolt_r ** 2
+    f = W.STRESS_FLANGE_SOLID
+    assert m.volume(f) == pytest.approx(d.flange_h * (ring - holes), rel=1e-10)
+    assert m.euler(f) == 2 - 2 * (nh + 1) == -32
+    for s in range(m.n_solid):
+        assert m.open_edges(s) == 0, s
+        if s != f:
+            assert m.euler(s) == 2, s
+    xyz, tri, ts, solids = m.arrays()
+    assert solids["parent"][f] == 1 and solids["material"][f] == W.MAT_CU
+    # the flange's top and bottom faces cover exactly the ring minus the holes
+    area = 0.0
+    for t in tri[ts == f]:
+        a, b, cc = xyz[t[0]], xyz[t[1]], xyz[t[2]]
+        n = np.cross(b - a, cc - a)
+        if abs(n[2]) > 1e-9 * np.linalg.norm(n):
+            area += 0.5 * abs(n[2])
+    assert area == pytest.approx(2 * (ring - holes), rel=1e-10)
+    # parity rule in the new features
+    tc = 2 * math.pi * 0.5 / nh                      # hole 0 centre angle
+    hx, hy = d.bolt_rc * math.cos(tc), d.bolt_rc * math.sin(tc)
+    zmid = d.flange_z_top - d.flange_h / 2
+    cases = [
+        ((hx, hy, zmid), 1),                                           # inside a bolt hole
+        ((d.flange_r_in + 0.2, 0.0, zmid), f),                         # flange material
+        ((d.flange_r_out + 0.2, 0.0, zmid), 1),                        # beyond the flange
+        ((d.groove_r, 0.0, zb + d.groove_d / 2), 1),                   # in the groove channel
+        ((d.groove_r, 0.0, zb + d.groove_d + sep / 2), 3),             # dead layer over the groove
+        ((d.groove_r, 0.0, zb + d.groove_d + 3 * sep), 4),             # active Ge above it
+        ((gi - sep / 2, 0.0, zb + d.groove_d / 2), 3),                 # dead wall of the groove
+    ]
+    dirs = [(0, 0, 1), (0.3, -0.5, 0.81), (-1, 0, 0.02), (0.1, 0.99, -0.05)]
+    for p, want in cases:
+        for dd in dirs:
+            n = np.array(dd, dtype=float)
+            n /= np.linalg.norm(n)
+            assert m.locate(p, n) == want, (p, dd)
