@@ -289,6 +289,26 @@ gadep_status build_bvh_host(const detmesh_mesh *m, gadep_bvh *out)
         r[2] = so.parent + 1;
         r[3] = roots[(size_t)s + 1];
     }
+    // planes of the stored (binary32) triangles, computed in FP64: the transport
+    // takes the distance of the hit it selected from these (see plane_t)
+    out->planes.assign(4 * (size_t)nt, 0.0f);
+    for (int32_t t = 0; t < nt; ++t) {
+        double v[3][3];
+        for (int k = 0; k < 3; ++k)
+            for (int c = 0; c < 3; ++c) v[k][c] = (double)m->xyz_f[3 * (size_t)g.tri[3 * (size_t)t + k] + c];
+        const double e1[3] = { v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2] };
+        const double e2[3] = { v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2] };
+        double n[3] = { e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0] };
+        const double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(len > 0.0)) return fail(GADEP_E_MESH, "bvh: degenerate triangle %d", t);
+        double w = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            n[c] /= len;
+            w += n[c] * (v[0][c] + v[1][c] + v[2][c]) / 3.0;
+        }
+        for (int c = 0; c < 3; ++c) out->planes[4 * (size_t)t + c] = (float)n[c];
+        out->planes[4 * (size_t)t + 3] = (float)w;
+    }
     out->geo = g;
     gadep_bvh_stats &stt = out->stats;
     stt.n_nodes = (int32_t)(out->nodes.size() / 16);

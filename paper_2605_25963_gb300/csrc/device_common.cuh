@@ -212,6 +212,23 @@ __device__ __forceinline__ void leaf_test_k(const float4 *__restrict__ tris, int
 
 struct TravStats { uint32_t nodes, tris, relocated; };
 
+// Distance of the hit on mesh triangle m, taken from the triangle's plane (unit
+// normal and offset computed in FP64 from the stored vertices) once the
+// watertight test has selected it.  On a sliver triangle the edge-function
+// distance loses accuracy as eps |v - o|^2 / width; the plane form keeps about
+// eps |o| / |cos|.  The selection (which triangle, entering or leaving) is not
+// touched; a plane distance that is not finite or not beyond t_min (a hit within
+// rounding of the ray start) keeps the edge-function value.
+__device__ __forceinline__ float plane_t(const float4 *__restrict__ planes, int m, float ox, float oy, float oz,
+                                         float dx, float dy, float dz, float t_edge, float t_min)
+{
+    const float4 p = __ldg(planes + m);
+    const float dn = fmaf(p.x, dx, fmaf(p.y, dy, p.z * dz));
+    const float num = fmaf(-p.x, ox, fmaf(-p.y, oy, fmaf(-p.z, oz, p.w)));
+    const float t = num / dn;
+    return (isfinite(t) && t > t_min) ? t : t_edge;
+}
+
 // Child word of a node: >= 0 inner node index; < 0 leaf ~(first << 3 | count).
 constexpr int kSentinel = 0x7fffffff;
 
@@ -237,7 +254,8 @@ __device__ __forceinline__ void leaf_test(const float4 *__restrict__ tris, int r
 // lockstep instead of branching between them at every node.
 template <bool COUNT>
 __device__ __forceinline__ int traverse(const float4 *__restrict__ nodes,
-                                        const float4 *__restrict__ tris, int root, float ox, float oy,
+                                        const float4 *__restrict__ tris,
+                                        const float4 *__restrict__ planes, int root, float ox, float oy,
                                         float oz, float dx, float dy, float dz, float t_min,
                                         int exclude, float &t_hit, bool &entering, uint32_t &err,
                                         TravStats &st)
@@ -298,7 +316,13 @@ __device__ __forceinline__ int traverse(const float4 *__restrict__ nodes,
         }
     }
     if (COUNT) { st.nodes += nn; st.tris += nt; }
-    if (best >= 0) { t_hit = t_best; entering = ent; }
+    if (best >= 0) {
+        // direction back from its reciprocals, as the wavefront trace kernel does,
+        // so that both forms take the same distance
+        t_hit = plane_t(planes, __float_as_int(__ldg(&tris[3 * best + 1].w)), ox, oy, oz, __frcp_rn(ix),
+                        __frcp_rn(iy), __frcp_rn(iz), t_best, t_min);
+        entering = ent;
+    }
     return best;
 }
 

@@ -63,6 +63,7 @@ struct gadep_bvh {
     std::vector<float> nodes;            // 16 floats per node
     std::vector<float> tris;             // 12 floats per triangle slot (leaf order, per tree)
     std::vector<int32_t> tri_orig;       // triangle slot -> mesh triangle index
+    std::vector<float> planes;           // per mesh triangle: unit normal, offset n . centroid
     std::vector<int32_t> regions;        // 4 ints per region: material, active | (group + 1) << 1,
                                          // parent region, root node of the region's tree (-1 = none)
     int32_t root_all = -1;               // tree over every triangle
@@ -73,7 +74,8 @@ struct gadep_bvh {
     int wf_cache_slots = 0;
     bool wf_cache_busy = false;
     gadep_bvh_stats stats{};
-    void *d_nodes = nullptr, *d_tris = nullptr, *d_tri_orig = nullptr, *d_regions = nullptr;
+    void *d_nodes = nullptr, *d_tris = nullptr, *d_tri_orig = nullptr, *d_regions = nullptr,
+         *d_planes = nullptr;
 };
 
 namespace gadep {

@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsig
                 bool entering = false;
                 // region record: material slot, active | (group + 1) << 1, parent, tree root
                 int4 R = s_reg[region];
-                int hit = traverse<COUNT>(P.nodes, P.tris, R.w, ox, oy, oz, dx, dy, dz, t_cur, last_tri,
+                int hit = traverse<COUNT>(P.nodes, P.tris, P.planes, R.w, ox, oy, oz, dx, dy, dz, t_cur, last_tri,
                                           t_hit, entering, herr, ts);
                 if (hit < 0 && region != 0 && !(herr & ERR_STACK)) {
                     // Inside a solid every ray meets that solid's boundary, so the
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsig
                     // point computed in FP32 right at a surface).  Relocate by the
                     // nearest surface of the whole mesh and the nesting-tree rule;
                     // with no surface ahead it is outside every solid.
-                    hit = traverse<COUNT>(P.nodes, P.tris, P.root_all, ox, oy, oz, dx, dy, dz, t_cur, last_tri,
+                    hit = traverse<COUNT>(P.nodes, P.tris, P.planes, P.root_all, ox, oy, oz, dx, dy, dz, t_cur, last_tri,
                                           t_hit, entering, herr, ts);
                     if (COUNT) ts.relocated++;
                     if (hit < 0) {
@@ -337,7 +337,8 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsig
 // One query per thread.  region[i] (0 = world, s + 1 = solid s) selects that
 // region's tree; without regions, or for an out-of-range id, the tree over every
 // triangle is used.
-__global__ void nearest_hit_kernel(const float4 *nodes, const float4 *tris, const int32_t *region_roots,
+__global__ void nearest_hit_kernel(const float4 *nodes, const float4 *tris, const float4 *planes,
+                                   const int32_t *region_roots,
                                    int32_t n_region, int32_t root_all, const int32_t *regions,
                                    const float *rays, long long n, float *t_out, int32_t *tri_out,
                                    int32_t *ent_out)
@@ -355,7 +356,8 @@ __global__ void nearest_hit_kernel(const float4 *nodes, const float4 *tris, cons
     bool ent = false;
     uint32_t err = 0;
     TravStats st{ 0, 0 };
-    const int hit = traverse<false>(nodes, tris, root, r[0], r[1], r[2], r[4], r[5], r[6], r[3], ex, t, ent, err, st);
+    const int hit = traverse<false>(nodes, tris, planes, root, r[0], r[1], r[2], r[4], r[5], r[6], r[3], ex, t, ent,
+                                    err, st);
     t_out[i] = hit >= 0 ? t : INFINITY;
     tri_out[i] = hit >= 0 ? __float_as_int(__ldg(&tris[3 * hit + 1].w)) : -1;
     ent_out[i] = hit >= 0 ? (ent ? 1 : 0) : (err ? -2 : -1);
@@ -430,6 +432,7 @@ gadep_status upload_bvh(gadep_bvh *b)
     gadep_status st;
     if ((st = dalloc((float **)&b->d_nodes, b->nodes.size(), "bvh nodes")) != GADEP_OK) return st;
     if ((st = dalloc((float **)&b->d_tris, b->tris.size(), "bvh triangles")) != GADEP_OK) return st;
+    if ((st = dalloc((float **)&b->d_planes, b->planes.size(), "bvh planes")) != GADEP_OK) return st;
     const size_t nr = b->regions.size() / 4;
     std::vector<int32_t> roots(nr);
     for (size_t r = 0; r < nr; ++r) roots[r] = b->regions[4 * r + 3];
@@ -437,6 +440,7 @@ gadep_status upload_bvh(gadep_bvh *b)
     cudaError_t e;
     if ((e = cudaMemcpy(b->d_nodes, b->nodes.data(), b->nodes.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(b->d_tris, b->tris.data(), b->tris.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_planes, b->planes.data(), b->planes.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(b->d_regions, roots.data(), nr * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "gadep_bvh_build: upload");
     return GADEP_OK;
@@ -444,14 +448,15 @@ gadep_status upload_bvh(gadep_bvh *b)
 
 void free_bvh_device(gadep_bvh *b)
 {
-    if (!b->d_nodes && !b->d_tris && !b->d_regions) return;
+    if (!b->d_nodes && !b->d_tris && !b->d_regions && !b->d_planes) return;
     DeviceGuard g(b->device);
     wavefront_destroy(b->wf_cache);
     b->wf_cache = nullptr;
     cudaFree(b->d_nodes);
     cudaFree(b->d_tris);
     cudaFree(b->d_regions);
-    b->d_nodes = b->d_tris = b->d_regions = nullptr;
+    cudaFree(b->d_planes);
+    b->d_nodes = b->d_tris = b->d_regions = b->d_planes = nullptr;
 }
 
 }  // namespace gadep
@@ -577,7 +582,8 @@ extern "C" gadep_status gadep_nearest_hit(const gadep_bvh *b, const float *rays,
     const int threads = 128;
     const long long blocks = (n + threads - 1) / threads;
     gadep::dev::nearest_hit_kernel<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(
-        (const float4 *)b->d_nodes, (const float4 *)b->d_tris, (const int32_t *)b->d_regions,
+        (const float4 *)b->d_nodes, (const float4 *)b->d_tris, (const float4 *)b->d_planes,
+        (const int32_t *)b->d_regions,
         (int32_t)(b->regions.size() / 4), b->root_all, regions, rays, n, t_out, tri_out, entering_out);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GADEP_OK : gadep::cuda_fail(e, "gadep_nearest_hit");
@@ -810,6 +816,7 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
     dev::Params &P = p->P;
     P.nodes = (const float4 *)b->d_nodes;
     P.tris = (const float4 *)b->d_tris;
+    P.planes = (const float4 *)b->d_planes;
     P.xs = p->d_xs;
     P.regions = p->d_regions;
     P.inst = p->d_inst;
@@ -1287,6 +1294,7 @@ extern "C" gadep_status gadep_run_noalloc(const gadep_bvh *b, const gadep_materi
     dev::Params P{};
     P.nodes = (const float4 *)b->d_nodes;
     P.tris = (const float4 *)b->d_tris;
+    P.planes = (const float4 *)b->d_planes;
     P.xs = S->xs;
     P.regions = S->regions;
     P.inst = &S->inst;

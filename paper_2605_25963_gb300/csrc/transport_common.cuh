@@ -35,6 +35,7 @@ struct TallyDev {
 struct Params {
     const float4 *nodes;
     const float4 *tris;
+    const float4 *planes;             // per mesh triangle: unit normal, offset
     const float4 *xs;                 // [n_mat][n_grid] (pe, compton, pair, 0), mm^-1
     const int4 *regions;              // (material slot or -1, active, group, parent)
     const InstDev *inst;

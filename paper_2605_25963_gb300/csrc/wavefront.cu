@@ -605,6 +605,7 @@ constexpr int kFetchThreshold = 20;   // refill lanes when fewer are still trave
 template <bool COUNT>
 __global__ void __launch_bounds__(256, 5) trace_kernel(const float4 *__restrict__ nodes,
                                                     const float4 *__restrict__ tris,
+                                                    const float4 *__restrict__ planes,
                                                     const int4 *__restrict__ regions, int n_region, State S,
                                                     int cur, unsigned long long *counters)
 {
@@ -715,8 +716,12 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const float4 *__restrict_
             }
             if (node == kSentinel) {
                 Hit h;
-                h.t = best >= 0 ? t_best : INFINITY;
                 h.tri = best >= 0 ? __float_as_int(__ldg(&tris[3 * best + 1].w)) : -1;
+                // the direction back from its reciprocals: the plane distance only
+                // needs it to a few ulp
+                h.t = best >= 0 ? plane_t(planes, h.tri, ox, oy, oz, __frcp_rn(ix), __frcp_rn(iy), __frcp_rn(iz), t_best,
+                                          t_min)
+                                : INFINITY;
                 h.region = best >= 0 ? __float_as_int(__ldg(&tris[3 * best].w)) : 0;
                 h.entering = best >= 0 ? (ent ? 1 : 0) : ((err & ERR_STACK) ? -2 : 0);
                 S.hit[qidx] = h;
@@ -803,7 +808,7 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
                     // Inside a solid every ray meets its boundary, so the photon sits a
                     // rounding error past it: relocate by the nearest surface of the
                     // whole mesh; with none ahead it is outside every solid.
-                    const int k = traverse<COUNT>(P.nodes, P.tris, P.root_all, ry.o.x, ry.o.y, ry.o.z, ry.d.x,
+                    const int k = traverse<COUNT>(P.nodes, P.tris, P.planes, P.root_all, ry.o.x, ry.o.y, ry.o.z, ry.d.x,
                                                   ry.d.y, ry.d.z, ry.o.w, last_tri, t_hit, entering, herr, ts);
                     if (COUNT) ts.relocated++;
                     if (k < 0) {
@@ -1149,10 +1154,10 @@ gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P0, bool grad
         T.after(KK_SORT, s);
         T.before(s);
         if (count)
-            wf::trace_kernel<true><<<w->trace_grid, 256, 0, s>>>(P.nodes, P.tris, P.regions, P.n_region, S, cur,
+            wf::trace_kernel<true><<<w->trace_grid, 256, 0, s>>>(P.nodes, P.tris, P.planes, P.regions, P.n_region, S, cur,
                                                                   counters);
         else
-            wf::trace_kernel<false><<<w->trace_grid, 256, 0, s>>>(P.nodes, P.tris, P.regions, P.n_region, S, cur,
+            wf::trace_kernel<false><<<w->trace_grid, 256, 0, s>>>(P.nodes, P.tris, P.planes, P.regions, P.n_region, S, cur,
                                                                    counters);
         T.after(KK_TRACE, s);
         T.before(s);
