@@ -168,6 +168,9 @@ def measure_forms(dev, scale=1.0):
     gradient: coax detector + water prism volume source, 4 energies x 5e7
     histories: plain runs vs the score-accumulating kernels (dFEPE/ds for 4
     density groups); also against central finite differences (1 + 2 x 4 runs).
+    stress: the gradient geometry at 1024 segments with a contact groove and a
+    bolted flange (~1e6 triangles), 8 energies x 1.25e8 histories: per-instance
+    runs vs one batched plan, plain and with gradients.
     """
     import torch
     from paper_2605_25963_gb300 import api, batch
@@ -222,6 +225,38 @@ def measure_forms(dev, scale=1.0):
     out["gradient"] = {"histories": n4 * len(items4), "plain_s": t_p, "grad_s": t_g,
                        "grad_vs_plain": t_p / t_g, "grad_vs_central_fd": (1 + 2 * 4) * t_p / t_g,
                        "per_energy": dict(zip([str(E) for E in W.GRAD_ENERGIES], grads))}
+    # ---- stress: ~1e6-triangle mesh, 8 energies, batched and with gradients ----
+    t0 = time.perf_counter()
+    m5 = api.detmesh_build(W.STRESS_DET)
+    t_mesh5 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b5 = api.gadep_bvh_build(m5, dev)
+    t_bvh5 = time.perf_counter() - t0
+    n5 = max(1, int(W.STRESS_HISTORIES * scale))
+    items5 = [(E, W.STRESS_SOURCE, n5, i, [1, 1, 1, 1]) for i, E in enumerate(W.STRESS_ENERGIES)]
+    total5 = n5 * len(items5)
+    t_p5, _ = batch.time_plain(b5, mats, items5)
+
+    def one_plan(grad):
+        p = api.Plan(b5, mats, api.make_instances(items5), api.make_opts(n_group=4 if grad else 0), grad=grad)
+        p.launch()                                   # warm-up (slot buffers, caches)
+        torch.cuda.synchronize()
+        a5, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a5.record()
+        p.launch()
+        e5.record()
+        torch.cuda.synchronize()
+        return a5.elapsed_time(e5) / 1e3, p.results(want_spectra=False)
+
+    t_b5, (rb5, _, _, _) = one_plan(False)
+    t_g5, (rg5, _, dg5, _) = one_plan(True)
+    out["stress"] = {"triangles": int(b5.stats()["n_tri"]), "mesh_build_s": round(t_mesh5, 3),
+                     "bvh_build_s": round(t_bvh5, 3), "instances": len(items5), "histories": total5,
+                     "plain_hist_per_s": total5 / t_p5, "batched_hist_per_s": total5 / t_b5,
+                     "batched_grad_hist_per_s": total5 / t_g5, "batched_vs_plain": t_p5 / t_b5,
+                     "batched_grad_vs_plain": t_p5 / t_g5,
+                     "fepe": [r["fepe"] for r in rg5], "dfepe_first": [float(x) for x in dg5[0]],
+                     "n_err": sum(r["n_err"] for r in rb5) + sum(r["n_err"] for r in rg5)}
     return out
 
 
@@ -344,7 +379,7 @@ def main():
     for p in plans:
         res, _, _, _ = p.results(want_spectra=False, raise_device_errors=False)
         fepe.append({"E_keV": None, "fepe": res[0]["fepe"], "sigma": res[0]["sigma"], "n_err": res[0]["n_err"],
-                     "dev_err": res[0]["dev_err"], "segments": res[0]["n_segments"]})
+                     "dev_err": res[0]["dev_err"], "segments": res[0]["n_segments"], "culled": res[0]["n_culled"]})
     for f, E in zip(fepe, cfg["energies"]):
         f["E_keV"] = E
 
@@ -382,7 +417,8 @@ def main():
         xs_bytes = 3 * 1000 * 16            # staged tables of Ge, Al, Cu
         n_region = len(mesh.arrays()[3]) + 1
         h2d = len(plans) * (xs_bytes + 16 * n_region + 96 + 8)   # tables, regions, instance, prefix
-        d2h = len(plans) * (opts.n_bins * 4 + 216 + 32)
+        # spectrum, the tally copies (256 stripes of 224 bytes for one instance), work counters
+        d2h = len(plans) * (opts.n_bins * 4 + 256 * 224 + 32)
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
@@ -432,6 +468,8 @@ def main():
             "gpu_launches": sum(nl for nl, _ in kstats.values()),
             "kernels": kernels,
             "clocks": clocks,
+            "hits_only": {"value": sum(n - f["culled"] for f in fepe) * world * args.steps / (total_ms / 1e3),
+                          "unit": UNIT, "note": "histories whose first ray reaches the scene box"},
             "fepe": fepe,
             "forms": forms,
         }

@@ -251,6 +251,7 @@ void gadep_opts_default(gadep_opts *o);
 typedef struct {
     uint64_t n_hist, n_fep, n_zero, n_over, n_err;
     uint64_t n_segments, n_interactions;
+    uint64_t n_culled;        /* histories born in the world whose first ray misses every solid's box */
     double   fepe, sigma;
     double   sum_dep_active, sum_dep_all, sum_esc;
     uint32_t dev_err;
@@ -275,7 +276,7 @@ gadep_status gadep_run(const gadep_bvh *b, const gadep_materials *mat, const gad
  * It computes the same histories as gadep_run with the same arguments (n_trace 0)
  * and returns the same result.
  * Scratch: instead of allocating, the call keeps the staged tables, region table,
- * instance record, tallies and work counter in one fixed device array of 345,456
+ * instance record, tallies and work counter in one fixed device array of 345,472
  * bytes (337 KiB) that every GPU loading the library holds until the process exits.
  * Limits (GADEP_E_INVAL beyond them): at most 63 solids, and (materials with
  * non-zero tables used by the mesh) x n_grid <= 12288, n_grid <= 12288.

@@ -81,7 +81,8 @@ class gadep_opts(C.Structure):
 class gadep_result(C.Structure):
     _fields_ = [("n_hist", C.c_uint64), ("n_fep", C.c_uint64), ("n_zero", C.c_uint64),
                 ("n_over", C.c_uint64), ("n_err", C.c_uint64), ("n_segments", C.c_uint64),
-                ("n_interactions", C.c_uint64), ("fepe", C.c_double), ("sigma", C.c_double),
+                ("n_interactions", C.c_uint64), ("n_culled", C.c_uint64), ("fepe", C.c_double),
+                ("sigma", C.c_double),
                 ("sum_dep_active", C.c_double), ("sum_dep_all", C.c_double), ("sum_esc", C.c_double),
                 ("dev_err", C.c_uint32)]
 

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsig
                     // Born in the world and aimed away from every solid: the one
                     // segment of this history escapes with nothing deposited.  It
                     // ends here so the lane can take the next history at once.
-                    acc.hist++; acc.zero++; acc.seg++;
+                    acc.hist++; acc.zero++; acc.seg++; acc.culled++;
                     acc.esc += E0;
                     if (g_hist < P.n_trace) P.edep_trace[g_hist] = 0.0f;
                 } else {
@@ -921,6 +921,7 @@ gadep_status plan_results(gadep_plan *p, uint32_t *spectra_host, gadep_result *r
             dev::TallyDev &t = T[i];
             t.n_hist += a.n_hist; t.n_fep += a.n_fep; t.n_zero += a.n_zero; t.n_over += a.n_over;
             t.n_err += a.n_err; t.n_segments += a.n_segments; t.n_interactions += a.n_interactions;
+            t.n_culled += a.n_culled;
             t.err_bits |= a.err_bits;
             t.sum_dep_active += a.sum_dep_active; t.sum_dep_all += a.sum_dep_all; t.sum_esc += a.sum_esc;
             for (int g2 = 0; g2 < GADEP_MAX_GROUPS; ++g2) {
@@ -936,7 +937,7 @@ gadep_status plan_results(gadep_plan *p, uint32_t *spectra_host, gadep_result *r
             gadep_result &r = res[i];
             std::memset(&r, 0, sizeof(r));
             r.n_hist = t.n_hist; r.n_fep = t.n_fep; r.n_zero = t.n_zero; r.n_over = t.n_over; r.n_err = t.n_err;
-            r.n_segments = t.n_segments; r.n_interactions = t.n_interactions;
+            r.n_segments = t.n_segments; r.n_interactions = t.n_interactions; r.n_culled = t.n_culled;
             r.fepe = t.n_hist ? (double)t.n_fep / (double)t.n_hist : 0.0;
             r.sigma = t.n_hist ? std::sqrt(r.fepe * (1.0 - r.fepe) / (double)t.n_hist) : 0.0;
             r.sum_dep_active = t.sum_dep_active; r.sum_dep_all = t.sum_dep_all; r.sum_esc = t.sum_esc;
@@ -1131,8 +1132,8 @@ struct __align__(16) Layout {
 }  // namespace noalloc
 }  // namespace gadep
 
-// 345,456 bytes (337 KiB) on every device that loads the library.
-static_assert(sizeof(gadep::noalloc::Layout) == 345456, "scratch size stated in gadep.h");
+// 345,472 bytes (337 KiB) on every device that loads the library.
+static_assert(sizeof(gadep::noalloc::Layout) == 345472, "scratch size stated in gadep.h");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(gadep::noalloc::Layout)];
 
 namespace gadep {

@@ -26,7 +26,7 @@ struct InstDev {
 };
 
 struct TallyDev {
-    unsigned long long n_hist, n_fep, n_zero, n_over, n_err, n_segments, n_interactions;
+    unsigned long long n_hist, n_fep, n_zero, n_over, n_err, n_segments, n_interactions, n_culled;
     unsigned long long err_bits;
     double sum_dep_active, sum_dep_all, sum_esc;
     double fep_score[GADEP_MAX_GROUPS], fep_score_sq[GADEP_MAX_GROUPS];
@@ -77,12 +77,12 @@ __device__ __forceinline__ bool ray_hits_box(const float lo[3], const float hi[3
 template <bool GRAD>
 struct Acc {
     int inst;
-    uint32_t hist, fep, zero, over, err, seg, inter, errbits;
+    uint32_t hist, fep, zero, over, err, seg, inter, errbits, culled;
     float dep, dep_all, esc;
     double score[GRAD ? 4 : 1], score2[GRAD ? 4 : 1];
     __device__ void reset(int i)
     {
-        inst = i; hist = fep = zero = over = err = seg = inter = errbits = 0u;
+        inst = i; hist = fep = zero = over = err = seg = inter = errbits = culled = 0u;
         dep = dep_all = esc = 0.0f;
 #pragma unroll
         for (int g = 0; g < (GRAD ? 4 : 1); ++g) { score[g] = 0.0; score2[g] = 0.0; }
@@ -98,6 +98,7 @@ struct Acc {
         if (err) { atomicAdd(&t.n_err, (unsigned long long)err); atomicOr(&t.err_bits, (unsigned long long)errbits); }
         atomicAdd(&t.n_segments, (unsigned long long)seg);
         atomicAdd(&t.n_interactions, (unsigned long long)inter);
+        if (culled) atomicAdd(&t.n_culled, (unsigned long long)culled);
         atomicAdd(&t.sum_dep_active, (double)dep);
         atomicAdd(&t.sum_dep_all, (double)dep_all);
         atomicAdd(&t.sum_esc, (double)esc);
@@ -140,6 +141,7 @@ __device__ void flush_warp(const Acc<GRAD> &a, TallyDev *T)
     const uint32_t errbits = __reduce_or_sync(0xffffffffu, a.errbits);
     const uint32_t seg = __reduce_add_sync(0xffffffffu, a.seg);
     const uint32_t inter = __reduce_add_sync(0xffffffffu, a.inter);
+    const uint32_t culled = __reduce_add_sync(0xffffffffu, a.culled);
     const double dep = warp_sum((double)a.dep), dep_all = warp_sum((double)a.dep_all),
                  esc = warp_sum((double)a.esc);
     double sc[4] = { 0, 0, 0, 0 }, sc2[4] = { 0, 0, 0, 0 };
@@ -156,6 +158,7 @@ __device__ void flush_warp(const Acc<GRAD> &a, TallyDev *T)
         if (err) { atomicAdd(&t.n_err, (unsigned long long)err); atomicOr(&t.err_bits, (unsigned long long)errbits); }
         atomicAdd(&t.n_segments, (unsigned long long)seg);
         atomicAdd(&t.n_interactions, (unsigned long long)inter);
+        if (culled) atomicAdd(&t.n_culled, (unsigned long long)culled);
         atomicAdd(&t.sum_dep_active, dep);
         atomicAdd(&t.sum_dep_all, dep_all);
         atomicAdd(&t.sum_esc, esc);

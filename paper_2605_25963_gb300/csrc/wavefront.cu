@@ -141,7 +141,8 @@ struct Words {
 // in every launch, so per-thread accumulators would flush constantly.
 struct STally {
     unsigned int hist, fep, zero, over, err, seg, inter, errbits;
-    float dep, dep_all, esc, pad;
+    float dep, dep_all, esc;
+    unsigned int culled;
 };
 
 template <bool GRAD>
@@ -154,7 +155,7 @@ struct BlockTally {
         t = reinterpret_cast<STally *>(smem);
         sc = reinterpret_cast<double *>(t + n_inst);
         n = n_inst;
-        for (int i = threadIdx.x; i < n_inst; i += blockDim.x) t[i] = STally{ 0, 0, 0, 0, 0, 0, 0, 0, 0.f, 0.f, 0.f, 0.f };
+        for (int i = threadIdx.x; i < n_inst; i += blockDim.x) t[i] = STally{ 0, 0, 0, 0, 0, 0, 0, 0, 0.f, 0.f, 0.f, 0u };
         if (GRAD)
             for (int i = threadIdx.x; i < 8 * n_inst; i += blockDim.x) sc[i] = 0.0;
     }
@@ -192,6 +193,7 @@ struct BlockTally {
         atomicAdd(&s.hist, n);
         atomicAdd(&s.seg, n);
         atomicAdd(&s.zero, n);
+        atomicAdd(&s.culled, n);
         atomicAdd(&s.esc, (float)n * E0);
     }
     __device__ void flush(TallyDev *T)
@@ -208,6 +210,7 @@ struct BlockTally {
             if (s.err) { atomicAdd(&d.n_err, (unsigned long long)s.err); atomicOr(&d.err_bits, (unsigned long long)s.errbits); }
             if (s.seg) atomicAdd(&d.n_segments, (unsigned long long)s.seg);
             if (s.inter) atomicAdd(&d.n_interactions, (unsigned long long)s.inter);
+            if (s.culled) atomicAdd(&d.n_culled, (unsigned long long)s.culled);
             atomicAdd(&d.sum_dep_active, (double)s.dep);
             atomicAdd(&d.sum_dep_all, (double)s.dep_all);
             atomicAdd(&d.sum_esc, (double)s.esc);
