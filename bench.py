@@ -52,6 +52,12 @@ def workload_config(name, n_hist):
                     desc="coax_p: p-type coaxial HPGe (R 30.5 L 62, bore 5x48, 0.7 mm dead layer, 0.3 um contact, "
                          "Al endcap, Cu holder), 128 segments (13824 triangles), point source 25 mm, "
                          "59.5/122/662/1332 keV")
+    if name == "table4":
+        return dict(det=W.DET2, src=W.TABLE4_SOURCE, energies=W.TABLE4_ENERGIES, n_hist=n_hist or 100_000_000,
+                    desc="table4: detector #2 of Table 1 (crystal 68.1 x 63.3, hole 10.1 x 50.2, 0.7 mm / 0.3 um "
+                         "dead layers) in the coax housing, N_theta 32, N_phi 10, point source 250 mm above "
+                         "the window, the 13 Table 3 energies 59.54-1408.02 keV",
+                    paper_s={"1e7": 11.96, "1e8": 66.08})
     if name == "bare":
         return dict(det=W.BARE_CYLINDER, src=W.BARE_POINT_100, energies=(662.0,), n_hist=n_hist or 1_000_000,
                     desc="bare Ge cylinder R 30 L 60, 48 segments (192 triangles), point source 100 mm, 662 keV")
@@ -281,7 +287,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gadep", choices=["gadep", "reference"])
-    ap.add_argument("--workload", default="coax", choices=["coax", "bare"])
+    ap.add_argument("--workload", default="coax", choices=["coax", "bare", "table4"])
     ap.add_argument("--hist", type=int, default=0, help="histories per energy (default: the workload's)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
@@ -452,6 +458,7 @@ def main():
             "config": {"workload": cfg["desc"], "n_hist_per_energy": n, "energies_keV": list(cfg["energies"]),
                        "seed": 1, "triangles": bvh.stats()["n_tri"], "grid": g, "block": blk,
                        "smem_bytes": smem, "l2": "flushed between steps (512 MB write)",
+                       "paper_rtx4090_s_all_energies": cfg.get("paper_s"),
                        "mesh_build_s": round(t_mesh, 4), "bvh_build_s": round(t_bvh, 4)},
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved_tflops, "peak": peak_tflops,
                          "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,

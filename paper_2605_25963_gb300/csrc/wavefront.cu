@@ -3,9 +3,9 @@
 //
 // Photons live in device-memory slots.  One iteration runs five kernels on the
 // stream, with no host round trip between them:
-//   spawn    free slots take births from the pending ring (an index map: the
-//            i-th free slot gets the i-th pending history) and join the trace
-//            queue after the survivors of the previous iteration;
+//   spawn    free slots (popped from a stack) take births from the pending ring
+//            (an index map: the i-th popped slot gets the i-th pending history)
+//            and join the trace queue after the survivors of the previous iteration;
 //   sort     counting sort of the queue by (region, direction class), from the
 //            key histogram that physics and spawn accumulate, so that a warp
 //            traverses one region's tree with rays of similar direction;
@@ -16,7 +16,7 @@
 //   physics  one thread per queued photon applies the segment: free flight,
 //            boundary crossing (nesting-tree rule), interaction or escape, and the
 //            end-of-history tally; survivors go to the next trace queue, finished
-//            slots to the next free list (one global atomic per list, block and pass);
+//            slots back onto the free stack (one global atomic per list, block and pass);
 //   gen      history ids in chunks: source point and direction of each id;
 //            histories born in the world whose first ray misses the scene box end
 //            here with nothing deposited, the others join the pending ring;
@@ -232,7 +232,7 @@ __host__ __device__ constexpr size_t block_tally_bytes(int n_inst)
 struct Ctrl {
     // counters
     unsigned int q_count[2];       // trace queue sizes, by iteration parity
-    unsigned int dead_count[2];    // free-slot lists, by iteration parity
+    unsigned int free_top;         // free slots: a stack, free_slots[0 .. free_top)
     unsigned int trace_head;       // chunk cursor of the trace kernel
     unsigned int iter;
     unsigned long long work;       // next history index handed to gen (may run past the total)
@@ -240,7 +240,7 @@ struct Ctrl {
     unsigned long long pend_head;  // births consumed so far
     unsigned long long pend_tail;  // births produced so far
     // plan of the next spawn and gen, written by ctrl only
-    unsigned int sp_n_dead, sp_filled, sp_q0, done;   // done: 1 finished, 2 iteration bound reached
+    unsigned int sp_free, sp_filled, sp_q0, done;     // done: 1 finished, 2 iteration bound reached
     unsigned long long sp_head;
     unsigned long long gen_live;   // ring entries left once the next spawn has run
     unsigned long long max_iter;
@@ -258,7 +258,7 @@ struct State {
     unsigned int *fill;            // bucket cursors of the sort
     unsigned int *base;            // bucket starts of the sort
     unsigned int *qsort;           // the queue in key order: what trace and physics walk
-    unsigned int *dead[2];
+    unsigned int *free_slots;      // stack of free slots: spawn pops, physics pushes
     unsigned long long *pend;      // ring of global history indices waiting for a slot
     unsigned long long pend_mask;  // ring size - 1 (a power of two)
     unsigned long long gen_target; // ring fill at which gen stops claiming ids
@@ -319,7 +319,7 @@ __device__ __forceinline__ void sample_birth(const InstDev &I, Words &r, uint32_
 __global__ void init_kernel(State S, unsigned long long max_iter)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < S.slots) S.dead[0][i] = (unsigned int)i;
+    if (i < S.slots) S.free_slots[i] = (unsigned int)i;
     for (int k = i; k < kMaxKeys; k += gridDim.x * blockDim.x) {
         S.hist[0][k] = 0u;
         S.hist[1][k] = 0u;
@@ -328,13 +328,12 @@ __global__ void init_kernel(State S, unsigned long long max_iter)
     if (i == 0) {
         Ctrl &c = *S.ctrl;
         c.q_count[0] = c.q_count[1] = 0;
-        c.dead_count[0] = (unsigned int)S.slots;
-        c.dead_count[1] = 0;
+        c.free_top = (unsigned int)S.slots;
         c.trace_head = 0;
         c.iter = 0;
         c.work = 0;
         c.pend_add = c.pend_head = c.pend_tail = 0;
-        c.sp_n_dead = c.sp_filled = c.sp_q0 = c.done = 0;
+        c.sp_free = c.sp_filled = c.sp_q0 = c.done = 0;
         c.sp_head = 0;
         c.gen_live = 0;
         c.max_iter = max_iter;
@@ -358,16 +357,17 @@ __global__ void ctrl_kernel(State S, int cur, unsigned long long total)
     c.pend_head += c.sp_filled;
     const unsigned long long work = c.work < total ? c.work : total;
     c.work = work;
-    const unsigned int n_alive = c.q_count[nxt], n_dead = c.dead_count[nxt];
+    const unsigned int n_alive = c.q_count[nxt], n_free = c.free_top;
     const unsigned long long avail = c.pend_tail - c.pend_head;
-    const unsigned int filled = (unsigned int)(avail < n_dead ? avail : n_dead);
-    c.sp_n_dead = n_dead;
+    const unsigned int filled = (unsigned int)(avail < n_free ? avail : n_free);
+    // the next spawn pops the top `filled` free slots; physics then pushes above them
+    c.sp_free = n_free - filled;
     c.sp_filled = filled;
     c.sp_q0 = n_alive;
     c.sp_head = c.pend_head;
+    c.free_top = n_free - filled;
     c.q_count[nxt] = n_alive + filled;
     c.q_count[cur] = 0;
-    c.dead_count[cur] = n_dead - filled;
     c.trace_head = 0;
     c.gen_live = avail - filled;
     c.iter++;
@@ -491,8 +491,8 @@ template <bool GRAD>
 __global__ void __launch_bounds__(256) spawn_kernel(const Params P, State S, int cur)
 {
     const Ctrl &c = *S.ctrl;
-    const unsigned int n_dead = c.sp_n_dead, filled = c.sp_filled, q0 = c.sp_q0;
-    if (n_dead == 0) return;
+    const unsigned int first = c.sp_free, filled = c.sp_filled, q0 = c.sp_q0;
+    if (filled == 0) return;
     const unsigned long long head = c.sp_head;
     const uint32_t k0 = P.key0, k1 = P.key1;
     const int n_keys = P.n_keys;
@@ -501,19 +501,13 @@ __global__ void __launch_bounds__(256) spawn_kernel(const Params P, State S, int
     __syncthreads();
     int inst = 0;
     const unsigned int stride = gridDim.x * blockDim.x;
-    for (unsigned int base = blockIdx.x * blockDim.x; base < n_dead; base += stride) {   // warp-uniform
+    for (unsigned int base = blockIdx.x * blockDim.x; base < filled; base += stride) {   // warp-uniform
         const unsigned int i = base + threadIdx.x;
-        bool born = false;
+        const bool born = i < filled;
         uint32_t key = 0;
-        if (i < n_dead) {
-            const unsigned int slot = S.dead[cur][i];
-            if (i >= filled) {
-                S.dead[cur ^ 1][i - filled] = slot;
-            } else {
-                key = spawn_one<GRAD>(P, S, cur, slot, S.pend[(head + i) & S.pend_mask], q0 + i, k0, k1, inst);
-                born = true;
-            }
-        }
+        if (born)
+            key = spawn_one<GRAD>(P, S, cur, S.free_slots[first + i], S.pend[(head + i) & S.pend_mask], q0 + i, k0,
+                                  k1, inst);
         warp_hist_add(born, key, s_hist);
     }
     __syncthreads();
@@ -976,7 +970,7 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
         __syncthreads();
         if (threadIdx.x == 0) {
             s_base[0] = s_cnt[0] ? atomicAdd(&S.ctrl->q_count[nxt], s_cnt[0]) : 0u;
-            s_base[1] = s_cnt[1] ? atomicAdd(&S.ctrl->dead_count[nxt], s_cnt[1]) : 0u;
+            s_base[1] = s_cnt[1] ? atomicAdd(&S.ctrl->free_top, s_cnt[1]) : 0u;
             s_cnt[0] = s_cnt[1] = 0;
         }
         __syncthreads();
@@ -984,7 +978,7 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
             S.queue[nxt][s_base[0] + oa] = slot;
             S.qkey[nxt][s_base[0] + oa] = key;
         }
-        if (finished) S.dead[nxt][s_base[1] + of] = slot;
+        if (finished) S.free_slots[s_base[1] + of] = slot;
         warp_hist_add(alive_slot, key, s_hist);
     }
     if (inter_acc) atomicAdd(&bt.t[inter_inst].inter, inter_acc);
@@ -1050,7 +1044,6 @@ gadep_status wavefront_create(int device, int slots, bool grad, WavefrontBuffers
     size_t o_qs = off; off = align_up(off + n * 4);
     size_t o_h = off; off = align_up(off + 4 * wf::kMaxKeys * 4);
     size_t o_d0 = off; off = align_up(off + n * 4);
-    size_t o_d1 = off; off = align_up(off + n * 4);
     size_t o_pend = off; off = align_up(off + ring * sizeof(unsigned long long));
     size_t o_ctrl = off; off = align_up(off + sizeof(wf::Ctrl));
     cudaError_t e = cudaMalloc(&w->block, off);
@@ -1080,8 +1073,7 @@ gadep_status wavefront_create(int device, int slots, bool grad, WavefrontBuffers
     w->S.hist[1] = w->S.hist[0] + wf::kMaxKeys;
     w->S.fill = w->S.hist[1] + wf::kMaxKeys;
     w->S.base = w->S.fill + wf::kMaxKeys;
-    w->S.dead[0] = (unsigned int *)(b + o_d0);
-    w->S.dead[1] = (unsigned int *)(b + o_d1);
+    w->S.free_slots = (unsigned int *)(b + o_d0);
     w->S.pend = (unsigned long long *)(b + o_pend);
     w->S.pend_mask = ring - 1;
     w->S.gen_target = target;

@@ -143,6 +143,17 @@ GRAD_ENERGIES = (59.5, 122.0, 662.0, 1332.0)
 GRAD_HISTORIES = 50_000_000
 GRAD_N_GROUP = 4
 
+# ---------------- Table 4 shape ----------------
+# Detector #2 of Table 1 (p-type, crystal 68.1 dia x 63.3, hole 10.1 dia x 50.2,
+# dead layers 0.7 mm / 0.3 um) in the coax_p housing, N_theta 32 and N_phi 10 (the
+# paper's defaults); front-edge rounding 3 mm (Table 1 gives none).  Point source
+# on the axis 250 mm above the endcap window; the 13 energies of Table 3.
+DET2 = Detector(kind=DET_COAX, d=COAX_D_EXT, D=(63.3, 34.05, 3.0, 0.7, 50.2, 5.05, 0.0003), n_theta=32, n_phi=10,
+                cup_rim_drop=10.0, sep_delta=1e-4)
+TABLE4_SOURCE = Source(kind=SRC_POINT, pos=(0.0, 0.0, 250.0))
+TABLE4_ENERGIES = (59.54, 81.00, 121.78, 244.70, 344.28, 356.02, 411.13, 443.97, 778.90, 964.06, 1112.09,
+                   1332.49, 1408.02)
+
 # ---------------- stress ----------------
 # The gradient workload's detector and volume source at 1024 segments per circle,
 # with a 2 x 1 mm contact groove on the crystal back face (centred at r = 8 mm)

@@ -43,7 +43,7 @@ def det_pair(orc, d):
 
 
 @pytest.mark.parametrize("name", ["BARE_CYLINDER", "COAX_P", "COAX_N", "BATCH_DET", "GRAD_DET", "STRESS_SMALL",
-                                  "STRESS_DET"])
+                                  "STRESS_DET", "DET2"])
 def test_detmesh_matches_oracle_surfaces(orc, name):
     d = getattr(W, name)
     m, o = det_pair(orc, d)

@@ -109,6 +109,19 @@ def test_volume_source_parity(orc, otab, mats):
         assert abs(r["fepe"] - ro.fepe) <= 3 * math.hypot(r["sigma"], ro.sigma)
 
 
+@pytest.mark.parametrize("E", [W.TABLE4_ENERGIES[0], W.TABLE4_ENERGIES[-1]])
+def test_table4_detector_parity(orc, otab, mats, E):
+    """Detector #2 of Table 1 with the point source 250 mm away: almost every
+    history misses the scene box and ends at birth on both sides."""
+    n = 2_000_000
+    r, spec, ro, same = compare_run(orc, otab, mats, "DET2", W.TABLE4_SOURCE, E, n, n)
+    assert r["n_err"] == 0 and ro.tally["n_err"] == 0 and ro.tally["n_parity_mismatch"] == 0
+    assert same.mean() >= 0.9999, same.mean()
+    assert abs(r["fepe"] - ro.fepe) <= 3 * math.hypot(r["sigma"], ro.sigma)
+    assert 0.98 < r["n_culled"] / n < 1.0
+    assert r["sum_dep_all"] + r["sum_esc"] == pytest.approx(n * E, rel=1e-6)
+
+
 def test_nearest_hit_matches_bruteforce(orc):
     """GPU traversal vs FP64 brute force over the same triangles (the oracle's own
     vertices rounded to binary32, the precision the GPU stores).  Distances agree
