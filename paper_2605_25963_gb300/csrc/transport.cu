@@ -630,6 +630,73 @@ extern "C" void gadep_plan_destroy(gadep_plan *p)
 
 namespace gadep {
 
+// Bounds of every solid seen from the world: the union of the world tree's root
+// child boxes (lo > hi when the world tree is empty).
+void scene_box(const gadep_bvh *b, float lo[3], float hi[3])
+{
+    for (int k = 0; k < 3; ++k) { lo[k] = 0.0f; hi[k] = -1.0f; }
+    if (b->regions[3] < 0) return;
+    const float *f = b->nodes.data() + (size_t)b->regions[3] * 16;
+    int32_t w[4];
+    std::memcpy(w, &f[12], 16);
+    for (int k = 0; k < 3; ++k) { lo[k] = INFINITY; hi[k] = -INFINITY; }
+    for (int c = 0; c < 2; ++c) {
+        if (w[c] < 0 && ((~w[c]) & 7) == 0) continue;  // empty leaf slot
+        const float clo[3] = { f[4 * c + 0], f[4 * c + 2], f[8 + 2 * c] };
+        const float chi[3] = { f[4 * c + 1], f[4 * c + 3], f[9 + 2 * c] };
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], clo[k]);
+            hi[k] = std::max(hi[k], chi[k]);
+        }
+    }
+}
+
+// Fraction of an instance's histories whose first ray reaches the scene box
+// (the rest end at birth): 1 for sources inside a solid; otherwise estimated
+// with 4096 directions on a Fibonacci spiral from the source point (a disk
+// source adds 16 points on its area).  Only the choice of transport form and
+// the number of photon slots depend on it.
+double hit_fraction(const dev::InstDev &d, const float lo[3], const float hi[3])
+{
+    if (d.birth_region != 0) return 1.0;
+    if (!(lo[0] <= hi[0])) return 0.0;
+    auto hits = [&](const double o[3], const double dir[3]) {
+        double t0 = 0.0, t1 = INFINITY;
+        for (int k = 0; k < 3; ++k) {
+            if (dir[k] == 0.0) {
+                if (o[k] < lo[k] || o[k] > hi[k]) return false;
+                continue;
+            }
+            double a = (lo[k] - o[k]) / dir[k], c = (hi[k] - o[k]) / dir[k];
+            if (a > c) std::swap(a, c);
+            t0 = std::max(t0, a);
+            t1 = std::min(t1, c);
+        }
+        return t0 <= t1;
+    };
+    if (d.src_kind == GADEP_SRC_PENCIL) {
+        const double o[3] = { d.px, d.py, d.pz }, dir[3] = { d.dx, d.dy, d.dz };
+        return hits(o, dir) ? 1.0 : 0.0;
+    }
+    const int n_dir = 4096, n_pos = d.src_kind == GADEP_SRC_DISK ? 16 : 1;
+    const double golden = 3.14159265358979323846 * (3.0 - std::sqrt(5.0));
+    long hit = 0;
+    for (int q = 0; q < n_pos; ++q) {
+        double o[3] = { d.px, d.py, d.pz };
+        if (n_pos > 1) {
+            const double r = d.radius * std::sqrt((q + 0.5) / n_pos), a = golden * q;
+            o[0] += r * std::cos(a);
+            o[1] += r * std::sin(a);
+        }
+        for (int i = 0; i < n_dir; ++i) {
+            const double z = 1.0 - (2.0 * i + 1.0) / n_dir, rr = std::sqrt(std::max(0.0, 1.0 - z * z));
+            const double dir[3] = { rr * std::cos(golden * i), rr * std::sin(golden * i), z };
+            hit += hits(o, dir);
+        }
+    }
+    return (double)hit / ((double)n_dir * n_pos);
+}
+
 gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t n_inst,
                          const gadep_instance *inst, const gadep_opts *opts, bool grad, bool count,
                          gadep_plan **out)
@@ -749,13 +816,25 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
     if (e != cudaSuccess || bps < 1) { gadep_plan_destroy(p); return fail(GADEP_E_CUDA, "plan: kernel does not fit on the device"); }
     if (opts->blocks_per_sm > 0) bps = std::min(bps, opts->blocks_per_sm);
     p->grid = n_sm * bps;
-    // form of the transport: AUTO takes the wavefront kernels for large runs
-    // (measured faster from a few million histories on) and the megakernel otherwise
+    // form of the transport.  AUTO takes the wavefront kernels when many photons
+    // reach the scene (measured faster from a few million histories on), and for
+    // very large runs of a distant source, whose histories mostly end at birth
+    // (gen culls them faster than the megakernel's lanes); the megakernel
+    // otherwise -- with few photons in flight the wavefront's ~0.1 ms per
+    // iteration dominates (measured: detector #2, source at 250 mm, 1e7 histories
+    // per energy 5x faster in the megakernel, 1e8 per energy 2.5x faster in the
+    // wavefront form)
+    float box_lo[3], box_hi[3];
+    scene_box(b, box_lo, box_hi);
+    double reaching = 0.0;   // histories expected to reach the scene
+    for (int32_t i = 0; i < n_inst; ++i) reaching += (double)inst[i].n_hist * hit_fraction(p->inst[i], box_lo, box_hi);
     int variant = opts->variant;
     const bool wf_ok = n_inst <= kWavefrontMaxInstances &&
                        wavefront_supports((int)(regions.size() / 4), (long long)b->geo.n_tri());
     if (variant == GADEP_VARIANT_AUTO)
-        variant = (total >= (1ull << 23) && wf_ok) ? GADEP_VARIANT_WAVEFRONT : GADEP_VARIANT_MEGA;
+        variant = wf_ok && ((total >= (1ull << 23) && reaching >= (double)(1u << 20)) || total >= (1ull << 26))
+                      ? GADEP_VARIANT_WAVEFRONT
+                      : GADEP_VARIANT_MEGA;
     if (variant == GADEP_VARIANT_WAVEFRONT && !wf_ok) {
         gadep_plan_destroy(p);
         return fail(GADEP_E_INVAL, "plan: the wavefront form takes at most %d instances, 256 regions and "
@@ -765,7 +844,7 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
         int slots = opts->wf_slots;
         if (slots <= 0) {
             slots = 1 << 20;
-            while (slots < (1 << 24) && (unsigned long long)slots * 8 <= total) slots <<= 1;
+            while (slots < (1 << 24) && (double)slots * 2.0 <= reaching) slots <<= 1;
         }
         gadep_bvh *bm = const_cast<gadep_bvh *>(b);
         {
@@ -845,23 +924,8 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
     P.chunk = opts->chunk > 0 ? opts->chunk : 256;
     P.n_stripes = p->n_stripes;
     P.root_all = b->root_all;
-    // scene bounds seen from the world = union of the world tree's root child boxes
-    for (int k = 0; k < 3; ++k) { P.root_lo[k] = 0.0f; P.root_hi[k] = -1.0f; }
-    if (b->regions[3] >= 0) {
-        const float *f = b->nodes.data() + (size_t)b->regions[3] * 16;
-        int32_t w[4];
-        std::memcpy(w, &f[12], 16);
-        for (int k = 0; k < 3; ++k) { P.root_lo[k] = INFINITY; P.root_hi[k] = -INFINITY; }
-        for (int c = 0; c < 2; ++c) {
-            if (w[c] < 0 && ((~w[c]) & 7) == 0) continue;  // empty leaf slot
-            const float lo[3] = { f[4 * c + 0], f[4 * c + 2], f[8 + 2 * c] };
-            const float hi[3] = { f[4 * c + 1], f[4 * c + 3], f[9 + 2 * c] };
-            for (int k = 0; k < 3; ++k) {
-                P.root_lo[k] = std::min(P.root_lo[k], lo[k]);
-                P.root_hi[k] = std::max(P.root_hi[k], hi[k]);
-            }
-        }
-    }
+    // scene bounds seen from the world (births outside it whose ray misses it end at once)
+    scene_box(b, P.root_lo, P.root_hi);
     *out = p;
     return GADEP_OK;
 }
@@ -1324,22 +1388,7 @@ extern "C" gadep_status gadep_run_noalloc(const gadep_bvh *b, const gadep_materi
     P.chunk = opts->chunk > 0 ? opts->chunk : 256;
     P.n_stripes = 1;                       // the one tally record of the scratch array
     P.root_all = b->root_all;
-    for (int k = 0; k < 3; ++k) { P.root_lo[k] = 0.0f; P.root_hi[k] = -1.0f; }
-    if (b->regions[3] >= 0) {
-        const float *f = b->nodes.data() + (size_t)b->regions[3] * 16;
-        int32_t w[4];
-        std::memcpy(w, &f[12], 16);
-        for (int k = 0; k < 3; ++k) { P.root_lo[k] = INFINITY; P.root_hi[k] = -INFINITY; }
-        for (int c = 0; c < 2; ++c) {
-            if (w[c] < 0 && ((~w[c]) & 7) == 0) continue;
-            const float lo[3] = { f[4 * c + 0], f[4 * c + 2], f[8 + 2 * c] };
-            const float hi[3] = { f[4 * c + 1], f[4 * c + 3], f[9 + 2 * c] };
-            for (int k = 0; k < 3; ++k) {
-                P.root_lo[k] = std::min(P.root_lo[k], lo[k]);
-                P.root_hi[k] = std::max(P.root_hi[k], hi[k]);
-            }
-        }
-    }
+    gadep::scene_box(b, P.root_lo, P.root_hi);
     if (n_hist > 0)
         dev::transport_kernel<false, false><<<n_sm * bps, block, smem, s>>>(P, S->counters);
     e = cudaGetLastError();
