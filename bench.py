@@ -191,26 +191,15 @@ def measure_forms(dev, scale=1.0):
     t_plain, _ = batch.time_plain(b3, mats, items)
     kw, table = batch.autotune(b3, mats, items)
     a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if kw.get("variant") == batch.WAVEFRONT:
-        runner = api.Plan(b3, mats, api.make_instances(items), api.make_opts(**kw))
-        runner.launch()
-        torch.cuda.synchronize()
-        a.record()
-        runner.launch()
-        e.record()
-        torch.cuda.synchronize()
-        res, _, _, _ = runner.results(want_spectra=False)
-        how = "wavefront plan"
-    else:
-        g = batch.GraphBatch(b3, mats, items, kw)
-        g.replay()
-        torch.cuda.synchronize()
-        a.record()
-        g.replay()
-        e.record()
-        torch.cuda.synchronize()
-        res, _, _, _ = g.results(want_spectra=False)
-        how = "megakernel replayed from a CUDA graph"
+    g = batch.GraphBatch(b3, mats, items, kw)
+    g.replay()
+    torch.cuda.synchronize()
+    a.record()
+    g.replay()
+    e.record()
+    torch.cuda.synchronize()
+    res, _, _, _ = g.results(want_spectra=False)
+    how = ("wavefront" if kw.get("variant") == batch.WAVEFRONT else "megakernel") + " plan replayed from a CUDA graph"
     t_batch = a.elapsed_time(e) / 1e3
     out["batched"] = {"instances": len(items), "histories": total, "plain_s": t_plain, "batched_s": t_batch,
                       "plain_hist_per_s": total / t_plain, "batched_hist_per_s": total / t_batch,

@@ -3,11 +3,13 @@
 The device side is a libgadep plan (``gadep_plan_*``): one work counter over the
 flattened history range of all instances feeds every warp, so instances with
 uneven history counts share the GPU without per-instance launch tails.  Two
-forms exist: the persistent megakernel (one kernel launch, which this module can
-capture in a CUDA graph and replay) and the wavefront kernels (photon slots in
-device memory, birth / trace / physics per iteration, driven from the host).
-``autotune`` times both forms and the megakernel's launch shapes on a
-scaled-down copy of the batch and keeps the fastest.
+forms exist: the persistent megakernel (one kernel launch) and the wavefront
+kernels (photon slots in device memory, iterations of spawn / sort / trace /
+physics / gen / ctrl repeated by a device-side WHILE node of a CUDA graph).
+Both launch without host synchronisation, so ``GraphBatch`` captures either in
+a CUDA graph and replays it.  ``autotune`` times both forms and the
+megakernel's launch shapes on a scaled-down copy of the batch and keeps the
+fastest.
 """
 from __future__ import annotations
 
@@ -19,13 +21,12 @@ MEGA, WAVEFRONT = 1, 2
 
 
 class GraphBatch:
-    """A megakernel plan whose launch is captured in a CUDA graph and replayed."""
+    """A plan (either form) whose launch is captured in a CUDA graph and replayed."""
 
     def __init__(self, bvh, mats, items, opts_kw=None, grad=False):
         import torch
         self.torch = torch
         kw = dict(opts_kw or {})
-        kw["variant"] = MEGA
         self.items = list(items)
         self.opts = api.make_opts(**kw)
         self.plan = api.Plan(bvh, mats, api.make_instances(self.items), self.opts, grad=grad)

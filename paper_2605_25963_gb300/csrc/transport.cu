@@ -975,6 +975,10 @@ gadep_status plan_results(gadep_plan *p, uint32_t *spectra_host, gadep_result *r
     if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, p->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "plan results");
+    if (p->wf) {
+        const gadep_status st = wavefront_check(p->wf, s);   // iteration bound of a graph-driven run
+        if (st != GADEP_OK) return st;
+    }
     if (counters) std::memcpy(counters, cnt, sizeof(cnt));
     // sum the per-block tally copies (integer counts exactly, FP64 sums in stripe order)
     std::vector<dev::TallyDev> T(p->n_inst);

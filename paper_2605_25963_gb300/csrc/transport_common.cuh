@@ -281,6 +281,7 @@ void wavefront_destroy(WavefrontBuffers *w);
 gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P, bool grad, bool count,
                            unsigned long long *counters, KernelTimer *timer, cudaStream_t s);
 int wavefront_trace_grid(const WavefrontBuffers *w);
+gadep_status wavefront_check(WavefrontBuffers *w, cudaStream_t s);
 // Whether the wavefront records can address the mesh (region and triangle ids
 // share one 32-bit word).
 bool wavefront_supports(int n_region, long long n_mesh_tri);

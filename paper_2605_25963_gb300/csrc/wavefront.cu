@@ -341,16 +341,10 @@ __global__ void init_kernel(State S, unsigned long long max_iter)
 }
 
 // ---------------------------------------------------------------- ctrl
-// Close iteration `cur` (spawn, trace, physics and gen have run) and plan the next.
-__global__ void ctrl_kernel(State S, int cur, unsigned long long total)
+// One step of the control block: close iteration `cur` (spawn, sort, trace,
+// physics and gen have run) and plan the next.
+__device__ __forceinline__ void ctrl_step(Ctrl &c, int cur, unsigned long long total)
 {
-    for (int k = threadIdx.x; k < kMaxKeys; k += blockDim.x) {
-        S.hist[cur][k] = 0u;        // the sort of iteration `cur` is done with it
-        S.fill[k] = 0u;
-    }
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    Ctrl &c = *S.ctrl;
-    if (c.done) return;
     const int nxt = cur ^ 1;
     c.pend_tail += c.pend_add;
     c.pend_add = 0;
@@ -373,6 +367,21 @@ __global__ void ctrl_kernel(State S, int cur, unsigned long long total)
     c.iter++;
     if (work >= total && avail == 0 && n_alive == 0) c.done = 1;
     else if (c.iter >= c.max_iter) c.done = 2;
+}
+
+// In a graph (in_graph != 0) it also sets the condition of the WHILE node that
+// repeats the iterations: 0 once the run is done or the iteration bound is hit.
+__global__ void ctrl_kernel(State S, int cur, unsigned long long total, cudaGraphConditionalHandle loop,
+                            int in_graph)
+{
+    for (int k = threadIdx.x; k < kMaxKeys; k += blockDim.x) {
+        S.hist[cur][k] = 0u;        // the sort of iteration `cur` is done with it
+        S.fill[k] = 0u;
+    }
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    Ctrl &c = *S.ctrl;
+    if (!c.done) ctrl_step(c, cur, total);
+    if (in_graph) cudaGraphSetConditional(loop, c.done ? 0u : 1u);
 }
 
 // ---------------------------------------------------------------- gen
@@ -1001,6 +1010,11 @@ struct WavefrontBuffers {
     void *block = nullptr;
     wf::Ctrl *host_ctrl = nullptr;   // pinned mirror of the control block
     int trace_grid = 0, work_grid = 0;
+    // executable graph of the last run launched outside stream capture, and the
+    // bytes of the arguments it was built for
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<unsigned char> graph_key;
 };
 
 int wavefront_trace_grid(const WavefrontBuffers *w) { return w ? w->trace_grid : 0; }
@@ -1086,6 +1100,8 @@ gadep_status wavefront_create(int device, int slots, bool grad, WavefrontBuffers
 void wavefront_destroy(WavefrontBuffers *w)
 {
     if (!w) return;
+    if (w->exec) cudaGraphExecDestroy(w->exec);
+    if (w->graph) cudaGraphDestroy(w->graph);
     cudaFree(w->block);
     cudaFreeHost(w->host_ctrl);
     delete w;
@@ -1124,56 +1140,149 @@ gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P0, bool grad
         if (e != cudaSuccess) return fail(GADEP_E_CUDA, "wavefront: shared memory: %s", cudaGetErrorString(e));
     }
     const unsigned long long max_iter = (unsigned long long)P.step_cap * 4 + P.total / 1024 + 1000000ull;
+    const int sort_grid = (S.slots + 256 * wf::kSortPerThread - 1) / (256 * wf::kSortPerThread);
+    // the kernels of the run, in order (cur = -1: the pre-loop part)
+    const unsigned long long total = P.total;
+    const int n_keys = P.n_keys;
+    auto launch = [&](int kind, int cur, cudaGraph_t g, const cudaGraphNode_t *dep, size_t n_dep,
+                      cudaGraphNode_t *node, cudaGraphConditionalHandle loop, int in_graph) -> cudaError_t {
+        const void *fn = nullptr;
+        dim3 grid(1), block(256);
+        size_t smem = 0;
+        int c = cur < 0 ? 1 : cur;
+        void *args[8];
+        switch (kind) {
+        case KK_INIT: fn = (const void *)wf::init_kernel; grid = dim3((S.slots + 255) / 256);
+            args[0] = &S; args[1] = (void *)&max_iter; break;
+        case KK_GEN: fn = (const void *)wf::gen_kernel; grid = dim3(w->work_grid); smem = gsm;
+            args[0] = &P; args[1] = &S; break;
+        case KK_CTRL: fn = (const void *)wf::ctrl_kernel;
+            args[0] = &S; args[1] = &c; args[2] = (void *)&total; args[3] = &loop; args[4] = &in_graph; break;
+        case KK_SPAWN: fn = grad ? (const void *)wf::spawn_kernel<true> : (const void *)wf::spawn_kernel<false>;
+            grid = dim3(w->work_grid); smem = ksm; args[0] = &P; args[1] = &S; args[2] = &c; break;
+        case KK_SORT: fn = (const void *)wf::sort_kernel; grid = dim3(sort_grid); smem = ssm;
+            args[0] = &S; args[1] = &c; args[2] = (void *)&n_keys; break;
+        case KK_N: fn = (const void *)wf::sort_prefix_kernel; block = dim3(1024);   // the sort's prefix
+            args[0] = &S; args[1] = &c; args[2] = (void *)&n_keys; break;
+        case KK_TRACE: fn = count ? (const void *)wf::trace_kernel<true> : (const void *)wf::trace_kernel<false>;
+            grid = dim3(w->trace_grid);
+            args[0] = (void *)&P.nodes; args[1] = (void *)&P.tris; args[2] = (void *)&P.planes;
+            args[3] = (void *)&P.regions; args[4] = (void *)&P.n_region; args[5] = &S; args[6] = &c;
+            args[7] = &counters; break;
+        case KK_PHYSICS:
+            fn = grad ? (count ? (const void *)wf::physics_kernel<true, true> : (const void *)wf::physics_kernel<true, false>)
+                      : (count ? (const void *)wf::physics_kernel<false, true> : (const void *)wf::physics_kernel<false, false>);
+            grid = dim3(w->work_grid); smem = rsm; args[0] = &P; args[1] = &S; args[2] = &c; args[3] = &counters; break;
+        default: return cudaErrorInvalidValue;
+        }
+        if (!g) return cudaLaunchKernel(fn, grid, block, args, smem, s);
+        cudaKernelNodeParams kp{};
+        kp.func = const_cast<void *>(fn);
+        kp.gridDim = grid;
+        kp.blockDim = block;
+        kp.sharedMemBytes = (unsigned int)smem;
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        return cudaGraphAddKernelNode(node, g, dep, n_dep, &kp);
+    };
+    static const int kIteration[] = { KK_SPAWN, KK_N, KK_SORT, KK_TRACE, KK_PHYSICS, KK_GEN, KK_CTRL };
     KernelTimer none;
     KernelTimer &T = timer ? *timer : none;
-    T.before(s);
-    wf::init_kernel<<<(S.slots + 255) / 256, 256, 0, s>>>(S, max_iter);
-    T.after(KK_INIT, s);
-    T.before(s);
-    wf::gen_kernel<<<w->work_grid, 256, gsm, s>>>(P, S);
-    T.after(KK_GEN, s);
-    T.before(s);
-    wf::ctrl_kernel<<<1, 256, 0, s>>>(S, 1, P.total);
-    T.after(KK_CTRL, s);
-    const int sort_grid = (S.slots + 256 * wf::kSortPerThread - 1) / (256 * wf::kSortPerThread);
+
+    if (!T.timing) {
+        // ---- graph: init, gen, ctrl, then WHILE(condition) { two iterations } ----
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaError_t e = cudaStreamIsCapturing(s, &cap);
+        if (e != cudaSuccess) return fail(GADEP_E_CUDA, "wavefront: stream query: %s", cudaGetErrorString(e));
+        const bool capturing = cap == cudaStreamCaptureStatusActive;
+        // graph arguments: the bytes of everything the nodes capture
+        std::vector<unsigned char> key(sizeof(P) + sizeof(S) + 16);
+        std::memcpy(key.data(), &P, sizeof(P));
+        std::memcpy(key.data() + sizeof(P), &S, sizeof(S));
+        unsigned char *kx = key.data() + sizeof(P) + sizeof(S);
+        kx[0] = grad; kx[1] = count;
+        std::memcpy(kx + 8, &counters, sizeof(counters));
+        if (!capturing && w->exec && key == w->graph_key) {
+            e = cudaGraphLaunch(w->exec, s);
+            return e == cudaSuccess ? GADEP_OK : fail(GADEP_E_CUDA, "wavefront: graph launch: %s", cudaGetErrorString(e));
+        }
+        cudaGraph_t g = nullptr;
+        std::vector<cudaGraphNode_t> deps;
+        if (capturing) {
+            const cudaGraphNode_t *d = nullptr;
+            size_t nd = 0;
+            e = cudaStreamGetCaptureInfo(s, &cap, nullptr, &g, &d, nullptr, &nd);
+            if (e != cudaSuccess) return fail(GADEP_E_CUDA, "wavefront: capture info: %s", cudaGetErrorString(e));
+            deps.assign(d, d + nd);
+        } else {
+            if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
+            if (w->graph) { cudaGraphDestroy(w->graph); w->graph = nullptr; }
+            w->graph_key.clear();
+            if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess)
+                return fail(GADEP_E_CUDA, "wavefront: graph: %s", cudaGetErrorString(e));
+            w->graph = g;
+        }
+        cudaGraphConditionalHandle loop = 0;
+        e = cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault);
+        cudaGraphNode_t prev = nullptr, node = nullptr;
+        const int pre[] = { KK_INIT, KK_GEN, KK_CTRL };
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+            if (prev) e = launch(pre[k], -1, g, &prev, 1, &node, loop, 0);
+            else e = launch(pre[k], -1, g, deps.data(), deps.size(), &node, loop, 0);
+            prev = node;
+        }
+        cudaGraphNode_t loop_node = nullptr;
+        if (e == cudaSuccess) {
+            cudaGraphNodeParams cp{};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = loop;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            e = cudaGraphAddNode(&loop_node, g, &prev, nullptr, 1, &cp);
+            if (e == cudaSuccess) {
+                cudaGraph_t body = cp.conditional.phGraph_out[0];
+                cudaGraphNode_t bprev = nullptr;
+                for (int cur = 0; cur < 2 && e == cudaSuccess; ++cur)
+                    for (int k = 0; k < 7 && e == cudaSuccess; ++k) {
+                        e = launch(kIteration[k], cur, body, bprev ? &bprev : nullptr, bprev ? 1 : 0, &node, loop, 1);
+                        bprev = node;
+                    }
+            }
+        }
+        if (e != cudaSuccess) return fail(GADEP_E_CUDA, "wavefront: graph build: %s", cudaGetErrorString(e));
+        if (capturing) {
+            e = cudaStreamUpdateCaptureDependencies(s, &loop_node, nullptr, 1, cudaStreamSetCaptureDependencies);
+            return e == cudaSuccess ? GADEP_OK : fail(GADEP_E_CUDA, "wavefront: capture: %s", cudaGetErrorString(e));
+        }
+        if ((e = cudaGraphInstantiate(&w->exec, g, 0)) != cudaSuccess) {
+            w->exec = nullptr;
+            return fail(GADEP_E_CUDA, "wavefront: graph instantiation: %s", cudaGetErrorString(e));
+        }
+        w->graph_key = key;
+        e = cudaGraphLaunch(w->exec, s);
+        return e == cudaSuccess ? GADEP_OK : fail(GADEP_E_CUDA, "wavefront: graph launch: %s", cudaGetErrorString(e));
+    }
+
+    // ---- host loop with a CUDA event pair around every kernel (timing) ----
+    const int pre[] = { KK_INIT, KK_GEN, KK_CTRL };
+    for (int k = 0; k < 3; ++k) {
+        T.before(s);
+        const cudaError_t e = launch(pre[k], -1, nullptr, nullptr, 0, nullptr, 0, 0);
+        T.after(pre[k], s);
+        if (e != cudaSuccess) return fail(GADEP_E_CUDA, "wavefront: launch: %s", cudaGetErrorString(e));
+    }
     const int check_every = 16;
     for (unsigned long long it = 0;; ++it) {
         const int cur = (int)(it & 1);
-        T.before(s);
-        if (grad) wf::spawn_kernel<true><<<w->work_grid, 256, ksm, s>>>(P, S, cur);
-        else wf::spawn_kernel<false><<<w->work_grid, 256, ksm, s>>>(P, S, cur);
-        T.after(KK_SPAWN, s);
-        T.before(s);
-        wf::sort_prefix_kernel<<<1, 1024, 0, s>>>(S, cur, P.n_keys);
-        wf::sort_kernel<<<sort_grid, 256, ssm, s>>>(S, cur, P.n_keys);
-        T.after(KK_SORT, s);
-        T.before(s);
-        if (count)
-            wf::trace_kernel<true><<<w->trace_grid, 256, 0, s>>>(P.nodes, P.tris, P.planes, P.regions, P.n_region, S, cur,
-                                                                  counters);
-        else
-            wf::trace_kernel<false><<<w->trace_grid, 256, 0, s>>>(P.nodes, P.tris, P.planes, P.regions, P.n_region, S, cur,
-                                                                   counters);
-        T.after(KK_TRACE, s);
-        T.before(s);
-        if (grad) {
-            if (count) wf::physics_kernel<true, true><<<w->work_grid, 256, rsm, s>>>(P, S, cur, counters);
-            else wf::physics_kernel<true, false><<<w->work_grid, 256, rsm, s>>>(P, S, cur, counters);
-        } else {
-            if (count) wf::physics_kernel<false, true><<<w->work_grid, 256, rsm, s>>>(P, S, cur, counters);
-            else wf::physics_kernel<false, false><<<w->work_grid, 256, rsm, s>>>(P, S, cur, counters);
+        for (int k = 0; k < 7; ++k) {
+            const int kind = kIteration[k];
+            if (kind != KK_SORT) T.before(s);      // the prefix and the sort are timed together
+            const cudaError_t e = launch(kind, cur, nullptr, nullptr, 0, nullptr, 0, 0);
+            if (kind != KK_N) T.after(kind, s);
+            if (e != cudaSuccess) return fail(GADEP_E_CUDA, "wavefront: launch: %s", cudaGetErrorString(e));
         }
-        T.after(KK_PHYSICS, s);
-        T.before(s);
-        wf::gen_kernel<<<w->work_grid, 256, gsm, s>>>(P, S);
-        T.after(KK_GEN, s);
-        T.before(s);
-        wf::ctrl_kernel<<<1, 256, 0, s>>>(S, cur, P.total);
-        T.after(KK_CTRL, s);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return fail(GADEP_E_CUDA, "wavefront: launch: %s", cudaGetErrorString(e));
         if (it % check_every == check_every - 1) {
-            e = cudaMemcpyAsync(w->host_ctrl, S.ctrl, sizeof(wf::Ctrl), cudaMemcpyDeviceToHost, s);
+            cudaError_t e = cudaMemcpyAsync(w->host_ctrl, S.ctrl, sizeof(wf::Ctrl), cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return fail(GADEP_E_CUDA, "wavefront: control read: %s", cudaGetErrorString(e));
             if (w->host_ctrl->done == 1) return GADEP_OK;
@@ -1181,6 +1290,18 @@ gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P0, bool grad
                 return fail(GADEP_E_TIMEOUT, "wavefront: iteration bound reached with photons still alive");
         }
     }
+}
+
+// After a run has completed on `s` (the caller synchronised it): the iteration
+// bound status of the control block.
+gadep_status wavefront_check(WavefrontBuffers *w, cudaStream_t s)
+{
+    cudaError_t e = cudaMemcpyAsync(w->host_ctrl, w->S.ctrl, sizeof(wf::Ctrl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(GADEP_E_CUDA, "wavefront: control read: %s", cudaGetErrorString(e));
+    if (w->host_ctrl->done == 2)
+        return fail(GADEP_E_TIMEOUT, "wavefront: iteration bound reached with photons still alive");
+    return GADEP_OK;
 }
 
 }  // namespace gadep

@@ -53,3 +53,50 @@ def test_wavefront_batched_and_gradient():
     # the plain batched call through the wavefront form
     rb, sb = api.gadep_run_batch(b, mats, inst, api.make_opts(variant=WAVEFRONT, wf_slots=16384))
     assert [r["n_fep"] for r in rb] == [r["n_fep"] for r in rw]
+
+
+def test_graph_loop_equals_host_loop():
+    """The wavefront iterations driven by the graph's WHILE node (default) and by
+    the host loop with per-kernel events (timing on) give the same histories."""
+    m = api.detmesh_build(W.COAX_P)
+    b = api.gadep_bvh_build(m, 0)
+    mats = api.Materials.default()
+    inst = api.make_instances([(662.0, W.COAX_POINT_25, 500_003, 0, []), (1332.0, W.COAX_POINT_25, 250_001, 1, [])])
+    opts = api.make_opts(variant=WAVEFRONT, wf_slots=65536)
+    p = api.Plan(b, mats, inst, opts)
+    p.launch()
+    rg, sg, _, _ = p.results()
+    p.set_timing(True)
+    p.launch()
+    rh, sh, _, _ = p.results()
+    stats = p.kernel_stats()
+    p.set_timing(False)
+    p.launch()                       # graph again, from the cached executable
+    rg2, sg2, _, _ = p.results()
+    for a, c, d in zip(rg, rh, rg2):
+        for k in ("n_hist", "n_fep", "n_zero", "n_over", "n_err", "n_segments", "n_interactions", "n_culled"):
+            assert a[k] == c[k] == d[k], k
+    assert np.array_equal(sg, sh) and np.array_equal(sg, sg2)
+    assert stats["trace"][0] > 0 and stats["trace"][1] > 0.0
+
+
+def test_graph_batch_captures_wavefront_plan():
+    """A wavefront plan launched under stream capture (its WHILE node goes into the
+    capturing graph) replays to the direct batched result."""
+    from paper_2605_25963_gb300 import batch
+    m = api.detmesh_build(W.BATCH_DET)
+    b = api.gadep_bvh_build(m, 0)
+    mats = api.Materials.default()
+    items = []
+    for i, (E, s, n, sm) in enumerate(W.batch_instances()[:7]):
+        items.append((E, W.BATCH_SOURCES[s], int(n // 500) + 13 * i, i, [1, 1, 1, sm]))
+    ref, ref_spec = api.gadep_run_batch(b, mats, api.make_instances(items), api.make_opts(variant=WAVEFRONT,
+                                                                                              wf_slots=32768))
+    g = batch.GraphBatch(b, mats, items, dict(variant=WAVEFRONT, wf_slots=32768))
+    for _ in range(2):
+        g.replay()
+        res, spec, _, _ = g.results()
+        for i in range(len(items)):
+            for k in ("n_hist", "n_fep", "n_zero", "n_over", "n_segments", "n_interactions"):
+                assert res[i][k] == ref[i][k], (i, k)
+        assert np.array_equal(spec, ref_spec)
