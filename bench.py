@@ -255,6 +255,39 @@ def measure_forms(dev, scale=1.0):
     return out
 
 
+def mesh_sweep(cfg, dev, n, opts):
+    """Mesh-density sensitivity (Sec. 3.3): the workload's detector discretised at
+    N_theta x N_phi from 32 x 10 to 1024 x 40, same histories; device time of one
+    step per mesh after one warm-up step."""
+    import dataclasses
+    import torch
+    from paper_2605_25963_gb300 import api
+    mats = api.Materials.default()
+    out = []
+    for nt, nph in ((32, 10), (64, 20), (128, 10), (256, 20), (512, 20), (1024, 40)):
+        det = dataclasses.replace(cfg["det"], n_theta=nt, n_phi=nph)
+        m = api.detmesh_build(det)
+        b = api.gadep_bvh_build(m, dev)
+        plans = [api.Plan(b, mats, api.make_instances([(E, cfg["src"], n, i, [])]), opts)
+                 for i, E in enumerate(cfg["energies"])]
+        for p in plans:
+            p.launch()
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for p in plans:
+            p.launch()
+        e.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e)
+        st = b.stats()
+        out.append({"n_theta": nt, "n_phi": nph, "triangles": int(st["n_tri"]),
+                    "bvh_mb": round((st["node_bytes"] + st["tri_bytes"]) / 1e6, 2), "ms_per_step": round(ms, 2),
+                    "hist_per_s": n * len(plans) / (ms / 1e3)})
+        del plans, b, m
+    return out
+
+
 def run_reference(args, cfg, rank, world):
     if rank != 0:
         return
@@ -286,6 +319,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / gradient comparison")
     ap.add_argument("--forms-scale", type=float, default=1.0, help="history-count scale of the form runs")
+    ap.add_argument("--mesh-sweep", action="store_true",
+                    help="also time the workload's detector at N_theta x N_phi from 32 x 10 to 1024 x 40")
     args = ap.parse_args()
     cfg = workload_config(args.workload, args.hist)
 
@@ -433,6 +468,7 @@ def main():
     forms = None
     if not args.no_forms and world == 1:
         forms = measure_forms(dev, args.forms_scale)
+    sweep = mesh_sweep(cfg, dev, n, opts) if args.mesh_sweep and world == 1 else None
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -469,6 +505,8 @@ def main():
             "fepe": fepe,
             "forms": forms,
         }
+        if sweep is not None:
+            line["mesh_sweep"] = sweep
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
