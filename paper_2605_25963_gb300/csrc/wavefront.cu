@@ -58,8 +58,10 @@ struct __align__(16) Hit {      // by queue position, written by trace
     float t;
     int tri;                    // mesh triangle id, -1 = nothing ahead
     int region;                 // region of the triangle's solid
-    int entering;               // 1 entering, 0 leaving, -2 traversal stack overflow
+    int entering;               // 1 entering, 0 leaving, -2 traversal stack overflow,
+                                // kBeyond: no surface before the sampled interaction point
 };
+constexpr int kBeyond = -3;
 static_assert(sizeof(Slot) == 64, "slot record is one 64-byte DRAM fetch");
 struct __align__(32) Sec {      // second annihilation photon, waiting for the first
     float4 p;                   // position
@@ -608,16 +610,21 @@ __global__ void __launch_bounds__(256) sort_kernel(State S, int cur, int n_keys)
 // ---------------------------------------------------------------- trace
 constexpr int kFetchThreshold = 20;   // refill lanes when fewer are still traversing (8, 12, 20 measured)
 
+// A query looks no further than the photon's sampled interaction point: the
+// slot record carries E and lam, so t_best starts at t_cur + lam / mu (with a
+// margin of 2^-10 relative + 1 um, above any rounding difference to the physics
+// kernel's own d_int and to the plane distance).  Every surface closer than the
+// interaction is still found, so physics decides exactly as with an unbounded
+// query; when none is, the hit is marked kBeyond (an interaction follows).
 template <bool COUNT>
-__global__ void __launch_bounds__(256, 5) trace_kernel(const float4 *__restrict__ nodes,
-                                                    const float4 *__restrict__ tris,
-                                                    const float4 *__restrict__ planes,
-                                                    const int4 *__restrict__ regions, int n_region, State S,
-                                                    int cur, unsigned long long *counters)
+__global__ void __launch_bounds__(256, 5) trace_kernel(const Params P, State S, int cur, unsigned long long *counters)
 {
     const uint32_t FULL = 0xffffffffu;
-    __shared__ int s_root[256];
-    for (int i = threadIdx.x; i < n_region; i += blockDim.x) s_root[i] = regions[i].w;
+    const float4 *__restrict__ nodes = P.nodes;
+    const float4 *__restrict__ tris = P.tris;
+    const float4 *__restrict__ planes = P.planes;
+    __shared__ int4 s_reg[256];
+    for (int i = threadIdx.x; i < P.n_region; i += blockDim.x) s_reg[i] = P.regions[i];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const unsigned int n = S.ctrl->q_count[cur];
@@ -626,7 +633,7 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const float4 *__restrict_
     unsigned int qidx = 0;
     float ox = 0, oy = 0, oz = 0, t_min = 0, ix = 0, iy = 0, iz = 0, oix = 0, oiy = 0, oiz = 0, t_best = 0;
     int exclude = -1, node = kSentinel, leaf = 0, sp = 0, best = -1;
-    bool ent = false;
+    bool ent = false, bounded = false;
     ShearK sh{ 2, false, 0.0f, 0.0f, 1.0f };
     int stack[kStack];
     uint32_t nn = 0, nt = 0, err = 0;
@@ -656,7 +663,10 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const float4 *__restrict_
             drained = global_done && wb >= we;
             if (!has && idx != 0xffffffffu) {
                 qidx = idx;
-                const Ray r = S.slot[queue[idx]].r;
+                const Slot &sr = S.slot[queue[idx]];
+                const Ray r = sr.r;
+                const float E = sr.p.f.x, lam = sr.p.f.y;
+                const uint32_t pinst = sr.p.u.z & 0xffffu;
                 const uint32_t tag = __float_as_uint(r.d.w);
                 ox = r.o.x; oy = r.o.y; oz = r.o.z; t_min = r.o.w;
                 exclude = (int)(tag >> kTagShift) - 1;
@@ -665,12 +675,22 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const float4 *__restrict_
                 iy = 1.0f / (fabsf(r.d.y) > 1e-30f ? r.d.y : copysignf(1e-30f, r.d.y));
                 iz = 1.0f / (fabsf(r.d.z) > 1e-30f ? r.d.z : copysignf(1e-30f, r.d.z));
                 oix = ox * ix; oiy = oy * iy; oiz = oz * iz;
+                const int4 R = s_reg[tag & 255u];
                 t_best = INFINITY;
+                if (R.x >= 0) {
+                    float pe, co, pa;
+                    mu_at(P.xs + (size_t)R.x * P.n_grid, P.n_grid, P.lnE_min, P.inv_dlnE, E, pe, co, pa);
+                    const int group = (R.y >> 1) - 1;
+                    const float scl = group >= 0 ? __ldg(&P.inst[pinst].scale[group]) : 1.0f;
+                    const float mu = (pe + co + pa) * scl;
+                    if (mu > 0.0f) t_best = fmaf(lam / mu, 1.0f + 1.0f / 1024.0f, t_min) + 1e-3f;
+                }
+                bounded = t_best < INFINITY;
                 best = -1;
                 ent = false;
                 stack[0] = kSentinel;
                 sp = 0;
-                const int root = s_root[tag & 255u];
+                const int root = R.w;
                 node = root < 0 ? kSentinel : root;
                 leaf = 0;
                 has = true;
@@ -729,7 +749,7 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const float4 *__restrict_
                                           t_min)
                                 : INFINITY;
                 h.region = best >= 0 ? __float_as_int(__ldg(&tris[3 * best].w)) : 0;
-                h.entering = best >= 0 ? (ent ? 1 : 0) : ((err & ERR_STACK) ? -2 : 0);
+                h.entering = best >= 0 ? (ent ? 1 : 0) : ((err & ERR_STACK) ? -2 : (bounded ? kBeyond : 0));
                 S.hit[qidx] = h;
                 err = 0;
                 has = false;
@@ -810,7 +830,7 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
                 float t_hit = ht.t;
                 int hit_tri = ht.tri, hit_region = ht.region;
                 bool entering = ht.entering == 1;
-                if (hit_tri < 0 && region != 0) {
+                if (hit_tri < 0 && region != 0 && ht.entering != kBeyond) {
                     // Inside a solid every ray meets its boundary, so the photon sits a
                     // rounding error past it: relocate by the nearest surface of the
                     // whole mesh; with none ahead it is outside every solid.
@@ -1166,9 +1186,7 @@ gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P0, bool grad
             args[0] = &S; args[1] = &c; args[2] = (void *)&n_keys; break;
         case KK_TRACE: fn = count ? (const void *)wf::trace_kernel<true> : (const void *)wf::trace_kernel<false>;
             grid = dim3(w->trace_grid);
-            args[0] = (void *)&P.nodes; args[1] = (void *)&P.tris; args[2] = (void *)&P.planes;
-            args[3] = (void *)&P.regions; args[4] = (void *)&P.n_region; args[5] = &S; args[6] = &c;
-            args[7] = &counters; break;
+            args[0] = &P; args[1] = &S; args[2] = &c; args[3] = &counters; break;
         case KK_PHYSICS:
             fn = grad ? (count ? (const void *)wf::physics_kernel<true, true> : (const void *)wf::physics_kernel<true, false>)
                       : (count ? (const void *)wf::physics_kernel<false, true> : (const void *)wf::physics_kernel<false, false>);
