@@ -437,6 +437,8 @@ def main():
     dom_launches, dom_ms = kstats[dom]
     achieved_tflops = flops_per_step * args.steps / (dom_ms / 1e3) / 1e12
     sm_max = (clocks or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
+    # the library's own microbenchmarks (after the timed region): FP32 FMA and L2 read peaks
+    fp32_meas, l2_meas = api.measure_peaks(dev)
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     segs = sum(f["segments"] for f in fepe)
 
@@ -492,6 +494,10 @@ def main():
                          "flop_per_launch": flops_per_step * args.steps / max(dom_launches, 1),
                          "peak_note": "FP32 non-tensor: %d SMs x %d lanes x 2 x %.0f MHz (derived)" % (
                              SM_COUNT, FP32_LANES_PER_SM, sm_max),
+                         "microbenchmarks": {"fp32_tflops": fp32_meas, "l2_read_gbs": l2_meas,
+                                             "frac_of_measured_fp32": achieved_tflops / fp32_meas,
+                                             "note": "library microbenchmarks: independent FMA chains on every "
+                                                     "SM; 64 MB re-read from L2"},
                          "per_query": {"nodes": nodes / max(segs, 1), "tris": tris / max(segs, 1),
                                        "relocated": relocated / max(segs, 1)},
                          "queries_per_step": segs},

@@ -337,6 +337,14 @@ gadep_status gadep_plan_shape(const gadep_plan *p, int32_t *grid, int32_t *block
                               int32_t *smem_bytes);
 void gadep_plan_destroy(gadep_plan *p);
 
+/* Peaks of `device` measured by the library's own microbenchmarks (no
+ * counterpart in the paper; denominators for the transport kernels, which are
+ * bound by FP32/ALU issue and served from L2): FP32 FMA throughput in TFLOP/s
+ * (an FMA counts 2 FLOP) of independent FMA chains on every SM, and the read
+ * bandwidth in GB/s of a 64 MB buffer re-read from L2.  Allocates and frees
+ * 64 MB of device memory and synchronises the device; either output may be NULL. */
+gadep_status gadep_measure_peaks(int32_t device, double *fp32_tflops, double *l2_read_gbs);
+
 /* Kernel launches of a plan since the last reset, per kind: the persistent
  * megakernel, or the six kernels of each wavefront iteration plus the slot-list
  * initialisation.  With timing on, gadep_plan_launch records a CUDA event pair

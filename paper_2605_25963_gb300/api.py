@@ -230,6 +230,13 @@ def make_instances(items):
     return arr
 
 
+def measure_peaks(device=0):
+    """(FP32 TFLOP/s, L2 read GB/s) of the device from the library's microbenchmarks."""
+    f, l2 = C.c_double(), C.c_double()
+    check(capi.load().gadep_measure_peaks(device, C.byref(f), C.byref(l2)))
+    return f.value, l2.value
+
+
 def result_dict(r: capi.gadep_result):
     return {k: getattr(r, k) for k, _ in capi.gadep_result._fields_}
 

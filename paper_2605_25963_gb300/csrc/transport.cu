@@ -363,6 +363,37 @@ __global__ void nearest_hit_kernel(const float4 *nodes, const float4 *tris, cons
     ent_out[i] = hit >= 0 ? (ent ? 1 : 0) : (err ? -2 : -1);
 }
 
+// FP32 FMA throughput: 8 independent chains per thread, kFmaIters rounds.
+constexpr int kFmaIters = 4096;
+__global__ void __launch_bounds__(256) fma_peak_kernel(float b, float c, float *out)
+{
+    float a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = (float)(threadIdx.x + k) * 1e-3f;
+    for (int it = 0; it < kFmaIters; ++it) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fmaf(a[k], b, c);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    if (s == 12345.678f) out[blockIdx.x * blockDim.x + threadIdx.x] = s;   // keeps the chains alive
+}
+
+// L2 read bandwidth: `rounds` grid-stride passes of 16-byte loads over n float4.
+__global__ void __launch_bounds__(256) l2_read_kernel(const float4 *__restrict__ buf, size_t n, int rounds,
+                                                      float *out)
+{
+    float s = 0.0f;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (int r = 0; r < rounds; ++r)
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+            const float4 v = __ldcg(buf + i);
+            s += v.x + v.y + v.z + v.w;
+        }
+    if (s == 12345.678f) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 __global__ void philox_words_kernel(unsigned long long seed, unsigned long long hid, uint32_t inst,
                                     int n_words, uint32_t *out)
 {
@@ -1050,6 +1081,53 @@ extern "C" gadep_status gadep_plan_results(gadep_plan *p, uint32_t *spectra_host
     gadep::clear_error();
     if (!p) return fail(GADEP_E_INVAL, "gadep_plan_results: NULL plan");
     return gadep::plan_results(p, spectra_host, results, dfepe, dsigma, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" gadep_status gadep_measure_peaks(int32_t device, double *fp32_tflops, double *l2_read_gbs)
+{
+    gadep::clear_error();
+    int n_dev = 0;
+    if (cudaGetDeviceCount(&n_dev) != cudaSuccess) { cudaGetLastError(); n_dev = 0; }
+    if (device < 0 || device >= n_dev) return fail(GADEP_E_INVAL, "gadep_measure_peaks: no CUDA device %d", device);
+    DeviceGuard g(device);
+    int n_sm = 0;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
+    const size_t n4 = (64u << 20) / sizeof(float4);
+    float4 *buf = nullptr;
+    float *out = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaMalloc(&buf, n4 * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&out, (size_t)n_sm * 8 * 256 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(buf, 0, n4 * sizeof(float4));
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    float best_fma = INFINITY, best_l2 = INFINITY;
+    const int grid = n_sm * 8, rounds = 16;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        float ms = 0.0f;
+        e = cudaEventRecord(a);
+        gadep::dev::fma_peak_kernel<<<grid, 256>>>(0.999999f, 1e-6f, out);
+        if (e == cudaSuccess) e = cudaEventRecord(b);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && rep > 0) best_fma = std::min(best_fma, ms);
+        if (e == cudaSuccess) e = cudaEventRecord(a);
+        gadep::dev::l2_read_kernel<<<grid, 256>>>(buf, n4, rounds, out);
+        if (e == cudaSuccess) e = cudaEventRecord(b);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && rep > 0) best_l2 = std::min(best_l2, ms);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(buf);
+    cudaFree(out);
+    if (e != cudaSuccess) return gadep::cuda_fail(e, "gadep_measure_peaks");
+    const double flop = 2.0 * 8.0 * gadep::dev::kFmaIters * (double)grid * 256.0;
+    if (fp32_tflops) *fp32_tflops = flop / (best_fma * 1e-3) / 1e12;
+    if (l2_read_gbs) *l2_read_gbs = (double)rounds * n4 * sizeof(float4) / (best_l2 * 1e-3) / 1e9;
+    return GADEP_OK;
 }
 
 extern "C" gadep_status gadep_plan_set_timing(gadep_plan *p, int32_t on)

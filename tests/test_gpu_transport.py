@@ -266,3 +266,42 @@ def test_invalid_run_arguments(orc, mats):
         api.gadep_run(b, mats, bad, 662.0, 10)
     with pytest.raises(capi.GadepError):
         api.gadep_run(b, mats, W.BARE_POINT_100, 662.0, 10, opts=api.make_opts(n_bins=0))
+
+
+def test_full_size_parity_bare_1e8(orc, otab, mats):
+    """The bare-cylinder workload at its full 1e8 histories on both sides: FEPE
+    within 3 combined sigma and 0.5 % relative, spectra by chi-square, the first
+    histories one by one."""
+    m, b, om = scene(orc, "BARE_CYLINDER")
+    n = 100_000_000
+    n_trace = 200_000
+    trace = torch.empty(n_trace, dtype=torch.float32, device="cuda")
+    r, spec = api.gadep_run(b, mats, W.BARE_POINT_100, 662.0, n, edep_trace=trace)
+    ro = orc.transport(om, otab, osrc(orc, W.BARE_POINT_100), 662.0, n, want_edep=False)
+    assert r["n_hist"] == n and r["n_err"] == 0 and ro.tally["n_err"] == 0
+    assert abs(r["fepe"] - ro.fepe) <= 3 * math.hypot(r["sigma"], ro.sigma)
+    assert abs(r["fepe"] - ro.fepe) <= 0.005 * ro.fepe
+    assert chi2_two_sample(spec, ro.spectrum) > 0.01
+    ro_t = orc.transport(om, otab, osrc(orc, W.BARE_POINT_100), 662.0, n_trace, want_edep=True)
+    g = trace.cpu().numpy().astype(np.float64)
+    assert np.mean(np.abs(g - ro_t.edep) <= 1e-3 + 1e-6 * np.abs(ro_t.edep)) >= 0.999
+
+
+def test_full_size_coax_against_oracle(orc, otab, mats):
+    """The coax workload in the bench's launch configuration (1e8 histories per
+    energy, AUTO form): against the oracle at 1e7 histories of the same streams,
+    FEPE within 3 combined sigma and 0.5 % relative; the first 1e5 histories one
+    by one."""
+    m, b, om = scene(orc, "COAX_P")
+    n, n_orc, n_trace = 100_000_000, 10_000_000, 100_000
+    for E in (122.0, 1332.0):
+        trace = torch.empty(n_trace, dtype=torch.float32, device="cuda")
+        r, spec = api.gadep_run(b, mats, W.COAX_POINT_25, E, n, edep_trace=trace)
+        ro = orc.transport(om, otab, osrc(orc, W.COAX_POINT_25), E, n_orc, want_edep=True)
+        assert r["n_err"] == 0 and ro.tally["n_err"] == 0 and ro.tally["n_parity_mismatch"] == 0
+        assert abs(r["fepe"] - ro.fepe) <= 3 * math.hypot(r["sigma"], ro.sigma)
+        assert abs(r["fepe"] - ro.fepe) <= 0.005 * ro.fepe
+        g = trace.cpu().numpy().astype(np.float64)
+        o = ro.edep[:n_trace]
+        assert np.mean(np.abs(g - o) <= 1e-3 + 1e-6 * np.abs(o)) >= 0.999
+        assert r["sum_dep_all"] + r["sum_esc"] == pytest.approx(n * E, rel=1e-6)
