@@ -43,6 +43,7 @@ FLOP_PER_NODE = 36.0
 FLOP_PER_TRI = 45.0
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+NODE_BYTES, TRI_BYTES = 64, 48        # BVH node record; three float4 vertices of a triangle
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -58,6 +59,11 @@ def workload_config(name, n_hist):
                          "dead layers) in the coax housing, N_theta 32, N_phi 10, point source 250 mm above "
                          "the window, the 13 Table 3 energies 59.54-1408.02 keV",
                     paper_s={"1e7": 11.96, "1e8": 66.08})
+    if name == "stress":
+        return dict(det=W.STRESS_DET, src=W.STRESS_SOURCE, energies=W.STRESS_ENERGIES,
+                    n_hist=n_hist or W.STRESS_HISTORIES,
+                    desc="stress: coax at 1024 segments with a 2 x 1 mm contact groove and a Cu flange with 16 "
+                         "bolt holes (1,012,288 triangles), water-prism volume source, 8 energies 59.5-1836 keV")
     if name == "bare":
         return dict(det=W.BARE_CYLINDER, src=W.BARE_POINT_100, energies=(662.0,), n_hist=n_hist or 1_000_000,
                     desc="bare Ge cylinder R 30 L 60, 48 segments (192 triangles), point source 100 mm, 662 keV")
@@ -309,11 +315,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gadep", choices=["gadep", "reference"])
-    ap.add_argument("--workload", default="coax", choices=["coax", "bare", "table4"])
+    ap.add_argument("--workload", default="coax", choices=["coax", "bare", "table4", "stress"])
     ap.add_argument("--hist", type=int, default=0, help="histories per energy (default: the workload's)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--variant", default="auto", choices=["auto", "mega", "wavefront"])
+    ap.add_argument("--bvh", default="", help="BVH build options, e.g. split_alpha=0,max_leaf=3 "
+                                             "(max_leaf, c_trav, c_tri, split_alpha, max_dup)")
     ap.add_argument("--wf-slots", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -342,11 +350,15 @@ def main():
         torch.cuda.set_device(local)
     dev = torch.cuda.current_device()
 
+    bvh_kw = {}
+    for item in filter(None, args.bvh.split(",")):
+        k, v = item.split("=")
+        bvh_kw[k.strip()] = int(v) if k.strip() == "max_leaf" else float(v)
     t0 = time.perf_counter()
     mesh = api.detmesh_build(cfg["det"])
     t_mesh = time.perf_counter() - t0
     t0 = time.perf_counter()
-    bvh = api.gadep_bvh_build(mesh, dev)
+    bvh = api.gadep_bvh_build(mesh, dev, **bvh_kw)
     t_bvh = time.perf_counter() - t0
     mats = api.Materials.default()
     n = cfg["n_hist"]
@@ -441,6 +453,9 @@ def main():
     fp32_meas, l2_meas = api.measure_peaks(dev)
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     segs = sum(f["segments"] for f in fepe)
+    # algorithmic node and triangle bytes of the traversal (64 B per node visit, 48 B per
+    # triangle test), served by L1 and L2, per second of the dominant kernel
+    l1l2_gbs = (NODE_BYTES * nodes + TRI_BYTES * tris) * args.steps / (dom_ms / 1e3) / 1e9
 
     # end to end through the public API with host buffers (tables and instance
     # uploaded, spectrum and tallies read back, every call)
@@ -486,7 +501,8 @@ def main():
                        "seed": 1, "triangles": bvh.stats()["n_tri"], "grid": g, "block": blk,
                        "smem_bytes": smem, "l2": "flushed between steps (512 MB write)",
                        "paper_rtx4090_s_all_energies": cfg.get("paper_s"),
-                       "mesh_build_s": round(t_mesh, 4), "bvh_build_s": round(t_bvh, 4)},
+                       "mesh_build_s": round(t_mesh, 4), "bvh_build_s": round(t_bvh, 4),
+                       "bvh": bvh.stats()["opts"]},
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved_tflops, "peak": peak_tflops,
                          "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
                          "traffic": recorded_traffic(args.workload, dom),
@@ -496,6 +512,8 @@ def main():
                              SM_COUNT, FP32_LANES_PER_SM, sm_max),
                          "microbenchmarks": {"fp32_tflops": fp32_meas, "l2_read_gbs": l2_meas,
                                              "frac_of_measured_fp32": achieved_tflops / fp32_meas,
+                                             "l1l2_bytes_gbs": l1l2_gbs,
+                                             "frac_of_measured_l2": l1l2_gbs / l2_meas if l2_meas else None,
                                              "note": "library microbenchmarks: independent FMA chains on every "
                                                      "SM; 64 MB re-read from L2"},
                          "per_query": {"nodes": nodes / max(segs, 1), "tris": tris / max(segs, 1),

@@ -162,21 +162,56 @@ gadep_status gadep_xs_build(const int32_t *codes, int32_t n_mat, int32_t n_grid,
 /* ------------------------------------------------------------------------- */
 
 typedef struct gadep_bvh gadep_bvh;
+
+/* Build options of the BVH.  The cost model is the surface-area heuristic
+ *   C = c_trav + (A_L N_L + A_R N_R) / A * c_tri
+ * (a node split where C is smallest; a leaf of N <= max_leaf triangles kept
+ * when N c_tri is not worse).  split_alpha > 0 turns on spatial splits (Stich,
+ * Friedrich and Dietrich 2009): where the two halves of the best centroid
+ * partition overlap by more than split_alpha times the root's surface area, a
+ * split plane that cuts triangle references in two is also costed; a cut
+ * triangle is stored in both subtrees (a copy of its 48-byte record each), at
+ * most max_dup records per triangle of a tree on average.  Long, thin
+ * triangles (the side walls of a cylinder) otherwise give every node near them
+ * a box as long as the wall.  On the coaxial detector meshes, though, spatial
+ * splits trade triangle tests for more node visits and the transport runs
+ * slower, so they are off by default; they stay available for meshes with
+ * large triangles. */
+typedef struct {
+    int32_t max_leaf;   /* 1..7 triangles per leaf at most; default 4 */
+    float c_trav;       /* >= 0; default 1.5 */
+    float c_tri;        /* > 0; default 1 */
+    float split_alpha;  /* >= 0, 0 = no spatial splits; default 0 (1e-5 is the usual value when on) */
+    float max_dup;      /* 1..16; default 2 */
+} gadep_bvh_opts;
+void gadep_bvh_opts_default(gadep_bvh_opts *o);
+
 typedef struct {
     int32_t n_nodes, n_leaves, max_depth, max_leaf_tris, n_tri, n_region;
     double  sah_cost;
     int64_t node_bytes, tri_bytes;
+    int64_t n_refs;          /* triangle records over all trees (copies from spatial splits included) */
+    gadep_bvh_opts opts;     /* the options the tree was built with */
 } gadep_bvh_stats;
 
 /* Binned-SAH BVH over all triangles of the mesh (the tree the paper's Gadep uses
  * to accelerate triangle queries, Sec. 2.4.3), compacted to 64-byte nodes and
- * 48-byte triangles, copied to `device`.  The mesh may be destroyed afterwards.
- * device = -1 builds the host copy only (stats and validation work; transport
- * calls on such a handle fail with GADEP_E_INVAL). */
+ * 48-byte triangle records, copied to `device`: one tree over every triangle and
+ * one per region (the triangles a photon in that region can reach first).  The
+ * mesh may be destroyed afterwards.  device = -1 builds the host copy only
+ * (stats and validation work; transport calls on such a handle fail with
+ * GADEP_E_INVAL).  gadep_bvh_build uses the default options;
+ * gadep_bvh_build_opts takes them (NULL = defaults; GADEP_E_INVAL when out of
+ * range). */
 gadep_status gadep_bvh_build(const detmesh_mesh *m, int32_t device, gadep_bvh **out);
+gadep_status gadep_bvh_build_opts(const detmesh_mesh *m, const gadep_bvh_opts *opts, int32_t device,
+                                  gadep_bvh **out);
 gadep_status gadep_bvh_get_stats(const gadep_bvh *b, gadep_bvh_stats *out);
-/* Host-side invariant check: every triangle in exactly one leaf, child boxes
- * inside parents, leaf boxes contain their triangles.  GADEP_E_MESH if violated. */
+/* Host-side invariant check of every tree: each of its triangles held by at
+ * least one leaf and never twice by one leaf, child boxes inside parents, every
+ * leaf box meeting the bounds of the triangles it holds, and the leaf boxes of
+ * each triangle covering a grid of points on it (vertices included; the whole
+ * triangle when it was not cut).  GADEP_E_MESH if violated. */
 gadep_status gadep_bvh_validate(const gadep_bvh *b);
 void gadep_bvh_destroy(gadep_bvh *b);
 

@@ -153,15 +153,34 @@ class Bvh:
     def stats(self):
         s = capi.gadep_bvh_stats()
         check(capi.load().gadep_bvh_get_stats(self._h, C.byref(s)))
-        return {k: getattr(s, k) for k, _ in capi.gadep_bvh_stats._fields_}
+        d = {k: getattr(s, k) for k, _ in capi.gadep_bvh_stats._fields_}
+        d["opts"] = {k: getattr(s.opts, k) for k, _ in capi.gadep_bvh_opts._fields_}
+        return d
 
     def validate(self):
         check(capi.load().gadep_bvh_validate(self._h))
 
 
-def gadep_bvh_build(mesh: Mesh, device: int = 0) -> Bvh:
+def bvh_opts(**kw) -> "capi.gadep_bvh_opts":
+    """gadep_bvh_opts with the library defaults, then the given fields
+    (max_leaf, c_trav, c_tri, split_alpha, max_dup)."""
+    o = capi.gadep_bvh_opts()
+    capi.load().gadep_bvh_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if k not in dict(capi.gadep_bvh_opts._fields_):
+            raise TypeError("unknown BVH option %r" % k)
+        setattr(o, k, v)
+    return o
+
+
+def gadep_bvh_build(mesh: Mesh, device: int = 0, **opts) -> Bvh:
+    """BVH of the mesh on `device` (-1: host copy only); keyword options as in
+    bvh_opts (defaults: the library's)."""
     h = C.c_void_p()
-    check(capi.load().gadep_bvh_build(mesh.handle, device, C.byref(h)))
+    if opts:
+        check(capi.load().gadep_bvh_build_opts(mesh.handle, C.byref(bvh_opts(**opts)), device, C.byref(h)))
+    else:
+        check(capi.load().gadep_bvh_build(mesh.handle, device, C.byref(h)))
     return Bvh(h)
 
 

@@ -20,7 +20,7 @@ MAX_GROUPS = 8
 EXPORTS = (
     "gadep_last_error", "gadep_abi_version", "detmesh_build", "detmesh_from_arrays", "detmesh_get",
     "detmesh_solid_stats", "detmesh_locate", "detmesh_destroy", "gadep_xs_build", "gadep_bvh_build",
-    "gadep_bvh_get_stats", "gadep_bvh_validate", "gadep_bvh_destroy", "gadep_nearest_hit",
+    "gadep_bvh_build_opts", "gadep_bvh_opts_default", "gadep_bvh_get_stats", "gadep_bvh_validate", "gadep_bvh_destroy", "gadep_nearest_hit",
     "gadep_opts_default", "gadep_run", "gadep_run_batch", "gadep_grad", "gadep_plan_create",
     "gadep_plan_launch", "gadep_plan_results", "gadep_plan_shape", "gadep_plan_destroy",
     "gadep_count_work", "gadep_philox_words", "gadep_run_noalloc", "gadep_plan_set_timing",
@@ -53,10 +53,16 @@ class gadep_solid(C.Structure):
                 ("parent", C.c_int32)]
 
 
+class gadep_bvh_opts(C.Structure):
+    _fields_ = [("max_leaf", C.c_int32), ("c_trav", C.c_float), ("c_tri", C.c_float), ("split_alpha", C.c_float),
+                ("max_dup", C.c_float)]
+
+
 class gadep_bvh_stats(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("n_leaves", C.c_int32), ("max_depth", C.c_int32),
                 ("max_leaf_tris", C.c_int32), ("n_tri", C.c_int32), ("n_region", C.c_int32),
-                ("sah_cost", C.c_double), ("node_bytes", C.c_int64), ("tri_bytes", C.c_int64)]
+                ("sah_cost", C.c_double), ("node_bytes", C.c_int64), ("tri_bytes", C.c_int64),
+                ("n_refs", C.c_int64), ("opts", gadep_bvh_opts)]
 
 
 class gadep_materials(C.Structure):
@@ -130,6 +136,8 @@ def load(build_if_missing: bool = True):
         "detmesh_destroy": (None, [vp]),
         "gadep_xs_build": (st, [P(C.c_int32), C.c_int32, C.c_int32, C.c_double, C.c_double, P(C.c_float)]),
         "gadep_bvh_build": (st, [vp, C.c_int32, P(vp)]),
+        "gadep_bvh_build_opts": (st, [vp, P(gadep_bvh_opts), C.c_int32, P(vp)]),
+        "gadep_bvh_opts_default": (None, [P(gadep_bvh_opts)]),
         "gadep_bvh_get_stats": (st, [vp, P(gadep_bvh_stats)]),
         "gadep_bvh_validate": (st, [vp]),
         "gadep_bvh_destroy": (None, [vp]),

@@ -6,6 +6,9 @@
 // of Wald (2007): at every node, 32 centroid bins per axis, split where
 //   C = C_trav + (A_L N_L + A_R N_R) / A * C_tri
 // is smallest; a leaf is kept when N <= max_leaf and N C_tri is not worse.
+// Optionally (split_alpha > 0) spatial splits cut triangle references too.
+// The costs, the leaf limit and the split threshold are build options
+// (gadep_bvh_opts); C_trav = 1.5 C_tri measured fastest on the coaxial meshes.
 // The tree is then compacted into the 64-byte two-child node layout documented
 // in gadep_internal.h (both child boxes stored in the parent, depth-first order,
 // the left child of an inner node right after it) with the triangles reordered
@@ -19,9 +22,8 @@
 
 namespace {
 
-constexpr int kBins = 32;
-constexpr float kCTrav = 1.0f, kCTri = 1.0f;
-constexpr int kMaxLeaf = 4;
+constexpr int kBins = 32;          // centroid bins of the object split
+constexpr int kSpatialBins = 32;   // slabs of the spatial split
 constexpr int kMaxDepth = 60;
 
 struct AABB {
@@ -36,89 +38,282 @@ struct AABB {
         return 2.0f * (d[0] * d[1] + d[1] * d[2] + d[2] * d[0]);
     }
     bool valid() const { return lo[0] <= hi[0]; }
+    bool nonempty() const { return lo[0] <= hi[0] && lo[1] <= hi[1] && lo[2] <= hi[2]; }
+    static AABB meet(const AABB &a, const AABB &b)
+    {
+        AABB r;
+        for (int k = 0; k < 3; ++k) { r.lo[k] = std::max(a.lo[k], b.lo[k]); r.hi[k] = std::min(a.hi[k], b.hi[k]); }
+        return r;
+    }
+    static AABB join(const AABB &a, const AABB &b) { AABB r = a; r.grow(b); return r; }
 };
 
+// A triangle reference: the box of the part of the triangle it stands for (the
+// whole triangle unless a spatial split cut it) and that box's centre.
 struct Ref { AABB box; float c[3]; int32_t tri; };
+
+Ref make_ref(const AABB &box, int32_t tri)
+{
+    Ref r;
+    r.box = box;
+    for (int k = 0; k < 3; ++k) r.c[k] = 0.5f * (box.lo[k] + box.hi[k]);
+    r.tri = tri;
+    return r;
+}
 
 struct BNode {
     AABB box;
     int32_t child[2] = { -1, -1 };   // build-node indices (inner)
-    int32_t start = 0, count = 0;    // leaf range in refs
+    int32_t start = 0, count = 0;    // leaf range in the leaf-ordered references
     bool leaf() const { return child[0] < 0; }
 };
 
+// binary32 bounds of an FP64 interval, rounded outward
+float round_down(double x) { float f = (float)x; return (double)f > x ? std::nextafter(f, -INFINITY) : f; }
+float round_up(double x) { float f = (float)x; return (double)f < x ? std::nextafter(f, INFINITY) : f; }
+
+// Box of the part of triangle v (FP64 copies of its binary32 vertices) with
+// lo <= x_k <= hi: the triangle clipped by the two planes (Sutherland-Hodgman),
+// its vertices bounded outward in binary32.  Empty (not nonempty()) when the
+// triangle misses the slab.
+AABB clip_box(const double v[3][3], int k, double lo, double hi)
+{
+    double poly[8][3], next[8][3];
+    int n = 3;
+    std::memcpy(poly, v, sizeof(double) * 9);
+    for (int side = 0; side < 2 && n > 0; ++side) {
+        const double plane = side == 0 ? lo : hi;
+        int m = 0;
+        for (int i = 0; i < n; ++i) {
+            const double *p = poly[i], *q = poly[(i + 1) % n];
+            const double dp = side == 0 ? p[k] - plane : plane - p[k];
+            const double dq = side == 0 ? q[k] - plane : plane - q[k];
+            if (dp >= 0.0) std::memcpy(next[m++], p, sizeof(double) * 3);
+            if ((dp >= 0.0) != (dq >= 0.0)) {
+                const double s = dp / (dp - dq);
+                for (int c = 0; c < 3; ++c) next[m][c] = p[c] + s * (q[c] - p[c]);
+                next[m][k] = plane;
+                ++m;
+            }
+        }
+        n = m;
+        std::memcpy(poly, next, sizeof(double) * 3 * (size_t)n);
+    }
+    AABB b;
+    for (int i = 0; i < n; ++i)
+        for (int c = 0; c < 3; ++c) {
+            b.lo[c] = std::min(b.lo[c], round_down(poly[i][c]));
+            b.hi[c] = std::max(b.hi[c], round_up(poly[i][c]));
+        }
+    return b;
+}
+
+struct Split {
+    float cost = INFINITY;
+    int axis = -1, bin = -1;
+    float pos = 0.0f;            // spatial: the plane x_axis = pos
+    AABB l, r;
+    int32_t nl = 0, nr = 0;
+};
+
+// Top-down builder.  Object splits partition the references by centroid bin
+// (binned SAH, Wald 2007).  Where the two children of the best object split
+// overlap by more than alpha times the root's surface area, a spatial split is
+// tried too (Stich, Friedrich and Dietrich 2009): the node's box is cut into
+// slabs along each axis, every reference is clipped into the slabs it spans,
+// and a plane between slabs is costed with the references that cross it counted
+// on both sides.  A reference that crosses the chosen plane goes to one side
+// whole when that is cheaper ("unsplitting"), else it is cut in two.  The
+// number of references is capped at max_dup times the triangles.
 struct Builder {
-    std::vector<Ref> refs;
+    const float *xyz = nullptr;      // binary32 vertex coordinates of the mesh
+    const int32_t *tv = nullptr;     // vertex indices of each mesh triangle
+    int max_leaf = 4;
+    float c_trav = 1.0f, c_tri = 1.0f, alpha = 0.0f;
+    int64_t ref_budget = 0, n_refs = 0;
+    float root_area = 0.0f;
     std::vector<BNode> nodes;
+    std::vector<Ref> leaf_refs;      // references in leaf order
     int max_depth = 0;
 
-    int32_t build(int32_t start, int32_t end, int depth)
+    void verts(int32_t t, double v[3][3]) const
+    {
+        for (int j = 0; j < 3; ++j)
+            for (int c = 0; c < 3; ++c) v[j][c] = (double)xyz[3 * (size_t)tv[3 * (size_t)t + j] + c];
+    }
+
+    Split object_split(const std::vector<Ref> &refs, const AABB &cb, float area) const
+    {
+        Split best;
+        for (int ax = 0; ax < 3; ++ax) {
+            const float ext = cb.hi[ax] - cb.lo[ax];
+            if (!(ext > 0.0f)) continue;
+            AABB bb[kBins];
+            int cnt[kBins] = { 0 };
+            const float scale = kBins / ext;
+            for (const Ref &r : refs) {
+                int b = std::min(kBins - 1, (int)((r.c[ax] - cb.lo[ax]) * scale));
+                cnt[b]++;
+                bb[b].grow(r.box);
+            }
+            AABB rbox[kBins];
+            int rcnt[kBins];
+            AABB acc;
+            int c = 0;
+            for (int b = kBins - 1; b > 0; --b) {
+                acc.grow(bb[b]); c += cnt[b];
+                rbox[b] = acc;
+                rcnt[b] = c;
+            }
+            AABB lacc;
+            int lc = 0;
+            for (int b = 1; b < kBins; ++b) {
+                lacc.grow(bb[b - 1]); lc += cnt[b - 1];
+                if (lc == 0 || rcnt[b] == 0) continue;
+                const float cost = c_trav + (lacc.area() * lc + rbox[b].area() * rcnt[b]) / area * c_tri;
+                if (cost < best.cost) {
+                    best.cost = cost; best.axis = ax; best.bin = b;
+                    best.l = lacc; best.r = rbox[b]; best.nl = lc; best.nr = rcnt[b];
+                }
+            }
+        }
+        return best;
+    }
+
+    Split spatial_split(const std::vector<Ref> &refs, const AABB &box, float area) const
+    {
+        Split best;
+        for (int ax = 0; ax < 3; ++ax) {
+            const float lo = box.lo[ax], ext = box.hi[ax] - box.lo[ax];
+            if (!(ext > 0.0f)) continue;
+            float plane[kSpatialBins + 1];
+            for (int i = 0; i <= kSpatialBins; ++i) plane[i] = lo + ext * ((float)i / kSpatialBins);
+            plane[kSpatialBins] = box.hi[ax];
+            const float scale = kSpatialBins / ext;
+            auto bin_of = [&](float x) { return std::max(0, std::min(kSpatialBins - 1, (int)((x - lo) * scale))); };
+            AABB bb[kSpatialBins];
+            int entry[kSpatialBins] = { 0 }, exit[kSpatialBins] = { 0 };
+            for (const Ref &r : refs) {
+                const int b0 = bin_of(r.box.lo[ax]), b1 = std::max(b0, bin_of(r.box.hi[ax]));
+                entry[b0]++;
+                exit[b1]++;
+                if (b0 == b1) { bb[b0].grow(r.box); continue; }
+                double v[3][3];
+                verts(r.tri, v);
+                for (int b = b0; b <= b1; ++b) {
+                    const AABB part = AABB::meet(clip_box(v, ax, plane[b], plane[b + 1]), r.box);
+                    if (part.nonempty()) bb[b].grow(part);
+                }
+            }
+            AABB rbox[kSpatialBins];
+            int rcnt[kSpatialBins];
+            AABB acc;
+            int c = 0;
+            for (int b = kSpatialBins - 1; b > 0; --b) {
+                acc.grow(bb[b]); c += exit[b];
+                rbox[b] = acc;
+                rcnt[b] = c;
+            }
+            AABB lacc;
+            int lc = 0;
+            for (int b = 1; b < kSpatialBins; ++b) {
+                lacc.grow(bb[b - 1]); lc += entry[b - 1];
+                if (lc == 0 || rcnt[b] == 0 || !lacc.valid() || !rbox[b].valid()) continue;
+                const float cost = c_trav + (lacc.area() * lc + rbox[b].area() * rcnt[b]) / area * c_tri;
+                if (cost < best.cost) {
+                    best.cost = cost; best.axis = ax; best.bin = b; best.pos = plane[b];
+                    best.l = lacc; best.r = rbox[b]; best.nl = lc; best.nr = rcnt[b];
+                }
+            }
+        }
+        return best;
+    }
+
+    // Partition by a spatial split; false when a side would keep every reference
+    // (no progress), in which case L and R are left empty.
+    bool spatial_partition(const std::vector<Ref> &refs, const Split &s, std::vector<Ref> &L, std::vector<Ref> &R)
+    {
+        const int ax = s.axis;
+        const float al = s.l.area(), ar = s.r.area();
+        int64_t added = 0;
+        for (const Ref &r : refs) {
+            if (r.box.hi[ax] <= s.pos) { L.push_back(r); continue; }
+            if (r.box.lo[ax] >= s.pos) { R.push_back(r); continue; }
+            const float c_split = al * s.nl + ar * s.nr;
+            const float c_left = AABB::join(s.l, r.box).area() * s.nl + ar * (s.nr - 1);
+            const float c_right = al * (s.nl - 1) + AABB::join(s.r, r.box).area() * s.nr;
+            if (c_left < c_split && c_left <= c_right) { L.push_back(r); continue; }
+            if (c_right < c_split) { R.push_back(r); continue; }
+            double v[3][3];
+            verts(r.tri, v);
+            const AABB a = AABB::meet(clip_box(v, ax, -INFINITY, s.pos), r.box);
+            const AABB b = AABB::meet(clip_box(v, ax, s.pos, INFINITY), r.box);
+            if (a.nonempty() && b.nonempty()) {
+                L.push_back(make_ref(a, r.tri));
+                R.push_back(make_ref(b, r.tri));
+                ++added;
+            } else if (a.nonempty()) {
+                L.push_back(r);
+            } else {
+                R.push_back(r);
+            }
+        }
+        if (L.empty() || R.empty() || L.size() >= refs.size() || R.size() >= refs.size()) {
+            L.clear(); R.clear();
+            return false;
+        }
+        n_refs += added;
+        return true;
+    }
+
+    int32_t build(std::vector<Ref> &refs, int depth)
     {
         max_depth = std::max(max_depth, depth);
         BNode n;
         AABB cb;
-        for (int32_t i = start; i < end; ++i) { n.box.grow(refs[i].box); cb.grow(refs[i].c); }
-        const int32_t N = end - start;
+        for (const Ref &r : refs) { n.box.grow(r.box); cb.grow(r.c); }
+        const int32_t N = (int32_t)refs.size();
         const int32_t id = (int32_t)nodes.size();
         nodes.push_back(n);
-        float best_cost = INFINITY;
-        int best_axis = -1, best_bin = -1;
-        const float parent_area = std::max(n.box.area(), 1e-30f);
+        const float area = std::max(n.box.area(), 1e-30f);
+        if (depth == 0) root_area = area;
+        Split os, ss;
         if (N > 1) {
-            for (int ax = 0; ax < 3; ++ax) {
-                const float ext = cb.hi[ax] - cb.lo[ax];
-                if (!(ext > 0.0f)) continue;
-                AABB bb[kBins];
-                int cnt[kBins] = { 0 };
-                const float scale = kBins / ext;
-                for (int32_t i = start; i < end; ++i) {
-                    int b = std::min(kBins - 1, (int)((refs[i].c[ax] - cb.lo[ax]) * scale));
-                    cnt[b]++;
-                    bb[b].grow(refs[i].box);
-                }
-                float right_area[kBins];
-                int right_cnt[kBins];
-                AABB acc;
-                int c = 0;
-                for (int b = kBins - 1; b > 0; --b) {
-                    acc.grow(bb[b]); c += cnt[b];
-                    right_area[b] = acc.valid() ? acc.area() : 0.0f;
-                    right_cnt[b] = c;
-                }
-                AABB lacc;
-                int lc = 0;
-                for (int b = 1; b < kBins; ++b) {
-                    lacc.grow(bb[b - 1]); lc += cnt[b - 1];
-                    if (lc == 0 || right_cnt[b] == 0) continue;
-                    float cost = kCTrav + (lacc.area() * lc + right_area[b] * right_cnt[b]) / parent_area * kCTri;
-                    if (cost < best_cost) { best_cost = cost; best_axis = ax; best_bin = b; }
-                }
+            os = object_split(refs, cb, area);
+            if (alpha > 0.0f && n_refs < ref_budget && depth + 1 < kMaxDepth) {
+                const AABB ov = os.axis >= 0 ? AABB::meet(os.l, os.r) : n.box;
+                const float lambda = ov.nonempty() ? ov.area() : 0.0f;
+                if (lambda > alpha * root_area) ss = spatial_split(refs, n.box, area);
             }
         }
-        const float leaf_cost = N * kCTri;
-        bool make_leaf = (N <= kMaxLeaf && leaf_cost <= best_cost) || N == 1 || depth >= kMaxDepth;
-        if (make_leaf && N > kMaxLeaf && depth < kMaxDepth) make_leaf = false;
+        const float best_cost = std::min(os.cost, ss.cost);
+        const float leaf_cost = N * c_tri;
+        bool make_leaf = (N <= max_leaf && leaf_cost <= best_cost) || N == 1 || depth >= kMaxDepth;
+        if (make_leaf && N > max_leaf && depth < kMaxDepth) make_leaf = false;
         if (make_leaf) {
-            nodes[id].start = start;
+            nodes[id].start = (int32_t)leaf_refs.size();
             nodes[id].count = N;
+            leaf_refs.insert(leaf_refs.end(), refs.begin(), refs.end());
             return id;
         }
-        int32_t mid;
-        if (best_axis >= 0) {
-            const float ext = cb.hi[best_axis] - cb.lo[best_axis];
-            const float scale = kBins / ext;
-            const int ax = best_axis, bin = best_bin;
-            const float lo = cb.lo[ax];
-            auto it = std::partition(refs.begin() + start, refs.begin() + end, [&](const Ref &r) {
-                return std::min(kBins - 1, (int)((r.c[ax] - lo) * scale)) < bin;
-            });
-            mid = (int32_t)(it - refs.begin());
-        } else {
-            mid = start + N / 2;  // all centroids coincide: split the list
+        std::vector<Ref> L, R;
+        bool done = ss.cost < os.cost && spatial_partition(refs, ss, L, R);
+        if (!done) {
+            auto mid = refs.begin() + N / 2;   // all centroids coincide: split the list
+            if (os.axis >= 0) {
+                const int ax = os.axis, bin = os.bin;
+                const float lo = cb.lo[ax], scale = kBins / (cb.hi[ax] - cb.lo[ax]);
+                auto it = std::partition(refs.begin(), refs.end(), [&](const Ref &r) {
+                    return std::min(kBins - 1, (int)((r.c[ax] - lo) * scale)) < bin;
+                });
+                if (it != refs.begin() && it != refs.end()) mid = it;
+            }
+            L.assign(refs.begin(), mid);
+            R.assign(mid, refs.end());
         }
-        if (mid == start || mid == end) mid = start + N / 2;
-        int32_t l = build(start, mid, depth + 1);
-        int32_t r = build(mid, end, depth + 1);
+        std::vector<Ref>().swap(refs);
+        const int32_t l = build(L, depth + 1);
+        const int32_t r = build(R, depth + 1);
         nodes[id].child[0] = l;
         nodes[id].child[1] = r;
         return id;
@@ -144,37 +339,50 @@ namespace gadep {
 
 namespace {
 
-struct TreeStats { int32_t leaves = 0, max_leaf = 0, depth = 0; double sah = 0.0; };
+struct TreeStats { int32_t leaves = 0, max_leaf = 0, depth = 0; double sah = 0.0; int64_t refs = 0; };
 
 // Build one BVH over the mesh triangles `ids`; append its nodes and its
-// leaf-ordered triangles to `out` and return the root node index.
-int32_t append_tree(const detmesh_mesh *m, const std::vector<int32_t> &ids, gadep_bvh *out, TreeStats &ts,
-                    gadep_status &st)
+// leaf-ordered triangle records to `out` and return the root node index.
+int32_t append_tree(const detmesh_mesh *m, const std::vector<int32_t> &ids, const gadep_bvh_opts &o,
+                    gadep_bvh *out, TreeStats &ts, gadep_status &st)
 {
     const MeshData &g = m->geo;
-    const int32_t nt = (int32_t)ids.size();
-    if (nt == 0) return -1;
+    const int32_t n_ids = (int32_t)ids.size();
+    if (n_ids == 0) return -1;
     Builder B;
-    B.refs.resize(nt);
-    for (int32_t i = 0; i < nt; ++i) {
-        Ref &r = B.refs[i];
+    B.xyz = m->xyz_f.data();
+    B.tv = g.tri.data();
+    B.max_leaf = o.max_leaf;
+    B.c_trav = o.c_trav;
+    B.c_tri = o.c_tri;
+    B.alpha = o.split_alpha;
+    B.n_refs = n_ids;
+    B.ref_budget = (int64_t)((double)o.max_dup * n_ids);
+    std::vector<Ref> refs(n_ids);
+    for (int32_t i = 0; i < n_ids; ++i) {
+        AABB box;
         const int32_t t = ids[i];
-        for (int j = 0; j < 3; ++j) r.box.grow(&m->xyz_f[3 * g.tri[3 * t + j]]);
-        for (int k = 0; k < 3; ++k) r.c[k] = 0.5f * (r.box.lo[k] + r.box.hi[k]);
-        r.tri = t;
+        for (int j = 0; j < 3; ++j) box.grow(&m->xyz_f[3 * g.tri[3 * t + j]]);
+        refs[i] = make_ref(box, t);
     }
-    B.nodes.reserve(2 * (size_t)nt / kMaxLeaf + 8);
-    B.build(0, nt, 0);
+    B.nodes.reserve(2 * (size_t)n_ids / o.max_leaf + 8);
+    B.build(refs, 0);
     if (B.max_depth >= kMaxDepth) {
         st = fail(GADEP_E_MESH, "bvh: depth limit reached (degenerate mesh?)");
         return -1;
     }
+    const int32_t nt = (int32_t)B.leaf_refs.size();
+    if ((int64_t)out->tris.size() / 12 + nt >= (1 << 27)) {
+        st = fail(GADEP_E_INVAL, "bvh: more than 2^27 triangle records");
+        return -1;
+    }
     ts.depth = std::max(ts.depth, B.max_depth);
+    ts.refs += nt;
     const int32_t tri_base = (int32_t)(out->tris.size() / 12);
     const int32_t node_base = (int32_t)(out->nodes.size() / 16);
     // triangles in leaf order: (v0, region), (v1, mesh triangle id), (v2, 0)
     for (int32_t i = 0; i < nt; ++i) {
-        const int32_t t = B.refs[i].tri;
+        const int32_t t = B.leaf_refs[i].tri;
         out->tri_orig.push_back(t);
         float rec[12];
         for (int j = 0; j < 3; ++j) {
@@ -214,16 +422,16 @@ int32_t append_tree(const detmesh_mesh *m, const std::vector<int32_t> &ids, gade
             for (int k = 0; k < 3; ++k) { lo[1][k] = 1.0f; hi[1][k] = -1.0f; }
             child[1] = leaf_ref(0, 0);
             ts.leaves++; ts.max_leaf = std::max(ts.max_leaf, n.count);
-            ts.sah += n.box.area() / root_area * n.count * kCTri;
+            ts.sah += n.box.area() / root_area * n.count * o.c_tri;
         } else {
-            ts.sah += n.box.area() / root_area * kCTrav;
+            ts.sah += n.box.area() / root_area * o.c_trav;
             for (int c = 0; c < 2; ++c) {
                 const BNode &ch = B.nodes[n.child[c]];
                 pad_box(ch.box, lo[c], hi[c]);
                 if (ch.leaf()) {
                     child[c] = leaf_ref(tri_base + ch.start, ch.count);
                     ts.leaves++; ts.max_leaf = std::max(ts.max_leaf, ch.count);
-                    ts.sah += ch.box.area() / root_area * ch.count * kCTri;
+                    ts.sah += ch.box.area() / root_area * ch.count * o.c_tri;
                 } else {
                     child[c] = dev_of[n.child[c]];
                 }
@@ -258,11 +466,15 @@ std::vector<std::vector<int32_t>> region_triangle_sets(const MeshData &g)
     return sets;
 }
 
-gadep_status build_bvh_host(const detmesh_mesh *m, gadep_bvh *out)
+gadep_status build_bvh_host(const detmesh_mesh *m, const gadep_bvh_opts &o, gadep_bvh *out)
 {
     const MeshData &g = m->geo;
     const int32_t nt = g.n_tri();
     if (nt >= (1 << 26)) return fail(GADEP_E_INVAL, "bvh: at most 2^26 triangles");
+    if (o.max_leaf < 1 || o.max_leaf > 7 || !(o.c_trav >= 0.0f) || !(o.c_tri > 0.0f) || !(o.split_alpha >= 0.0f) ||
+        !(o.max_dup >= 1.0f) || !(o.max_dup <= 16.0f))
+        return fail(GADEP_E_INVAL, "bvh: bad options (max_leaf 1..7, c_tri > 0, c_trav >= 0, split_alpha >= 0, "
+                                   "max_dup in [1, 16])");
     out->nodes.clear();
     out->tris.clear();
     out->tri_orig.clear();
@@ -270,12 +482,12 @@ gadep_status build_bvh_host(const detmesh_mesh *m, gadep_bvh *out)
     TreeStats all_ts, reg_ts;
     std::vector<int32_t> all(nt);
     for (int32_t t = 0; t < nt; ++t) all[t] = t;
-    out->root_all = append_tree(m, all, out, all_ts, st);
+    out->root_all = append_tree(m, all, o, out, all_ts, st);
     if (st != GADEP_OK) return st;
     const auto sets = region_triangle_sets(g);
     std::vector<int32_t> roots(sets.size(), -1);
     for (size_t r = 0; r < sets.size(); ++r) {
-        roots[r] = append_tree(m, sets[r], out, reg_ts, st);
+        roots[r] = append_tree(m, sets[r], o, out, reg_ts, st);
         if (st != GADEP_OK) return st;
     }
     // regions: 0 = world, s + 1 = solid s; (material, active | (group + 1) << 1, parent, root)
@@ -320,10 +532,22 @@ gadep_status build_bvh_host(const detmesh_mesh *m, gadep_bvh *out)
     stt.sah_cost = all_ts.sah;
     stt.node_bytes = (int64_t)stt.n_nodes * 64;
     stt.tri_bytes = (int64_t)(out->tris.size() / 12) * 48;
+    stt.n_refs = all_ts.refs + reg_ts.refs;
+    stt.opts = o;
     return GADEP_OK;
 }
 
 }  // namespace gadep
+
+extern "C" void gadep_bvh_opts_default(gadep_bvh_opts *o)
+{
+    if (!o) return;
+    o->max_leaf = 4;
+    o->c_trav = 1.5f;
+    o->c_tri = 1.0f;
+    o->split_alpha = 0.0f;
+    o->max_dup = 2.0f;
+}
 
 extern "C" gadep_status gadep_bvh_get_stats(const gadep_bvh *b, gadep_bvh_stats *out)
 {
@@ -335,9 +559,12 @@ extern "C" gadep_status gadep_bvh_get_stats(const gadep_bvh *b, gadep_bvh_stats 
 
 namespace {
 
-// Walk one tree: child boxes inside the box the parent stores, leaf boxes contain
-// their triangles; return the multiset of mesh triangle ids in its leaves.
-gadep_status walk_tree(const gadep_bvh *b, int32_t root, std::vector<int32_t> &ids)
+struct LeafBox { int32_t id, rec; float lo[3], hi[3]; };   // mesh triangle, its record
+
+// Walk one tree: child boxes inside the box the parent stores, every leaf box
+// meeting the bounding box of each triangle it holds, no triangle twice in one
+// leaf; append (mesh triangle id, leaf box) for every triangle record.
+gadep_status walk_tree(const gadep_bvh *b, int32_t root, std::vector<LeafBox> &out)
 {
     const int32_t nn = b->stats.n_nodes;
     const int32_t ns = (int32_t)(b->tris.size() / 12);
@@ -362,25 +589,57 @@ gadep_status walk_tree(const gadep_bvh *b, int32_t root, std::vector<int32_t> &i
                     return gadep::fail(GADEP_E_MESH, "bvh: child box of node %d not inside its parent", it.node);
             if (w[c] >= 0) {
                 stack.push_back(Item{ w[c], { lo[0], lo[1], lo[2] }, { hi[0], hi[1], hi[2] } });
-            } else {
-                const int32_t first = (~w[c]) >> 3, cnt = (~w[c]) & 7;
-                if (first < 0 || cnt < 1 || first + cnt > ns) return gadep::fail(GADEP_E_MESH, "bvh: bad leaf range");
-                for (int32_t t = first; t < first + cnt; ++t) {
-                    int32_t id;
-                    std::memcpy(&id, &b->tris[(size_t)t * 12 + 7], 4);
-                    if (id != b->tri_orig[t]) return gadep::fail(GADEP_E_MESH, "bvh: triangle id mismatch");
-                    ids.push_back(id);
-                    for (int j = 0; j < 3; ++j)
-                        for (int k = 0; k < 3; ++k) {
-                            const float v = b->tris[(size_t)t * 12 + 4 * j + k];
-                            if (v < lo[k] || v > hi[k])
-                                return gadep::fail(GADEP_E_MESH, "bvh: triangle outside its leaf box");
-                        }
+                continue;
+            }
+            const int32_t first = (~w[c]) >> 3, cnt = (~w[c]) & 7;
+            if (first < 0 || cnt < 1 || first + cnt > ns) return gadep::fail(GADEP_E_MESH, "bvh: bad leaf range");
+            for (int32_t t = first; t < first + cnt; ++t) {
+                int32_t id;
+                std::memcpy(&id, &b->tris[(size_t)t * 12 + 7], 4);
+                if (id != b->tri_orig[t]) return gadep::fail(GADEP_E_MESH, "bvh: triangle id mismatch");
+                for (int32_t u = first; u < t; ++u)
+                    if (b->tri_orig[u] == id) return gadep::fail(GADEP_E_MESH, "bvh: triangle %d twice in a leaf", id);
+                for (int k = 0; k < 3; ++k) {
+                    float vlo = INFINITY, vhi = -INFINITY;
+                    for (int j = 0; j < 3; ++j) {
+                        const float v = b->tris[(size_t)t * 12 + 4 * j + k];
+                        vlo = std::min(vlo, v);
+                        vhi = std::max(vhi, v);
+                    }
+                    if (vhi < lo[k] || vlo > hi[k]) return gadep::fail(GADEP_E_MESH, "bvh: leaf box misses its triangle");
                 }
+                out.push_back(LeafBox{ id, t, { lo[0], lo[1], lo[2] }, { hi[0], hi[1], hi[2] } });
             }
         }
     }
     return GADEP_OK;
+}
+
+// Every point of a barycentric grid on one triangle (its vertices included)
+// lies in one of the leaf boxes [first, last) that hold the triangle.
+bool covered(const gadep_bvh *b, const LeafBox *first, const LeafBox *last)
+{
+    constexpr int kGrid = 8;
+    const float *v[3];
+    for (int j = 0; j < 3; ++j) v[j] = &b->tris[(size_t)first->rec * 12 + 4 * j];
+    for (int i = 0; i <= kGrid; ++i)
+        for (int j = 0; i + j <= kGrid; ++j) {
+            const int k = kGrid - i - j;
+            float p[3];
+            for (int c = 0; c < 3; ++c) {
+                if (i == kGrid || j == kGrid || k == kGrid) {
+                    p[c] = i == kGrid ? v[0][c] : (j == kGrid ? v[1][c] : v[2][c]);
+                } else {
+                    p[c] = (float)(((double)i * v[0][c] + (double)j * v[1][c] + (double)k * v[2][c]) / kGrid);
+                }
+            }
+            bool in = false;
+            for (const LeafBox *lb = first; lb != last && !in; ++lb)
+                in = p[0] >= lb->lo[0] && p[0] <= lb->hi[0] && p[1] >= lb->lo[1] && p[1] <= lb->hi[1] &&
+                     p[2] >= lb->lo[2] && p[2] <= lb->hi[2];
+            if (!in) return false;
+        }
+    return true;
 }
 
 }  // namespace
@@ -396,15 +655,25 @@ extern "C" gadep_status gadep_bvh_validate(const gadep_bvh *b)
     sets.push_back(all);
     for (size_t r = 0; r < sets.size(); ++r) {
         const int32_t root = r + 1 < sets.size() ? b->regions[4 * r + 3] : b->root_all;
-        std::vector<int32_t> ids;
+        std::vector<LeafBox> boxes;
         if (root >= 0) {
-            gadep_status st = walk_tree(b, root, ids);
+            gadep_status st = walk_tree(b, root, boxes);
             if (st != GADEP_OK) return st;
         }
-        std::sort(ids.begin(), ids.end());
+        std::sort(boxes.begin(), boxes.end(), [](const LeafBox &x, const LeafBox &y) { return x.id < y.id; });
+        std::vector<int32_t> ids;
+        for (const LeafBox &lb : boxes)
+            if (ids.empty() || ids.back() != lb.id) ids.push_back(lb.id);
         std::vector<int32_t> want = sets[r];
         std::sort(want.begin(), want.end());
-        if (ids != want) return gadep::fail(GADEP_E_MESH, "bvh: tree %zu does not hold each of its triangles once", r);
+        if (ids != want) return gadep::fail(GADEP_E_MESH, "bvh: tree %zu does not hold each of its triangles", r);
+        for (size_t i = 0; i < boxes.size();) {
+            size_t j = i;
+            while (j < boxes.size() && boxes[j].id == boxes[i].id) ++j;
+            if (!covered(b, &boxes[i], &boxes[j]))
+                return gadep::fail(GADEP_E_MESH, "bvh: leaf boxes of triangle %d do not cover it", boxes[i].id);
+            i = j;
+        }
     }
     return GADEP_OK;
 }

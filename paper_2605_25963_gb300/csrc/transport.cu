@@ -42,7 +42,7 @@
 
 namespace gadep {
 
-gadep_status build_bvh_host(const detmesh_mesh *m, gadep_bvh *out);
+gadep_status build_bvh_host(const detmesh_mesh *m, const gadep_bvh_opts &o, gadep_bvh *out);
 
 namespace dev {
 template <bool GRAD, bool COUNT>
@@ -573,8 +573,17 @@ extern "C" void gadep_opts_default(gadep_opts *o)
 
 extern "C" gadep_status gadep_bvh_build(const detmesh_mesh *m, int32_t device, gadep_bvh **out)
 {
+    return gadep_bvh_build_opts(m, nullptr, device, out);
+}
+
+extern "C" gadep_status gadep_bvh_build_opts(const detmesh_mesh *m, const gadep_bvh_opts *opts, int32_t device,
+                                             gadep_bvh **out)
+{
     gadep::clear_error();
     if (!m || !out) return fail(GADEP_E_INVAL, "gadep_bvh_build: NULL argument");
+    gadep_bvh_opts o;
+    gadep_bvh_opts_default(&o);
+    if (opts) o = *opts;
     *out = nullptr;
     if (device != -1) {
         int n_dev = 0;
@@ -584,7 +593,7 @@ extern "C" gadep_status gadep_bvh_build(const detmesh_mesh *m, int32_t device, g
     gadep_bvh *b = new (std::nothrow) gadep_bvh();
     if (!b) return fail(GADEP_E_NOMEM, "gadep_bvh_build: out of host memory");
     b->device = device;
-    gadep_status st = gadep::build_bvh_host(m, b);
+    gadep_status st = gadep::build_bvh_host(m, o, b);
     if (st == GADEP_OK && device >= 0) st = gadep::upload_bvh(b);
     if (st != GADEP_OK) { gadep::free_bvh_device(b); delete b; return st; }
     *out = b;

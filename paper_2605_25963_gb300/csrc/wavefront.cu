@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(256) gen_kernel(const Params P, State S)
     constexpr int kPer = kGenChunk / 256;   // ids per thread and chunk
     Ctrl &c = *S.ctrl;
     if (c.done) return;
-    extern __shared__ double4 smem_gen[];
+    extern __shared__ int4 smem_gen[];     // 16-byte aligned: the tallies hold FP64 sums
     __shared__ unsigned long long s_chunk, s_base;
     __shared__ unsigned int s_warp[8];
     BlockTally<false> bt;               // culled histories carry no score

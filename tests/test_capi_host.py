@@ -89,20 +89,41 @@ def test_tables_match_oracle(orc):
 
 
 @pytest.mark.parametrize("name", ["BARE_CYLINDER", "COAX_P", "GRAD_DET"])
-def test_bvh_host_invariants(name):
+@pytest.mark.parametrize("spatial", [False, True])
+def test_bvh_host_invariants(name, spatial):
     m = api.detmesh_build(getattr(W, name))
-    b = api.gadep_bvh_build(m, device=-1)
+    b = api.gadep_bvh_build(m, device=-1, split_alpha=1e-5 if spatial else 0.0, max_dup=2.0)
     b.validate()
     st = b.stats()
     assert st["n_tri"] == len(m.arrays()[1])
     assert st["max_leaf_tris"] <= 4
     assert st["max_depth"] < 60
     # one tree over every triangle + one per region over its own and its children's
-    # triangles: each triangle is stored three times (global, own region, parent region)
-    assert st["node_bytes"] == 64 * st["n_nodes"] and st["tri_bytes"] == 3 * 48 * st["n_tri"]
+    # triangles: each triangle is in three trees (global, own region, parent region);
+    # spatial splits add copies, within the budget of max_dup records per triangle
+    assert st["node_bytes"] == 64 * st["n_nodes"] and st["tri_bytes"] == 48 * st["n_refs"]
+    if spatial:
+        assert 3 * st["n_tri"] <= st["n_refs"] <= 2 * 3 * st["n_tri"] + 64
+    else:
+        assert st["n_refs"] == 3 * st["n_tri"]
     n_trees = 1 + st["n_region"]
     assert st["n_nodes"] + 1 <= st["n_leaves"] <= st["n_nodes"] + n_trees
-    assert st["n_leaves"] >= 3 * st["n_tri"] / 4
+    assert st["n_leaves"] >= st["n_refs"] / 4
+
+
+def test_bvh_options():
+    m = api.detmesh_build(W.COAX_P)
+    for kw in (dict(max_leaf=0), dict(max_leaf=8), dict(c_tri=0.0), dict(split_alpha=-1.0), dict(max_dup=0.5)):
+        with pytest.raises(capi.GadepError):
+            api.gadep_bvh_build(m, device=-1, **kw)
+    with pytest.raises(TypeError):
+        api.gadep_bvh_build(m, device=-1, leaf=2)
+    b = api.gadep_bvh_build(m, device=-1, max_leaf=2, c_trav=0.5, split_alpha=0.0)
+    b.validate()
+    st = b.stats()
+    assert st["max_leaf_tris"] <= 2 and st["opts"]["max_leaf"] == 2 and st["opts"]["c_trav"] == 0.5
+    d = api.gadep_bvh_build(m, device=-1).stats()["opts"]
+    assert d == {"max_leaf": 4, "c_trav": 1.5, "c_tri": 1.0, "split_alpha": 0.0, "max_dup": 2.0}
 
 
 def test_invalid_parameters_rejected():
