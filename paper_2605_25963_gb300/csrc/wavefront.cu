@@ -700,10 +700,10 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const Params P, State S, 
         // ---- traversal (while-while), left early when too few lanes remain ----
         while (has) {
             while ((unsigned)node < (unsigned)kSentinel) {
-                const float4 n0 = __ldg(nodes + 4 * node + 0);
-                const float4 n1 = __ldg(nodes + 4 * node + 1);
-                const float4 n2 = __ldg(nodes + 4 * node + 2);
-                const int4 n3 = __ldg(reinterpret_cast<const int4 *>(nodes) + 4 * node + 3);
+                float4 n0, n1, n2, n3f;
+                ldg256(nodes + 4 * node, n0, n1);
+                ldg256(nodes + 4 * node + 2, n2, n3f);
+                const int4 n3 = make_int4(__float_as_int(n3f.x), __float_as_int(n3f.y), 0, 0);
                 ++nn;
                 const float a0 = fmaf(n0.x, ix, -oix), a1 = fmaf(n0.y, ix, -oix);
                 const float a2 = fmaf(n0.z, iy, -oiy), a3 = fmaf(n0.w, iy, -oiy);
