@@ -57,12 +57,30 @@ typedef struct {
     int n_mat, n_grid;
     double lnE_min, lnE_max;
     float *mu;
+    /* charged particles (continuous slowing down, see orc_xs.c): CSDA range in mm
+       at unit density scale on e_n log-spaced kinetic energies from ORC_E_TMIN to
+       E_max, [n_mat][e_n], FP64; a row of +inf for a material with no stopping
+       (vacuum); e_n = 0 when the tables were not built from material codes */
+    int e_n;
+    double lnT_min, lnT_max;
+    double *e_range;
 } orc_tables;
 orc_tables *orc_tables_build(const int *codes, int n_mat, int n_grid, double E_min, double E_max);
 orc_tables *orc_tables_from_array(int n_mat, int n_grid, double E_min, double E_max, const float *mu);
 void        orc_tables_free(orc_tables *t);
 /* interpolated mu (pe, compton, pair) of material m at E, FP64 arithmetic on the stored values */
 void        orc_tables_eval(const orc_tables *t, int m, double E_keV, double out[3]);
+
+/* charged particles: below ORC_E_TMIN a particle deposits where it is */
+#define ORC_E_TMIN 1.0   /* keV */
+/* mass stopping power of material `code` for an electron of kinetic energy T:
+   collision part and total (collision + radiative), MeV cm^2/g; -1 for an
+   unknown code, 0 with both zero for vacuum */
+int    orc_e_stopping(int code, double T_keV, double *s_col, double *s_tot);
+/* CSDA range (mm, unit density scale) of table material m at T; +inf for vacuum */
+double orc_e_range(const orc_tables *t, int m, double T_keV);
+/* kinetic energy left after a path of L mm (unit density scale) in material m */
+double orc_e_energy_after(const orc_tables *t, int m, double T_keV, double L_mm);
 
 /* ---------------- detector meshes (Sec. 2.2-2.3) ---------------- */
 enum { ORC_DET_BARE_CYLINDER = 0, ORC_DET_COAX = 1 };
@@ -134,6 +152,8 @@ typedef struct {
     int      step_cap;             /* segments per history */
     int      n_group;              /* density groups, <= 8 */
     double   group_scale[8];
+    int      e_model;              /* 0: charged particles deposit at their birth point;
+                                      1: continuous-slowing-down tracks (orc_transport.c) */
 } orc_opts;
 
 typedef struct {
@@ -152,6 +172,13 @@ typedef struct {
 int orc_transport(const orc_mesh *m, const orc_tables *t, const orc_source *src,
                   const orc_opts *o, uint64_t n_hist, int n_threads,
                   orc_tally *out, uint32_t *spectrum, double *edep);
+
+/* One charged-particle line of e_model 1 (orc_transport.c): `weight` particles of
+   kinetic energy T from p along unit u, born in region `region` (solid index,
+   -1 = world), density scales from o.  out = (active deposit, all deposits,
+   escaped), keV.  Returns 0, or nonzero on a geometry error. */
+int orc_e_track(const orc_mesh *m, const orc_tables *t, const orc_opts *o, const double p[3], const double u[3],
+                double T_keV, double weight, int region, double out[3]);
 
 #ifdef __cplusplus
 }

@@ -61,7 +61,8 @@ class MeshC(C.Structure):
 
 class TablesC(C.Structure):
     _fields_ = [("n_mat", C.c_int), ("n_grid", C.c_int), ("lnE_min", C.c_double),
-                ("lnE_max", C.c_double), ("mu", C.POINTER(C.c_float))]
+                ("lnE_max", C.c_double), ("mu", C.POINTER(C.c_float)), ("e_n", C.c_int),
+                ("lnT_min", C.c_double), ("lnT_max", C.c_double), ("e_range", C.POINTER(C.c_double))]
 
 
 class SourceC(C.Structure):
@@ -73,7 +74,8 @@ class OptsC(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("history_offset", C.c_uint64), ("instance", C.c_uint32),
                 ("energy_keV", C.c_double), ("e_cut_keV", C.c_double),
                 ("fep_delta_keV", C.c_double), ("e_max_keV", C.c_double), ("n_bins", C.c_int),
-                ("step_cap", C.c_int), ("n_group", C.c_int), ("group_scale", C.c_double * 8)]
+                ("step_cap", C.c_int), ("n_group", C.c_int), ("group_scale", C.c_double * 8),
+                ("e_model", C.c_int)]
 
 
 class TallyC(C.Structure):
@@ -118,6 +120,13 @@ def lib():
         L.orc_tables_free.argtypes = [C.POINTER(TablesC)]
         L.orc_tables_eval.argtypes = [C.POINTER(TablesC), C.c_int, C.c_double,
                                       C.POINTER(C.c_double)]
+        L.orc_e_stopping.argtypes = [C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.orc_e_range.restype = C.c_double
+        L.orc_e_range.argtypes = [C.POINTER(TablesC), C.c_int, C.c_double]
+        L.orc_e_energy_after.restype = C.c_double
+        L.orc_e_energy_after.argtypes = [C.POINTER(TablesC), C.c_int, C.c_double, C.c_double]
+        L.orc_e_track.argtypes = [C.POINTER(MeshC), C.POINTER(TablesC), C.POINTER(OptsC), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double), C.c_double, C.c_double, C.c_int, C.POINTER(C.c_double)]
         L.orc_mesh_build.argtypes = [C.POINTER(DetParams), C.POINTER(C.POINTER(MeshC))]
         L.orc_mesh_from_arrays.restype = C.POINTER(MeshC)
         L.orc_mesh_from_arrays.argtypes = [C.c_int, C.POINTER(C.c_double), C.c_int,
@@ -200,6 +209,20 @@ class Tables:
         t = ptr.contents
         self.n_mat, self.n_grid = t.n_mat, t.n_grid
         self.lnE_min, self.lnE_max = t.lnE_min, t.lnE_max
+
+    def e_range(self, m, T_keV):
+        """CSDA range (mm, unit density scale) of table material m at T."""
+        return lib().orc_e_range(self._p, m, T_keV)
+
+    def e_energy_after(self, m, T_keV, L_mm):
+        """Kinetic energy left after L mm in table material m."""
+        return lib().orc_e_energy_after(self._p, m, T_keV, L_mm)
+
+    def e_range_array(self):
+        """[n_mat][e_n] CSDA ranges (mm) and the kinetic energies of the grid (keV)."""
+        t = self._p.contents
+        a = np.ctypeslib.as_array(t.e_range, shape=(t.n_mat * t.e_n,)).reshape(t.n_mat, t.e_n).copy()
+        return a, np.exp(np.linspace(t.lnT_min, t.lnT_max, t.e_n))
 
     @classmethod
     def build(cls, codes, n_grid=1000, E_min=10.0, E_max=3000.0):
@@ -412,10 +435,40 @@ class Result:
         return max(m2 - m * m, 0.0) ** 0.5 / n ** 0.5
 
 
+E_TMIN = 1.0   # keV: charged particles below this deposit where they are
+
+
+def e_stopping(code, T_keV):
+    """(collision, total) mass stopping power of material `code` for an electron
+    of kinetic energy T, MeV cm^2/g."""
+    c, t = C.c_double(), C.c_double()
+    if lib().orc_e_stopping(code, T_keV, C.byref(c), C.byref(t)) != 0:
+        raise ValueError("unknown material code %r" % code)
+    return c.value, t.value
+
+
+def e_track(mesh: Mesh, tables: Tables, p, u, T_keV, region, weight=1.0, group_scale=()):
+    """One charged-particle line (e_model 1): returns (active deposit, all deposits,
+    escaped) in keV; raises on a geometry error."""
+    o = OptsC()
+    o.e_model = 1
+    o.n_group = len(group_scale)
+    for i, s in enumerate(group_scale):
+        o.group_scale[i] = s
+    pp = (C.c_double * 3)(*p)
+    uu = (C.c_double * 3)(*u)
+    out = (C.c_double * 3)()
+    rc = lib().orc_e_track(mesh._p, tables._p, C.byref(o), pp, uu, T_keV, weight, region, out)
+    if rc != 0:
+        raise ValueError("oracle e_track failed: %d" % rc)
+    return tuple(out)
+
+
 def transport(mesh: Mesh, tables: Tables, src: Source, energy, n_hist, seed=1, history_offset=0,
               instance=0, e_cut=10.0, fep_delta=0.01, n_bins=4096, e_max=3000.0, step_cap=10000,
-              group_scale=(), n_threads=None, want_edep=False) -> Result:
+              group_scale=(), n_threads=None, want_edep=False, e_model=0) -> Result:
     o = OptsC()
+    o.e_model = e_model
     o.seed, o.history_offset, o.instance = seed, history_offset, instance
     o.energy_keV, o.e_cut_keV, o.fep_delta_keV, o.e_max_keV = energy, e_cut, fep_delta, e_max
     o.n_bins, o.step_cap = n_bins, step_cap

@@ -15,7 +15,9 @@
  *   interaction process chosen by partial attenuation coefficients,
  *               photoabsorption (deposit E), Compton (Kahn sampler, deposit
  *               E - E'), pair production (deposit E - 2 mc^2, two 511 keV
- *               photons back to back); charged particles deposit locally;
+ *               photons back to back); charged particles deposit locally
+ *               (e_model 0) or run continuous-slowing-down tracks (e_model 1,
+ *               below);
  *   scoring     energy deposited in active solids is summed per history and
  *               binned; a history is in the full-energy peak when
  *               E0 - E_dep <= fep_delta (host scoring, Fig. 4).
@@ -25,6 +27,25 @@
  * every parity query along it (the same intersections the rule asks for).
  * At each crossing the oracle also evaluates the nesting-tree rule (entering
  * solid s -> s, leaving s -> parent of s) and counts disagreements.
+ *
+ * Charged-particle tracks (e_model 1; the stand-in for the paper's electron
+ * and positron transport, stopping powers and ranges in orc_xs.c).  Each
+ * interaction sets particles in motion: photoabsorption one electron of
+ * T = E along the photon's direction (binding energy neglected, as in the
+ * local deposit); Compton one electron of T = E - E' along E d - E' d'
+ * (momentum conservation); pair production an electron and a positron of
+ * T = (E - 2 mc^2) / 2 each, both along the photon's direction, so one line
+ * carries twice the deposits (the annihilation photons still start at the
+ * interaction point).  A particle with T < ORC_E_TMIN deposits at its birth
+ * point in the photon's region.  Otherwise it runs straight ahead: the regions
+ * along its line come from the same crossings and parity rule as a photon
+ * flight; in each region it goes as far as its CSDA range (divided by the
+ * region's density scale) allows, depositing T - T' where T' is what is left
+ * at the next boundary; it stops when the range runs out (depositing the
+ * rest there) or falls below ORC_E_TMIN (depositing the rest in the region it
+ * has entered), and what leaves the mesh escapes.  Vacuum takes no energy.
+ * The tracks draw no random numbers, so the photon histories are the same in
+ * both models.
  *
  * Density-perturbation scores: with mu of every solid of group p scaled by
  * s_p, d ln(track probability)/d s_p = (collisions in p)/s_p
@@ -354,9 +375,63 @@ typedef struct {
     const orc_source *src;
     const orc_opts *o;
     hit_t *buf; int cap;
+    hit_t *ebuf; int ecap;      /* crossings of a charged-particle line */
 } ctx_t;
 
 typedef struct { double edep; int fep, err; } hist_out;
+
+#define ORC_E_MAX_CROSSINGS 256
+
+/* One charged-particle line: `weight` particles of kinetic energy T each from
+   p along unit u, born in the photon's region `region0`.  Adds the deposits to
+   edep (active regions) and dep_all, what leaves the mesh to esc.  Returns
+   nonzero on a geometry error. */
+static int e_track(ctx_t *cx, const double p[3], const double u[3], double T, double weight, int region0,
+                   double *edep, double *dep_all, double *esc)
+{
+    const orc_mesh *m = cx->sc->m;
+    const orc_opts *o = cx->o;
+    if (T < ORC_E_TMIN) {
+        *dep_all += weight * T;
+        if (region0 >= 0 && m->solid_active[region0]) *edep += weight * T;
+        return 0;
+    }
+    uint64_t dup = 0;
+    int n = collect_hits(cx->sc, p, u, &cx->ebuf, &cx->ecap, &dup);
+    const hit_t *h = cx->ebuf;
+    int region = parity_region(h, 0, n, m->n_solid);
+    double t_cur = 0.0;
+    for (int i = 0; i <= ORC_E_MAX_CROSSINGS; ++i) {
+        int active = region >= 0 && m->solid_active[region];
+        if (T < ORC_E_TMIN) {
+            *dep_all += weight * T;
+            if (active) *edep += weight * T;
+            return 0;
+        }
+        int mat = region >= 0 ? m->solid_material[region] : 0;
+        int grp = region >= 0 ? m->solid_group[region] : -1;
+        double sc = (grp >= 0 && grp < o->n_group) ? o->group_scale[grp] : 1.0;
+        double reach = orc_e_range(cx->xs, mat, T) / sc;
+        double t_next = i < n ? h[i].t : INFINITY;
+        if (reach < INFINITY && t_next - t_cur >= reach) {   /* stops in this region */
+            *dep_all += weight * T;
+            if (active) *edep += weight * T;
+            return 0;
+        }
+        if (i == n) {                            /* leaves the mesh (only through vacuum) */
+            if (region != -1) return 1;
+            *esc += weight * T;
+            return 0;
+        }
+        double T2 = orc_e_energy_after(cx->xs, mat, T, (t_next - t_cur) * sc);
+        *dep_all += weight * (T - T2);
+        if (active) *edep += weight * (T - T2);
+        T = T2;
+        t_cur = t_next;
+        region = parity_region(h, i + 1, n, m->n_solid);
+    }
+    return 1;
+}
 
 static void run_history(ctx_t *cx, uint64_t hid, orc_tally *T, uint32_t *spec, hist_out *ho)
 {
@@ -418,20 +493,32 @@ static void run_history(ctx_t *cx, uint64_t hid, orc_tally *T, uint32_t *spec, h
                         else T->n_first_pair++;
                     }
                     double dep = 0.0;
+                    /* charged particles of e_model 1: kinetic energy, direction, count */
+                    double eT = 0.0, eu[3] = { dir[0], dir[1], dir[2] }, ew = 1.0;
                     if (proc == 0) {
-                        dep = E; E = 0.0; alive = 0;
+                        if (o->e_model) eT = E;
+                        else dep = E;
+                        E = 0.0; alive = 0;
                     } else if (proc == 1) {
                         double k = E / ORC_MEC2, x;
                         if (kahn(&r, k, &x) != 0) { err = 1; break; }
                         double c = 1.0 - (x - 1.0) / k;
                         double phi = 2.0 * ORC_PI * rng_u(&r);
                         double Ep = E / x;
-                        dep = E - Ep;
                         rotate(dir, c, phi);
+                        if (o->e_model) {
+                            eT = E - Ep;
+                            double q[3] = { E * eu[0] - Ep * dir[0], E * eu[1] - Ep * dir[1], E * eu[2] - Ep * dir[2] };
+                            double ql = sqrt(dot3(q, q));
+                            if (ql > 0.0) { eu[0] = q[0] / ql; eu[1] = q[1] / ql; eu[2] = q[2] / ql; }
+                        } else {
+                            dep = E - Ep;
+                        }
                         E = Ep;
                         if (E < o->e_cut_keV) { dep += E; E = 0.0; alive = 0; }
                     } else {
-                        dep = E - 2.0 * ORC_MEC2;
+                        if (o->e_model) { eT = 0.5 * (E - 2.0 * ORC_MEC2); ew = 2.0; }
+                        else dep = E - 2.0 * ORC_MEC2;
                         double nd[3];
                         iso_dir(&r, nd);
                         E = ORC_MEC2;
@@ -443,6 +530,7 @@ static void run_history(ctx_t *cx, uint64_t hid, orc_tally *T, uint32_t *spec, h
                     }
                     dep_all += dep;
                     if (active) edep += dep;
+                    if (eT > 0.0 && e_track(cx, p, eu, eT, ew, region, &edep, &dep_all, &esc) != 0) { err = 1; break; }
                     memcpy(pos, p, sizeof(p));
                     carried = region;
                     flight_over = 1;
@@ -503,6 +591,21 @@ static void run_history(ctx_t *cx, uint64_t hid, orc_tally *T, uint32_t *spec, h
     ho->edep = edep; ho->fep = fep; ho->err = 0;
 }
 
+int orc_e_track(const orc_mesh *m, const orc_tables *t, const orc_opts *o, const double p[3], const double u[3],
+                double T_keV, double weight, int region, double out[3])
+{
+    if (!m || !t || !o || !out || t->e_n < 2 || m->n_solid > MAX_SOLIDS) return -1;
+    scene_t sc;
+    scene_init(&sc, m);
+    ctx_t cx = { &sc, t, NULL, o, NULL, 0, NULL, 0 };
+    out[0] = out[1] = out[2] = 0.0;
+    int rc = e_track(&cx, p, u, T_keV, weight, region, &out[0], &out[1], &out[2]);
+    free(cx.buf);
+    free(cx.ebuf);
+    scene_free(&sc);
+    return rc;
+}
+
 /* ---------- threads ---------- */
 
 typedef struct {
@@ -515,7 +618,7 @@ typedef struct {
 static void *worker(void *arg)
 {
     job_t *j = (job_t *)arg;
-    ctx_t cx = { j->sc, j->xs, j->src, j->o, NULL, 0 };
+    ctx_t cx = { j->sc, j->xs, j->src, j->o, NULL, 0, NULL, 0 };
     const uint64_t block = 256;
     for (uint64_t b0 = (uint64_t)j->tid * block; b0 < j->n_hist; b0 += (uint64_t)j->n_threads * block) {
         uint64_t b1 = b0 + block < j->n_hist ? b0 + block : j->n_hist;
@@ -526,6 +629,7 @@ static void *worker(void *arg)
         }
     }
     free(cx.buf);
+    free(cx.ebuf);
     return NULL;
 }
 
@@ -535,6 +639,7 @@ int orc_transport(const orc_mesh *m, const orc_tables *t, const orc_source *src,
 {
     if (!m || !t || !src || !o || !out || n_threads < 1 || m->n_solid > MAX_SOLIDS) return -1;
     if (o->n_group > 8 || o->n_bins < 1 || o->step_cap < 1) return -1;
+    if (o->e_model != 0 && (o->e_model != 1 || t->e_n < 2)) return -1;
     for (int s = 0; s < m->n_solid; ++s)
         if (m->solid_material[s] < 0 || m->solid_material[s] >= t->n_mat) return -1;
     memset(out, 0, sizeof(*out));
