@@ -183,6 +183,9 @@ def measure_forms(dev, scale=1.0):
     stress: the gradient geometry at 1024 segments with a contact groove and a
     bolted flange (~1e6 triangles), 8 energies x 1.25e8 histories: per-instance
     runs vs one batched plan, plain and with gradients.
+    electrons: the coax workload's 4 energies x 2.5e7 histories with charged
+    particles tracked in the continuous-slowing-down approximation (e_model 1)
+    vs deposited at the interaction point; the FEPE of both.
     """
     import torch
     from paper_2605_25963_gb300 import api, batch
@@ -226,6 +229,30 @@ def measure_forms(dev, scale=1.0):
     out["gradient"] = {"histories": n4 * len(items4), "plain_s": t_p, "grad_s": t_g,
                        "grad_vs_plain": t_p / t_g, "grad_vs_central_fd": (1 + 2 * 4) * t_p / t_g,
                        "per_energy": dict(zip([str(E) for E in W.GRAD_ENERGIES], grads))}
+    # ---- electrons: CSDA tracks vs local deposition, same histories ----
+    m6 = api.detmesh_build(W.COAX_P)
+    b6 = api.gadep_bvh_build(m6, dev)
+    n6 = max(1, int(25_000_000 * scale))
+    times6, fepe6 = {}, {}
+    for em in (0, 1):
+        o6 = api.make_opts(e_model=em)
+        api.gadep_run(b6, mats, W.COAX_POINT_25, W.COAX_ENERGIES[0], n6, opts=o6)      # warm-up
+        plans = [api.Plan(b6, mats, api.make_instances([(E, W.COAX_POINT_25, n6, i, [])]), o6)
+                 for i, E in enumerate(W.COAX_ENERGIES)]
+        torch.cuda.synchronize()
+        a6, e6 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a6.record()
+        for p6 in plans:
+            p6.launch()
+        e6.record()
+        torch.cuda.synchronize()
+        times6[em] = a6.elapsed_time(e6) / 1e3
+        fepe6[em] = [p6.results(want_spectra=False)[0][0]["fepe"] for p6 in plans]
+        del plans
+    h6 = n6 * len(W.COAX_ENERGIES)
+    out["electrons"] = {"histories": h6, "local_hist_per_s": h6 / times6[0], "csda_hist_per_s": h6 / times6[1],
+                        "csda_vs_local": times6[0] / times6[1],
+                        "fepe_local": fepe6[0], "fepe_csda": fepe6[1]}
     # ---- stress: ~1e6-triangle mesh, 8 energies, batched and with gradients ----
     t0 = time.perf_counter()
     m5 = api.detmesh_build(W.STRESS_DET)

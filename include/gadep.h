@@ -236,12 +236,35 @@ gadep_status gadep_nearest_hit(const gadep_bvh *b, const float *rays, const int3
 /* Attenuation tables on a log grid: mu[n_mat][3][n_grid] host memory (pe, Compton,
  * pair, mm^-1 at unit density), indexed by the solids' material codes.  Linear
  * interpolation in ln E, end intervals clamped; mu_pair is taken as 0 at and below
- * 2 m_e c^2. */
+ * 2 m_e c^2.
+ * Charged particles (used only with gadep_opts.e_model = 1): e_range[n_mat][e_n]
+ * host memory, the CSDA range in mm at unit density of an electron of kinetic
+ * energy T_k = exp(ln T_min + k (ln T_max - ln T_min) / (e_n - 1)), strictly
+ * increasing in k, +inf on every row of a material that does not slow charged
+ * particles (vacuum); gadep_erange_build fills it.  e_range NULL (e_n 0) when
+ * not given. */
 typedef struct {
     int32_t n_mat, n_grid;
     double  E_min, E_max;
     const float *mu;
+    int32_t e_n;
+    double  T_min, T_max;
+    const float *e_range;
 } gadep_materials;
+
+/* CSDA ranges of electrons for the charged-particle model (e_model 1), the
+ * stand-in for the paper's electron transport (Sec. 2.4.1 physics list), whose
+ * evaluated data are not available: mass stopping power
+ *   S(T) = S_col(T) (1 + Z_r T / 800 MeV),
+ * S_col the Bethe formula for electrons in Rohrlich-Carlson form (ICRU Report
+ * 37) without the density-effect term, mean excitation energies Ge 350 eV,
+ * Al 166 eV, Cu 322 eV, water 75 eV; the radiative share after Attix, with
+ * Z_r = sum n Z^2 / sum n Z; R(T) = T_min / S(T_min) + integral from T_min to
+ * T of dT' / S(T'), divided by the density.  range[n_mat][e_n] (mm), computed
+ * in FP64, stored as FP32; +inf rows for vacuum.  GADEP_E_INVAL for unknown
+ * codes, e_n < 2, T_min <= 0 or T_max <= T_min. */
+gadep_status gadep_erange_build(const int32_t *codes, int32_t n_mat, int32_t e_n, double T_min, double T_max,
+                                float *range);
 
 enum { GADEP_SRC_POINT = 0, GADEP_SRC_DISK = 1, GADEP_SRC_PRISM = 2, GADEP_SRC_PENCIL = 3 };
 /* Source: POINT at pos, isotropic.  DISK: uniform in the disk of `radius` centred
@@ -275,6 +298,17 @@ typedef struct {
     int32_t  n_group;         /* density groups scored by gadep_grad (<= 4) */
     float    group_scale[GADEP_MAX_GROUPS];  /* density scale per group (default 1) */
     int32_t  wf_slots;        /* wavefront variant: photon slots in device memory (0 = 2^20) */
+    int32_t  e_model;         /* charged particles set in motion by photon interactions:
+                                 0 (default) deposit their kinetic energy at the interaction point;
+                                 1 run straight ahead in the continuous-slowing-down
+                                 approximation, depositing region by region along the
+                                 mesh (needs gadep_materials.e_range; not with gadep_grad
+                                 or gadep_run_noalloc).  Photoabsorption: one electron of
+                                 T = E along the photon; Compton: one electron of T = E - E'
+                                 along E d - E' d'; pair: electron and positron of
+                                 (E - 2 mc^2) / 2 each along the photon (annihilation at the
+                                 interaction point).  Below T_min a particle deposits where
+                                 it is; what leaves the mesh escapes. */
 } gadep_opts;
 
 /* Fill *o with the defaults above (seed 1, offset 0, variant AUTO, scales 1). */

@@ -121,18 +121,34 @@ def gadep_xs_build(codes=W.MATERIAL_CODES, n_grid=W.TABLE_N_GRID, E_min=W.TABLE_
     return mu
 
 
-class Materials:
-    """Attenuation tables mu[n_mat][3][n_grid] (host, float32) on a log grid."""
+def gadep_erange_build(codes=W.MATERIAL_CODES, e_n=W.ERANGE_N, T_min=W.ERANGE_T_MIN, T_max=W.TABLE_E_MAX):
+    """CSDA ranges [n_mat][e_n] (mm, unit density) of electrons for e_model 1."""
+    c = np.ascontiguousarray(codes, dtype=np.int32)
+    r = np.zeros((len(c), e_n), dtype=np.float32)
+    check(capi.load().gadep_erange_build(_ptr(c, C.c_int32), len(c), e_n, T_min, T_max, _ptr(r, C.c_float)))
+    return r
 
-    def __init__(self, mu, E_min=W.TABLE_E_MIN, E_max=W.TABLE_E_MAX):
+
+class Materials:
+    """Attenuation tables mu[n_mat][3][n_grid] (host, float32) on a log grid, and
+    optionally the charged-particle ranges e_range[n_mat][e_n] on [T_min, T_max]."""
+
+    def __init__(self, mu, E_min=W.TABLE_E_MIN, E_max=W.TABLE_E_MAX, e_range=None, T_min=W.ERANGE_T_MIN,
+                 T_max=W.TABLE_E_MAX):
         self.mu = np.ascontiguousarray(mu, dtype=np.float32)
         self.E_min, self.E_max = E_min, E_max
+        self.e_range = None if e_range is None else np.ascontiguousarray(e_range, dtype=np.float32)
+        self.T_min, self.T_max = T_min, T_max
         self.c = capi.gadep_materials(self.mu.shape[0], self.mu.shape[2], E_min, E_max,
                                       _ptr(self.mu, C.c_float))
+        if self.e_range is not None:
+            assert self.e_range.shape[0] == self.mu.shape[0]
+            self.c.e_n, self.c.T_min, self.c.T_max = self.e_range.shape[1], T_min, T_max
+            self.c.e_range = _ptr(self.e_range, C.c_float)
 
     @classmethod
     def default(cls):
-        return cls(gadep_xs_build())
+        return cls(gadep_xs_build(), e_range=gadep_erange_build())
 
 
 # ---------------- BVH ----------------

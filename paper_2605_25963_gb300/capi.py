@@ -19,7 +19,7 @@ MAX_GROUPS = 8
 # every symbol include/gadep.h declares
 EXPORTS = (
     "gadep_last_error", "gadep_abi_version", "detmesh_build", "detmesh_from_arrays", "detmesh_get",
-    "detmesh_solid_stats", "detmesh_locate", "detmesh_destroy", "gadep_xs_build", "gadep_bvh_build",
+    "detmesh_solid_stats", "detmesh_locate", "detmesh_destroy", "gadep_xs_build", "gadep_erange_build", "gadep_bvh_build",
     "gadep_bvh_build_opts", "gadep_bvh_opts_default", "gadep_bvh_get_stats", "gadep_bvh_validate", "gadep_bvh_destroy", "gadep_nearest_hit",
     "gadep_opts_default", "gadep_run", "gadep_run_batch", "gadep_grad", "gadep_plan_create",
     "gadep_plan_launch", "gadep_plan_results", "gadep_plan_shape", "gadep_plan_destroy",
@@ -67,7 +67,8 @@ class gadep_bvh_stats(C.Structure):
 
 class gadep_materials(C.Structure):
     _fields_ = [("n_mat", C.c_int32), ("n_grid", C.c_int32), ("E_min", C.c_double),
-                ("E_max", C.c_double), ("mu", C.POINTER(C.c_float))]
+                ("E_max", C.c_double), ("mu", C.POINTER(C.c_float)), ("e_n", C.c_int32),
+                ("T_min", C.c_double), ("T_max", C.c_double), ("e_range", C.POINTER(C.c_float))]
 
 
 class gadep_source(C.Structure):
@@ -81,7 +82,7 @@ class gadep_opts(C.Structure):
                 ("fep_delta_keV", C.c_float), ("e_max_keV", C.c_float), ("n_bins", C.c_int32),
                 ("step_cap", C.c_int32), ("variant", C.c_int32), ("block", C.c_int32),
                 ("chunk", C.c_int32), ("blocks_per_sm", C.c_int32), ("n_group", C.c_int32),
-                ("group_scale", C.c_float * MAX_GROUPS), ("wf_slots", C.c_int32)]
+                ("group_scale", C.c_float * MAX_GROUPS), ("wf_slots", C.c_int32), ("e_model", C.c_int32)]
 
 
 class gadep_result(C.Structure):
@@ -135,6 +136,7 @@ def load(build_if_missing: bool = True):
         "detmesh_locate": (st, [vp, P(C.c_double), P(C.c_int32)]),
         "detmesh_destroy": (None, [vp]),
         "gadep_xs_build": (st, [P(C.c_int32), C.c_int32, C.c_int32, C.c_double, C.c_double, P(C.c_float)]),
+        "gadep_erange_build": (st, [P(C.c_int32), C.c_int32, C.c_int32, C.c_double, C.c_double, P(C.c_float)]),
         "gadep_bvh_build": (st, [vp, C.c_int32, P(vp)]),
         "gadep_bvh_build_opts": (st, [vp, P(gadep_bvh_opts), C.c_int32, P(vp)]),
         "gadep_bvh_opts_default": (None, [P(gadep_bvh_opts)]),

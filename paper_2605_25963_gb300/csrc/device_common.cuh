@@ -253,10 +253,10 @@ __device__ __forceinline__ void leaf_test(const float4 *__restrict__ tris, int r
     }
 }
 
-// Nearest triangle along o + t d with t_min < t (exclusive) in the tree rooted at
-// `root` (-1: empty), skipping mesh triangle `exclude`.  Returns the triangle slot
-// or -1; t_hit / entering set on a hit.  Sets ERR_STACK in err if the stack would
-// overflow (query abandoned).
+// Nearest triangle along o + t d with t_min < t < t_max (exclusive) in the tree
+// rooted at `root` (-1: empty), skipping mesh triangle `exclude`.  Returns the
+// triangle slot or -1; t_hit / entering set on a hit.  Sets ERR_STACK in err if
+// the stack would overflow (query abandoned).
 // Loop structure after Aila & Laine (HPG 2009): an inner-node loop that runs
 // until every lane of the warp holds a leaf (postponing at most one leaf per
 // lane), then a leaf loop, so lanes execute node steps and triangle tests in
@@ -267,7 +267,7 @@ __device__ __forceinline__ int traverse(const float4 *__restrict__ nodes,
                                         const float4 *__restrict__ planes, int root, float ox, float oy,
                                         float oz, float dx, float dy, float dz, float t_min,
                                         int exclude, float &t_hit, bool &entering, uint32_t &err,
-                                        TravStats &st)
+                                        TravStats &st, float t_max = INFINITY)
 {
     if (root < 0) return -1;
     const Shear sh = make_shear(dx, dy, dz);
@@ -275,7 +275,7 @@ __device__ __forceinline__ int traverse(const float4 *__restrict__ nodes,
     const float iy = 1.0f / (fabsf(dy) > 1e-30f ? dy : copysignf(1e-30f, dy));
     const float iz = 1.0f / (fabsf(dz) > 1e-30f ? dz : copysignf(1e-30f, dz));
     const float oix = ox * ix, oiy = oy * iy, oiz = oz * iz;
-    float t_best = INFINITY;
+    float t_best = t_max;
     int best = -1;
     bool ent = false;
     int stack[kStack];

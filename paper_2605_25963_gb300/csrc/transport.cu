@@ -45,7 +45,9 @@ namespace gadep {
 gadep_status build_bvh_host(const detmesh_mesh *m, const gadep_bvh_opts &o, gadep_bvh *out);
 
 namespace dev {
-template <bool GRAD, bool COUNT>
+// EM: charged-particle tracks (e_model 1), a separate instantiation so that the
+// photon-only kernels keep their registers.
+template <bool GRAD, bool COUNT, bool EM>
 // 4 blocks of 256 threads per SM (64 registers): measured faster than 2 or 3
 // blocks despite the register spills, as the traversal is latency bound.
 __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsigned long long *counters)
@@ -198,10 +200,14 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsig
                     const float tt = t_cur + d_int;
                     const float px = fmaf(tt, dx, ox), py = fmaf(tt, dy, oy), pz = fmaf(tt, dz, oz);
                     const float u = rng.u01(k0, k1) * mu_unit;
-                    float dep;
+                    float dep = 0.0f;
                     bool alive = true;
+                    // charged particles of e_model 1: kinetic energy, direction, count
+                    float eT = 0.0f, eux = dx, euy = dy, euz = dz, ew = 1.0f;
                     if (u < pe) {
-                        dep = E; E = 0.0f; alive = false;
+                        if (EM) eT = E;
+                        else dep = E;
+                        E = 0.0f; alive = false;
                     } else if (u < pe + co || pa == 0.0f) {
                         const float k = E * (1.0f / kMeC2);
                         const float a2k = 1.0f + 2.0f * k;
@@ -228,13 +234,21 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsig
                             float sp, cp;
                             sincospif(2.0f * rng.u01(k0, k1), &sp, &cp);
                             const float Ep = E / x;
-                            dep = E - Ep;
                             rotate(dx, dy, dz, c, sp, cp);
+                            if (EM) {
+                                eT = E - Ep;
+                                const float qx = E * eux - Ep * dx, qy = E * euy - Ep * dy, qz = E * euz - Ep * dz;
+                                const float ql = sqrtf(qx * qx + qy * qy + qz * qz);
+                                if (ql > 0.0f) { eux = qx / ql; euy = qy / ql; euz = qz / ql; }
+                            } else {
+                                dep = E - Ep;
+                            }
                             E = Ep;
                             if (E < P.e_cut) { dep += E; E = 0.0f; alive = false; }
                         }
                     } else {
-                        dep = E - kTwoMeC2;
+                        if (EM) { eT = 0.5f * (E - kTwoMeC2); ew = 2.0f; }
+                        else dep = E - kTwoMeC2;
                         float nx, ny, nz;
                         iso_dir(rng, k0, k1, nx, ny, nz);
                         E = kMeC2;
@@ -246,6 +260,9 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsig
                     }
                     if (R.y & 1) edep += dep;
                     dep_all += dep;
+                    if (eT > 0.0f && !herr)
+                        e_track<COUNT>(P, s_reg, P.inst[inst].scale, px, py, pz, eux, euy, euz, eT, ew, region, edep,
+                                       dep_all, esc, herr, ts);
                     if (herr) {
                         finished = true;
                     } else if (alive) {
@@ -505,6 +522,7 @@ struct gadep_plan {
     std::vector<gadep::dev::InstDev> inst;
     std::vector<unsigned long long> inst_end;
     float4 *d_xs = nullptr;
+    float *d_erange = nullptr;
     int4 *d_regions = nullptr;
     gadep::dev::InstDev *d_inst = nullptr;
     unsigned long long *d_end = nullptr;
@@ -532,22 +550,23 @@ gadep_status check_opts(const gadep_opts *o)
     if (!(o->e_cut_keV >= 0.0f) || !(o->fep_delta_keV >= 0.0f) || !(o->e_max_keV > 0.0f) ||
         o->n_bins < 1 || o->n_bins > (1 << 20) || o->step_cap < 1 || o->n_group < 0 ||
         o->n_group > 4 || o->block < 0 || o->block > 256 || (o->block % 32) != 0 || o->chunk < 0 ||
-        o->blocks_per_sm < 0 || o->blocks_per_sm > 32)
+        o->blocks_per_sm < 0 || o->blocks_per_sm > 32 || o->e_model < 0 || o->e_model > 1)
         return fail(GADEP_E_INVAL, "bad gadep_opts (n_bins in [1, 2^20], step_cap >= 1, n_group <= 4, "
-                                   "block a multiple of 32 <= 256)");
+                                   "block a multiple of 32 <= 256, e_model 0 or 1)");
     for (int g = 0; g < GADEP_MAX_GROUPS; ++g)
         if (!(o->group_scale[g] >= 0.0f) || !std::isfinite(o->group_scale[g]))
             return fail(GADEP_E_INVAL, "bad group scale");
     return GADEP_OK;
 }
 
-template <bool GRAD, bool COUNT>
-void *kernel_ptr() { return (void *)gadep::dev::transport_kernel<GRAD, COUNT>; }
+template <bool GRAD, bool COUNT, bool EM>
+void *kernel_ptr() { return (void *)gadep::dev::transport_kernel<GRAD, COUNT, EM>; }
 
-void *pick_kernel(bool grad, bool count)
+void *pick_kernel(bool grad, bool count, bool em)
 {
-    if (grad) return count ? kernel_ptr<true, true>() : kernel_ptr<true, false>();
-    return count ? kernel_ptr<false, true>() : kernel_ptr<false, false>();
+    if (grad) return count ? kernel_ptr<true, true, false>() : kernel_ptr<true, false, false>();
+    if (em) return count ? kernel_ptr<false, true, true>() : kernel_ptr<false, false, true>();
+    return count ? kernel_ptr<false, true, false>() : kernel_ptr<false, false, false>();
 }
 
 }  // namespace
@@ -649,6 +668,7 @@ extern "C" void gadep_plan_destroy(gadep_plan *p)
     {
         DeviceGuard g(p->device);
         cudaFree(p->d_xs);
+        cudaFree(p->d_erange);
         cudaFree(p->d_regions);
         cudaFree(p->d_inst);
         cudaFree(p->d_end);
@@ -750,11 +770,18 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
     if (!mat->mu || mat->n_mat < 1 || mat->n_mat > 1024 || mat->n_grid < 2 || mat->n_grid > 65536 ||
         !(mat->E_min > 0.0) || !(mat->E_max > mat->E_min))
         return fail(GADEP_E_INVAL, "plan: bad gadep_materials");
+    const bool electrons = opts->e_model == 1;
+    if (electrons && grad) return fail(GADEP_E_INVAL, "plan: e_model 1 is not available with gradients");
+    if (electrons && (!mat->e_range || mat->e_n < 2 || mat->e_n > 65536 || !(mat->T_min > 0.0) ||
+                      !(mat->T_max > mat->T_min) || !std::isfinite(mat->T_max)))
+        return fail(GADEP_E_INVAL, "plan: e_model 1 needs gadep_materials.e_range (e_n >= 2, 0 < T_min < T_max)");
     const MeshData &geo = b->geo;
-    // compact the materials the mesh uses; all-zero tables behave as vacuum (-1)
+    // compact the materials the mesh uses; all-zero tables behave as vacuum (-1),
+    // for charged particles too
     const size_t ng = (size_t)mat->n_grid;
     std::vector<int> slot(mat->n_mat, -2);
     std::vector<float4> xs;
+    std::vector<float> er;          // charged-particle ranges of the staged materials
     std::vector<int32_t> regions(b->regions);
     for (int32_t r = 0; r < (int32_t)regions.size() / 4; ++r) {
         const int code = regions[4 * r];
@@ -773,6 +800,15 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
                 for (size_t g = 0; g < ng; ++g) {
                     const float *m = mat->mu + (size_t)code * 3 * ng;
                     xs.push_back(make_float4(m[g], m[ng + g], m[2 * ng + g], 0.0f));
+                }
+                if (electrons) {
+                    const float *row = mat->e_range + (size_t)code * mat->e_n;
+                    for (int32_t g = 0; g < mat->e_n; ++g) {
+                        if (!(row[g] > 0.0f) || !std::isfinite(row[g]) || (g > 0 && !(row[g] > row[g - 1])))
+                            return fail(GADEP_E_INVAL, "plan: e_range of material %d is not finite, positive "
+                                                       "and increasing", code);
+                        er.push_back(row[g]);
+                    }
                 }
             }
         }
@@ -848,7 +884,7 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
         gadep_plan_destroy(p);
         return fail(GADEP_E_INVAL, "plan: tables need %zu bytes of shared memory, the device has %d", smem, dev_smem);
     }
-    void *kfn = pick_kernel(grad, count);
+    void *kfn = pick_kernel(grad, count, opts->e_model == 1);
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) { gadep_plan_destroy(p); return cuda_fail(e, "plan: cudaFuncSetAttribute"); }
     int bps = 0;
@@ -914,6 +950,7 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
     }
     // device buffers
     if ((st = dalloc(&p->d_xs, std::max<size_t>(xs.size(), 1), "plan tables")) != GADEP_OK ||
+        (!er.empty() && (st = dalloc(&p->d_erange, er.size(), "plan electron ranges")) != GADEP_OK) ||
         (st = dalloc((int32_t **)&p->d_regions, regions.size(), "plan regions")) != GADEP_OK ||
         (st = dalloc(&p->d_inst, (size_t)n_inst, "plan instances")) != GADEP_OK ||
         (st = dalloc(&p->d_end, (size_t)n_inst, "plan prefix")) != GADEP_OK ||
@@ -926,6 +963,7 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
         return st;
     }
     if ((!xs.empty() && (e = cudaMemcpy(p->d_xs, xs.data(), xs.size() * sizeof(float4), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (!er.empty() && (e = cudaMemcpy(p->d_erange, er.data(), er.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) ||
         (e = cudaMemcpy(p->d_regions, regions.data(), regions.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(p->d_inst, p->inst.data(), p->inst.size() * sizeof(dev::InstDev), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(p->d_end, p->inst_end.data(), p->inst_end.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess) {
@@ -964,6 +1002,12 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
     P.chunk = opts->chunk > 0 ? opts->chunk : 256;
     P.n_stripes = p->n_stripes;
     P.root_all = b->root_all;
+    P.erange = p->d_erange;
+    P.e_model = electrons ? 1 : 0;
+    P.e_n = electrons ? mat->e_n : 0;
+    P.e_T_min = electrons ? (float)mat->T_min : 0.0f;
+    P.e_lnT_min = electrons ? (float)std::log(mat->T_min) : 0.0f;
+    P.e_inv_dlnT = electrons ? (float)((mat->e_n - 1) / (std::log(mat->T_max) - std::log(mat->T_min))) : 0.0f;
     // scene bounds seen from the world (births outside it whose ray misses it end at once)
     scene_box(b, P.root_lo, P.root_hi);
     *out = p;
@@ -989,11 +1033,14 @@ gadep_status plan_launch(gadep_plan *p, uint32_t *spectra_dev, float *edep_trace
     if (p->wf) return wavefront_run(p->wf, P, p->grad, p->count, p->d_counters, &p->timer, s);
     p->timer.before(s);
     if (p->grad) {
-        if (p->count) dev::transport_kernel<true, true><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
-        else dev::transport_kernel<true, false><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
+        if (p->count) dev::transport_kernel<true, true, false><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
+        else dev::transport_kernel<true, false, false><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
+    } else if (P.e_model) {
+        if (p->count) dev::transport_kernel<false, true, true><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
+        else dev::transport_kernel<false, false, true><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
     } else {
-        if (p->count) dev::transport_kernel<false, true><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
-        else dev::transport_kernel<false, false><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
+        if (p->count) dev::transport_kernel<false, true, false><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
+        else dev::transport_kernel<false, false, false><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
     }
     p->timer.after(KK_MEGA, s);
     e = cudaGetLastError();
@@ -1341,6 +1388,7 @@ extern "C" gadep_status gadep_run_noalloc(const gadep_bvh *b, const gadep_materi
     if (b->device < 0 || !b->d_nodes) return fail(GADEP_E_INVAL, "gadep_run_noalloc: the BVH has no device copy");
     gadep_status st = check_opts(opts);
     if (st != GADEP_OK) return st;
+    if (opts->e_model != 0) return fail(GADEP_E_INVAL, "gadep_run_noalloc: e_model 1 needs gadep_run");
     if (n_hist >= (1ull << 32)) return fail(GADEP_E_INVAL, "gadep_run_noalloc: n_hist must be < 2^32");
     if (!(energy_keV > 0.0f) || !std::isfinite(energy_keV) || energy_keV > 1e5f)
         return fail(GADEP_E_INVAL, "gadep_run_noalloc: energy must be in (0, 1e5] keV");
@@ -1428,7 +1476,7 @@ extern "C" gadep_status gadep_run_noalloc(const gadep_bvh *b, const gadep_materi
     cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, b->device);
     if (smem > (size_t)dev_smem) return fail(GADEP_E_INVAL, "gadep_run_noalloc: tables need too much shared memory");
-    void *kfn = (void *)dev::transport_kernel<false, false>;
+    void *kfn = (void *)dev::transport_kernel<false, false, false>;
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn, block, smem);
     if (e == cudaSuccess && bps < 1) return fail(GADEP_E_CUDA, "gadep_run_noalloc: kernel does not fit on the device");
@@ -1481,7 +1529,7 @@ extern "C" gadep_status gadep_run_noalloc(const gadep_bvh *b, const gadep_materi
     P.root_all = b->root_all;
     gadep::scene_box(b, P.root_lo, P.root_hi);
     if (n_hist > 0)
-        dev::transport_kernel<false, false><<<n_sm * bps, block, smem, s>>>(P, S->counters);
+        dev::transport_kernel<false, false, false><<<n_sm * bps, block, smem, s>>>(P, S->counters);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "gadep_run_noalloc: launch");
     // tallies back to the host, finalise

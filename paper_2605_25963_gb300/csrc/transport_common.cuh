@@ -55,6 +55,11 @@ struct Params {
     float root_lo[3], root_hi[3];       // bounds of every triangle (padded)
     int root_all;                       // tree over every triangle
     int face_bins, n_keys;              // wavefront queue sort: direction cells, key count
+    // charged particles (e_model 1): CSDA range of each staged material on e_n
+    // log-spaced kinetic energies from e_T_min, mm at unit density
+    const float *erange;                // [n_mat][e_n]
+    int e_model, e_n;
+    float e_T_min, e_lnT_min, e_inv_dlnT;
 };
 
 // Slab test of the ray (t >= 0) against an axis-aligned box.
@@ -207,6 +212,101 @@ __device__ __forceinline__ void mu_at(const float4 *tab, int n_grid, float lnE_m
     pe = fmaf(f, b.x - a.x, a.x);
     co = fmaf(f, b.y - a.y, a.y);
     pa = E > kTwoMeC2 ? fmaf(f, b.z - a.z, a.z) : 0.0f;
+}
+
+// CSDA range (mm, unit density) of staged material m at kinetic energy T >= e_T_min:
+// linear in ln T between grid points (the last interval extended above the grid).
+__device__ __forceinline__ float erange_at(const Params &P, int m, float T)
+{
+    const float *row = P.erange + (size_t)m * P.e_n;
+    const float g = (logf(T) - P.e_lnT_min) * P.e_inv_dlnT;
+    const int k = min(max((int)floorf(g), 0), P.e_n - 2);
+    const float a = __ldg(row + k), b = __ldg(row + k + 1);
+    return fmaf(g - (float)k, b - a, a);
+}
+
+// Kinetic energy whose range is `left` mm (the inverse of erange_at): bisection
+// over the grid for the interval, then linear in ln T; below the first grid point
+// the range is taken proportional to T.
+__device__ __forceinline__ float e_energy_for_range(const Params &P, int m, float left)
+{
+    if (!(left > 0.0f)) return 0.0f;
+    const float *row = P.erange + (size_t)m * P.e_n;
+    const float r0 = __ldg(row);
+    if (left <= r0) return P.e_T_min * (left / r0);
+    int lo = 0, hi = P.e_n - 1;            // row[lo] < left; row[hi] >= left unless above the grid
+    if (left >= __ldg(row + hi)) {
+        lo = P.e_n - 2;
+    } else {
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(row + mid) < left) lo = mid;
+            else hi = mid;
+        }
+    }
+    const float a = __ldg(row + lo), b = __ldg(row + lo + 1);
+    return expf(P.e_lnT_min + ((float)lo + (left - a) / (b - a)) / P.e_inv_dlnT);
+}
+
+constexpr int kMaxTrackCrossings = 256;
+
+// One line of `w` identical charged particles (kinetic energy T each) from p along
+// unit u, born in `region` (the photon's): continuous slowing down straight ahead,
+// region by region through the mesh.  In a region of material m and density
+// scale s the particles reach R_m(T) / s; when the next boundary is nearer they
+// cross it with the T' of range R_m(T) - s L and deposit T - T' in the region.
+// Below e_T_min the rest is deposited where they are; vacuum takes nothing; what
+// leaves the mesh escapes.  Active deposits go to edep, all to dep_all.
+template <bool COUNT>
+__device__ __noinline__ void e_track(const Params &P, const int4 *s_reg, const float *scale, float px, float py, float pz,
+                        float ux, float uy, float uz, float T, float w, int region, float &edep, float &dep_all,
+                        float &esc, uint32_t &herr, TravStats &ts)
+{
+    float t_cur = 0.0f;
+    int last = -1;
+    for (int k = 0; k <= kMaxTrackCrossings; ++k) {
+        int4 R = s_reg[region];
+        if (T < P.e_T_min) {
+            dep_all += w * T;
+            if (R.y & 1) edep += w * T;
+            return;
+        }
+        const int group = (R.y >> 1) - 1;
+        const float sc = group >= 0 ? scale[group] : 1.0f;
+        const float rn = R.x >= 0 ? erange_at(P, R.x, T) : INFINITY;
+        const float reach = rn / sc;
+        float t_hit = INFINITY;
+        bool entering = false;
+        int hit = traverse<COUNT>(P.nodes, P.tris, P.planes, R.w, px, py, pz, ux, uy, uz, t_cur, last, t_hit,
+                                  entering, herr, ts, t_cur + reach);
+        if (herr & ERR_STACK) return;
+        if (hit < 0 && reach < INFINITY) {         // stops in this region
+            dep_all += w * T;
+            if (R.y & 1) edep += w * T;
+            return;
+        }
+        if (hit < 0 && region != 0) {
+            // vacuum inside a solid with no surface ahead: the start sits a rounding
+            // error past a boundary; relocate by the nearest surface of the mesh
+            hit = traverse<COUNT>(P.nodes, P.tris, P.planes, P.root_all, px, py, pz, ux, uy, uz, t_cur, last,
+                                  t_hit, entering, herr, ts);
+            if (herr & ERR_STACK) return;
+        }
+        if (hit < 0) {                             // leaves the mesh
+            esc += w * T;
+            return;
+        }
+        float T2 = T;
+        if (R.x >= 0) T2 = fminf(T, e_energy_for_range(P, R.x, rn - (t_hit - t_cur) * sc));
+        dep_all += w * (T - T2);
+        if (R.y & 1) edep += w * (T - T2);
+        T = T2;
+        t_cur = t_hit;
+        last = __float_as_int(__ldg(&P.tris[3 * hit + 1].w));
+        const int treg = __float_as_int(__ldg(&P.tris[3 * hit].w));
+        region = entering ? treg : s_reg[treg].z;
+    }
+    herr |= ERR_STEPCAP;
 }
 
 }  // namespace dev

@@ -764,7 +764,7 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const Params P, State S, 
 }
 
 // ---------------------------------------------------------------- physics
-template <bool GRAD, bool COUNT>
+template <bool GRAD, bool COUNT, bool EM>
 __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S, int cur,
                                                       unsigned long long *counters)
 {
@@ -864,9 +864,13 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
                     const float px = fmaf(tt, ry.d.x, ry.o.x), py = fmaf(tt, ry.d.y, ry.o.y),
                                 pz = fmaf(tt, ry.d.z, ry.o.z);
                     const float u = r.u01(k0, k1) * mu_unit;
-                    float dep;
+                    float dep = 0.0f;
+                    // charged particles of e_model 1: kinetic energy, direction, count
+                    float eT = 0.0f, eux = ry.d.x, euy = ry.d.y, euz = ry.d.z, ew = 1.0f;
                     if (u < pe) {
-                        dep = E; E = 0.0f; photon_done = true;
+                        if (EM) eT = E;
+                        else dep = E;
+                        E = 0.0f; photon_done = true;
                     } else if (u < pe + co || pa == 0.0f) {
                         const float k = E * (1.0f / kMeC2);
                         const float a2k = 1.0f + 2.0f * k;
@@ -893,13 +897,22 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
                             float sp, cp;
                             sincospif(2.0f * r.u01(k0, k1), &sp, &cp);
                             const float Ep = E / x;
-                            dep = E - Ep;
                             rotate(ry.d.x, ry.d.y, ry.d.z, c, sp, cp);
+                            if (EM) {
+                                eT = E - Ep;
+                                const float qx = E * eux - Ep * ry.d.x, qy = E * euy - Ep * ry.d.y,
+                                            qz = E * euz - Ep * ry.d.z;
+                                const float ql = sqrtf(qx * qx + qy * qy + qz * qz);
+                                if (ql > 0.0f) { eux = qx / ql; euy = qy / ql; euz = qz / ql; }
+                            } else {
+                                dep = E - Ep;
+                            }
                             E = Ep;
                             if (E < P.e_cut) { dep += E; E = 0.0f; photon_done = true; }
                         }
                     } else {
-                        dep = E - kTwoMeC2;
+                        if (EM) { eT = 0.5f * (E - kTwoMeC2); ew = 2.0f; }
+                        else dep = E - kTwoMeC2;
                         const float c = 2.0f * r.u01(k0, k1) - 1.0f;
                         float sp, cp;
                         sincospif(2.0f * r.u01(k0, k1), &sp, &cp);
@@ -915,6 +928,12 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
                     }
                     if (R.y & 1) edep += dep;
                     dep_all += dep;
+                    if (eT > 0.0f && !herr) {
+                        float e_esc = 0.0f;
+                        e_track<COUNT>(P, s_reg, I.scale, px, py, pz, eux, euy, euz, eT, ew, region, edep, dep_all,
+                                       e_esc, herr, ts);
+                        esc_now += e_esc;
+                    }
                     ry.o = make_float4(px, py, pz, 0.0f);
                     last_tri = -1;
                     if (herr) finished = true;
@@ -935,10 +954,12 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
                     region = entering ? hit_region : s_reg[hit_region].z;
                 }
                 if (esc_now != 0.0f) {
-                    // escaped energy of this history so far (at most two photons escape)
+                    // escaped energy of this history so far, kept in the slot while the
+                    // history goes on (a pending annihilation photon, or the photon
+                    // itself after a charged particle escaped)
                     if (flags & kFlagEsc) esc_now += S.esc[slot];
                     flags |= kFlagEsc;
-                    if (!finished && (flags & kFlagSec)) S.esc[slot] = esc_now;
+                    if (!finished && ((flags & kFlagSec) || !photon_done)) S.esc[slot] = esc_now;
                 }
                 if (photon_done && !finished) {
                     if (flags & kFlagSec) {
@@ -1153,10 +1174,12 @@ gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P0, bool grad
         };
         set((const void *)wf::gen_kernel, gsm);
         set((const void *)wf::sort_kernel, ssm);
-        set((const void *)wf::physics_kernel<true, true>, rsm);
-        set((const void *)wf::physics_kernel<true, false>, rsm);
-        set((const void *)wf::physics_kernel<false, true>, rsm);
-        set((const void *)wf::physics_kernel<false, false>, rsm);
+        set((const void *)wf::physics_kernel<true, true, false>, rsm);
+        set((const void *)wf::physics_kernel<true, false, false>, rsm);
+        set((const void *)wf::physics_kernel<false, true, false>, rsm);
+        set((const void *)wf::physics_kernel<false, false, false>, rsm);
+        set((const void *)wf::physics_kernel<false, true, true>, rsm);
+        set((const void *)wf::physics_kernel<false, false, true>, rsm);
         if (e != cudaSuccess) return fail(GADEP_E_CUDA, "wavefront: shared memory: %s", cudaGetErrorString(e));
     }
     const unsigned long long max_iter = (unsigned long long)P.step_cap * 4 + P.total / 1024 + 1000000ull;
@@ -1188,8 +1211,15 @@ gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P0, bool grad
             grid = dim3(w->trace_grid);
             args[0] = &P; args[1] = &S; args[2] = &c; args[3] = &counters; break;
         case KK_PHYSICS:
-            fn = grad ? (count ? (const void *)wf::physics_kernel<true, true> : (const void *)wf::physics_kernel<true, false>)
-                      : (count ? (const void *)wf::physics_kernel<false, true> : (const void *)wf::physics_kernel<false, false>);
+            if (grad)
+                fn = count ? (const void *)wf::physics_kernel<true, true, false>
+                           : (const void *)wf::physics_kernel<true, false, false>;
+            else if (P.e_model)
+                fn = count ? (const void *)wf::physics_kernel<false, true, true>
+                           : (const void *)wf::physics_kernel<false, false, true>;
+            else
+                fn = count ? (const void *)wf::physics_kernel<false, true, false>
+                           : (const void *)wf::physics_kernel<false, false, false>;
             grid = dim3(w->work_grid); smem = rsm; args[0] = &P; args[1] = &S; args[2] = &c; args[3] = &counters; break;
         default: return cudaErrorInvalidValue;
         }

@@ -199,6 +199,10 @@ def box_mesh(boxes):
 TABLE_N_GRID = 1000
 TABLE_E_MIN = 10.0
 TABLE_E_MAX = 3000.0
+# charged-particle (e_model 1) range tables: kinetic energies from 1 keV (below it a
+# particle deposits where it is) to TABLE_E_MAX
+ERANGE_T_MIN = 1.0
+ERANGE_N = 2048
 N_BINS = 4096
 E_MAX = 3000.0
 E_CUT = 10.0

@@ -77,6 +77,27 @@ def test_detmesh_locate_matches_oracle(orc):
         assert m.locate(p) == o.locate(p, (0.2672612, 0.5345225, 0.8017837)), p
 
 
+def test_electron_ranges_match_oracle(orc):
+    """The library's CSDA range tables (Gauss-Legendre, FP32) against the oracle's
+    independent ones (Simpson, FP64, pinned to ESTAR in test_oracle_electron)."""
+    r = api.gadep_erange_build()
+    t = orc.Tables.build(W.MATERIAL_CODES)
+    T = np.exp(np.linspace(np.log(W.ERANGE_T_MIN), np.log(W.TABLE_E_MAX), W.ERANGE_N))
+    assert r.shape == (5, W.ERANGE_N)
+    assert np.all(np.isinf(r[0]))                         # vacuum slows nothing
+    for m in range(1, 5):
+        o = np.array([t.e_range(m, x) for x in T[::7]])
+        assert np.allclose(r[m, ::7], o, rtol=1e-5, atol=0), m
+        assert np.all(np.diff(r[m]) > 0)
+    c = np.array([1], dtype=np.int32)
+    out = np.zeros(4, dtype=np.float32)
+    lib = capi.load()
+    assert lib.gadep_erange_build(api._ptr(c, C.c_int32), 1, 1, 1.0, 10.0, api._ptr(out, C.c_float)) != 0
+    assert lib.gadep_erange_build(api._ptr(c, C.c_int32), 1, 4, 10.0, 1.0, api._ptr(out, C.c_float)) != 0
+    c[0] = 77
+    assert lib.gadep_erange_build(api._ptr(c, C.c_int32), 1, 4, 1.0, 10.0, api._ptr(out, C.c_float)) != 0
+
+
 def test_tables_match_oracle(orc):
     mu = api.gadep_xs_build()
     ref = orc.Tables.build(W.MATERIAL_CODES).array()

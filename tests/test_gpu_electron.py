@@ -1,0 +1,114 @@
+"""Charged-particle tracks (e_model 1) on the GPU against the FP64 oracle.
+
+The tracks draw no random numbers, so both sides follow the same photon
+histories; a history whose charged particles all stop in the region they
+start in deposits exactly as with local deposition.  Tracks that cross a
+boundary deposit T - T' with T' from the FP32 range table on the GPU and from
+the FP64 table and bisection in the oracle (relative difference ~1e-5 of T),
+so the per-history comparison allows 0.05 keV + 1e-4 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2605_25963_gb300 import api, capi
+from paper_2605_25963_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from test_gpu_transport import chi2_two_sample, osrc, scene  # noqa: E402
+
+MEGA, WAVEFRONT = 1, 2
+
+
+@pytest.fixture(scope="module")
+def mats():
+    return api.Materials.default()
+
+
+@pytest.fixture(scope="module")
+def otab(orc):
+    return orc.Tables.build(W.MATERIAL_CODES)
+
+
+def run_both(orc, otab, mats, name, src, E, n, variant=MEGA, scales=()):
+    m, b, om = scene(orc, name)
+    trace = torch.empty(n, dtype=torch.float32, device="cuda")
+    opts = api.make_opts(e_model=1, variant=variant, group_scale=list(scales) or None)
+    r, spec = api.gadep_run(b, mats, src, E, n, opts=opts, edep_trace=trace)
+    ro = orc.transport(om, otab, osrc(orc, src), E, n, want_edep=True, e_model=1, group_scale=scales)
+    g = trace.cpu().numpy().astype(np.float64)
+    same = np.abs(g - ro.edep) <= 0.05 + 1e-4 * np.abs(ro.edep)
+    return r, spec, ro, same
+
+
+@pytest.mark.parametrize("E", [122.0, 662.0, 1332.0])
+def test_coax_tracks_parity(orc, otab, mats, E):
+    n = 200_000
+    r, spec, ro, same = run_both(orc, otab, mats, "COAX_P", W.COAX_POINT_25, E, n)
+    assert r["n_err"] == 0 and ro.tally["n_err"] == 0
+    assert same.mean() >= 0.999, same.mean()
+    assert abs(r["fepe"] - ro.fepe) <= 3 * math.hypot(r["sigma"], ro.sigma)
+    assert chi2_two_sample(spec, ro.spectrum) > 0.01
+    assert r["sum_dep_all"] + r["sum_esc"] == pytest.approx(n * E, rel=1e-5)
+    assert r["n_segments"] == pytest.approx(ro.tally["n_segments"], rel=2e-3)
+
+
+def test_tracks_change_only_where_energy_lands(orc, otab, mats):
+    """Same photon histories with and without tracks (the segment, interaction
+    and history counts agree exactly); the full-energy peak loses the histories
+    whose electrons leave the active volume.  The total active deposit may move
+    either way: electrons set going in the dead layer carry energy inward."""
+    m, b, _ = scene(orc, "COAX_P")
+    n = 1_000_003
+    r0, _ = api.gadep_run(b, mats, W.COAX_POINT_25, 1332.0, n, opts=api.make_opts(variant=MEGA))
+    r1, _ = api.gadep_run(b, mats, W.COAX_POINT_25, 1332.0, n, opts=api.make_opts(variant=MEGA, e_model=1))
+    for k in ("n_hist", "n_segments", "n_interactions", "n_culled"):
+        assert r0[k] == r1[k], k
+    assert r1["n_fep"] < r0["n_fep"]
+    assert r1["sum_dep_active"] != r0["sum_dep_active"]
+    for r in (r0, r1):
+        assert r["sum_dep_all"] + r["sum_esc"] == pytest.approx(n * 1332.0, rel=1e-5)
+
+
+def test_wavefront_equals_megakernel_with_tracks(mats, orc):
+    m, b, _ = scene(orc, "COAX_P")
+    n = 300_001
+    tm = torch.empty(n, dtype=torch.float32, device="cuda")
+    tw = torch.empty(n, dtype=torch.float32, device="cuda")
+    rm, sm = api.gadep_run(b, mats, W.COAX_POINT_25, 1332.0, n, edep_trace=tm, opts=api.make_opts(variant=MEGA, e_model=1))
+    rw, sw = api.gadep_run(b, mats, W.COAX_POINT_25, 1332.0, n, edep_trace=tw,
+                           opts=api.make_opts(variant=WAVEFRONT, wf_slots=32768, e_model=1))
+    assert rw["n_err"] == 0 and rw["n_hist"] == n
+    assert np.mean(tm.cpu().numpy() == tw.cpu().numpy()) >= 0.9999
+    for k in ("n_fep", "n_zero", "n_over"):
+        assert abs(rm[k] - rw[k]) <= 2, k
+    assert rw["sum_dep_all"] + rw["sum_esc"] == pytest.approx(n * 1332.0, rel=1e-5)
+
+
+def test_density_scale_and_volume_source_with_tracks(orc, otab, mats):
+    # the water prism source on the coax: tracks start in water and in the
+    # scaled dead layer (group 0) as well
+    r, spec, ro, same = run_both(orc, otab, mats, "GRAD_DET", W.GRAD_SOURCE, 662.0, 100_000,
+                                 scales=(1.6, 1.0, 1.0, 0.8))
+    assert r["n_err"] == 0 and same.mean() >= 0.999, same.mean()
+    assert abs(r["fepe"] - ro.fepe) <= 3 * math.hypot(r["sigma"], ro.sigma)
+
+
+def test_track_argument_errors(orc, mats):
+    m, b, _ = scene(orc, "COAX_P")
+    bare = api.Materials(mats.mu)                       # no range tables
+    with pytest.raises(capi.GadepError):
+        api.gadep_run(b, bare, W.COAX_POINT_25, 662.0, 1000, opts=api.make_opts(e_model=1))
+    with pytest.raises(capi.GadepError):
+        api.gadep_run(b, mats, W.COAX_POINT_25, 662.0, 1000, opts=api.make_opts(e_model=2))
+    inst = api.make_instances([(662.0, W.COAX_POINT_25, 1000, 0, [1, 1, 1, 1])])
+    with pytest.raises(capi.GadepError):
+        api.gadep_grad(b, mats, inst, api.make_opts(n_group=4, e_model=1))
+    spec = torch.zeros(4096, dtype=torch.int32, device="cuda")
+    with pytest.raises(capi.GadepError):
+        api.gadep_run_noalloc(b, mats, W.COAX_POINT_25, 662.0, 1000, spec, opts=api.make_opts(e_model=1))
