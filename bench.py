@@ -480,6 +480,9 @@ def main():
     fp32_meas, l2_meas = api.measure_peaks(dev)
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     segs = sum(f["segments"] for f in fepe)
+    # nearest-hit queries: every segment but the one of a history that ends at birth
+    # (born in the world aimed away from the scene box), which is counted without a query
+    queries = segs - sum(f["culled"] for f in fepe)
     # algorithmic node and triangle bytes of the traversal (64 B per node visit, 48 B per
     # triangle test), served by L1 and L2, per second of the dominant kernel
     l1l2_gbs = (NODE_BYTES * nodes + TRI_BYTES * tris) * args.steps / (dom_ms / 1e3) / 1e9
@@ -543,9 +546,9 @@ def main():
                                              "frac_of_measured_l2": l1l2_gbs / l2_meas if l2_meas else None,
                                              "note": "library microbenchmarks: independent FMA chains on every "
                                                      "SM; 64 MB re-read from L2"},
-                         "per_query": {"nodes": nodes / max(segs, 1), "tris": tris / max(segs, 1),
-                                       "relocated": relocated / max(segs, 1)},
-                         "queries_per_step": segs},
+                         "per_query": {"nodes": nodes / max(queries, 1), "tris": tris / max(queries, 1),
+                                       "relocated": relocated / max(queries, 1)},
+                         "queries_per_step": queries, "segments_per_step": segs},
             "cpu_baseline": cb,
             "e2e": e2e,
             "gpu_launches": sum(nl for nl, _ in kstats.values()),
