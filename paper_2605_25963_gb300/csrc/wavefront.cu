@@ -187,6 +187,49 @@ struct BlockTally {
         if (dep_all != 0.0f) atomicAdd(&s.dep_all, dep_all);
         if (esc != 0.0f) atomicAdd(&s.esc, esc);
     }
+    // The finished histories of a warp (every lane calls; fin: this lane finished
+    // one): the lanes of one instance are summed in registers and one lane adds
+    // the sums, instead of every lane adding its own.
+    __device__ void history_warp(bool fin, int inst, uint32_t segs, uint32_t herr, bool fep, float edep,
+                                 float dep_all, float esc, float e_max)
+    {
+        const uint32_t FULL = 0xffffffffu;
+        const int lane = threadIdx.x & 31;
+        uint32_t todo = __ballot_sync(FULL, fin);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            const int gi = __shfl_sync(FULL, inst, src);
+            const bool mine = fin && inst == gi;
+            const uint32_t grp = __ballot_sync(FULL, mine);
+            todo &= ~grp;
+            const bool ok = mine && !herr;
+            const uint32_t n_err = __popc(__ballot_sync(FULL, mine && herr));
+            const uint32_t n_fep = __popc(__ballot_sync(FULL, ok && fep));
+            const uint32_t n_zero = __popc(__ballot_sync(FULL, ok && edep == 0.0f));
+            const uint32_t n_over = __popc(__ballot_sync(FULL, ok && edep != 0.0f && edep >= e_max));
+            const uint32_t seg = __reduce_add_sync(FULL, mine ? segs : 0u);
+            const uint32_t eb = __reduce_or_sync(FULL, mine ? herr : 0u);
+            float d = ok ? edep : 0.0f, da = ok ? dep_all : 0.0f, e = ok ? esc : 0.0f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                d += __shfl_xor_sync(FULL, d, o);
+                da += __shfl_xor_sync(FULL, da, o);
+                e += __shfl_xor_sync(FULL, e, o);
+            }
+            if (lane == src) {
+                STally &s = t[gi];
+                atomicAdd(&s.hist, (unsigned int)__popc(grp));
+                atomicAdd(&s.seg, seg);
+                if (n_err) { atomicAdd(&s.err, n_err); atomicOr(&s.errbits, eb); }
+                if (n_fep) atomicAdd(&s.fep, n_fep);
+                if (n_zero) atomicAdd(&s.zero, n_zero);
+                if (n_over) atomicAdd(&s.over, n_over);
+                if (d != 0.0f) atomicAdd(&s.dep, d);
+                if (da != 0.0f) atomicAdd(&s.dep_all, da);
+                if (e != 0.0f) atomicAdd(&s.esc, e);
+            }
+        }
+    }
     // n histories of instance inst that ended at birth: one segment each, nothing
     // deposited, the source energy escaped
     __device__ void culled(int inst, uint32_t n, float E0)
@@ -799,6 +842,9 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
         int inst = 0;
         float edep_out = 0.0f;
         uint32_t herr_out = 0;
+        bool fep_out = false;
+        float dep_all_out = 0.0f, esc_out = 0.0f;
+        uint32_t segs_out = 0;
         if (mine) {
             const Hit ht = S.hit[j];
             const Slot sl = S.slot[slot];
@@ -994,11 +1040,16 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
                 float esc = 0.0f;
                 if (flags & kFlagEsc) esc = esc_now != 0.0f ? esc_now : S.esc[slot];
                 const bool fep = !herr && (I.E0 - edep) <= P.fep_delta;
-                bt.history(inst, steps, herr, fep, edep, dep_all, esc, P.e_max, score);
+                if (GRAD) {
+                    bt.history(inst, steps, herr, fep, edep, dep_all, esc, P.e_max, score);
+                } else {
+                    fep_out = fep; dep_all_out = dep_all; esc_out = esc; segs_out = steps;
+                }
                 const unsigned long long g = (inst ? P.inst_end[inst - 1] : 0ull) + local;
                 if (g < P.n_trace) P.edep_trace[g] = herr ? -1.0f : edep;
             }
         }
+        if (!GRAD) bt.history_warp(finished, inst, segs_out, herr_out, fep_out, edep_out, dep_all_out, esc_out, P.e_max);
         // ---- spectrum atomics (warp-aggregated per bin) ----
         const bool binned = finished && herr_out == 0u && edep_out > 0.0f && edep_out < P.e_max;
         int bin = 0;
