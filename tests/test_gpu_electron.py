@@ -112,3 +112,25 @@ def test_track_argument_errors(orc, mats):
     spec = torch.zeros(4096, dtype=torch.int32, device="cuda")
     with pytest.raises(capi.GadepError):
         api.gadep_run_noalloc(b, mats, W.COAX_POINT_25, 662.0, 1000, spec, opts=api.make_opts(e_model=1))
+
+
+def test_full_size_coax_tracks_against_oracle(orc, otab, mats):
+    """Tracks at the bench's size and launch configuration (1e8 histories, AUTO
+    form, the wavefront kernels here): against the oracle's e_model 1 at 1e7
+    histories of the same streams, FEPE within 3 combined sigma, and the first
+    1e5 histories one by one; a 1e7-history GPU run (the same histories as the
+    oracle's) has the oracle's full-energy-peak count within 0.3 %."""
+    m, b, om = scene(orc, "COAX_P")
+    n, n_orc, n_trace = 100_000_000, 10_000_000, 100_000
+    E = 1332.0
+    trace = torch.empty(n_trace, dtype=torch.float32, device="cuda")
+    r, spec = api.gadep_run(b, mats, W.COAX_POINT_25, E, n, edep_trace=trace, opts=api.make_opts(e_model=1))
+    ro = orc.transport(om, otab, osrc(orc, W.COAX_POINT_25), E, n_orc, want_edep=True, e_model=1)
+    assert r["n_err"] == 0 and ro.tally["n_err"] == 0
+    assert abs(r["fepe"] - ro.fepe) <= 3 * math.hypot(r["sigma"], ro.sigma)
+    r7, _ = api.gadep_run(b, mats, W.COAX_POINT_25, E, n_orc, opts=api.make_opts(e_model=1))
+    assert abs(r7["n_fep"] - ro.tally["n_fep"]) <= 0.003 * ro.tally["n_fep"], (r7["n_fep"], ro.tally["n_fep"])
+    g = trace.cpu().numpy().astype(np.float64)
+    o = ro.edep[:n_trace]
+    assert np.mean(np.abs(g - o) <= 0.05 + 1e-4 * np.abs(o)) >= 0.999
+    assert r["sum_dep_all"] + r["sum_esc"] == pytest.approx(n * E, rel=1e-5)
