@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(256) spawn_kernel(const Params P, State S, int
 }
 
 // ---------------------------------------------------------------- sort
-constexpr int kSortPerThread = 32;
+constexpr int kSortPerThread = 16;
 
 // Exclusive prefix of the key histogram of queue[cur]: the start of every bucket.
 __global__ void __launch_bounds__(1024) sort_prefix_kernel(State S, int cur, int n_keys)
