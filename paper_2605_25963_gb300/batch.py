@@ -77,9 +77,14 @@ def _time_plan(plan, repeats):
     return best
 
 
-def autotune(bvh, mats, items, grad=False, sample_histories=20_000_000, candidates=None, repeats=2):
-    """Time each launch form / shape on a scaled copy of the batch; return (best opts, table)."""
-    cands = candidates or default_candidates()
+def autotune(bvh, mats, items, grad=False, sample_histories=20_000_000, candidates=None, repeats=2,
+             opts_kw=None):
+    """Time each launch form / shape on a scaled copy of the batch; return (best opts, table).
+
+    opts_kw: the caller's own options (e_model, e_cut_keV, seed, ...), kept in every
+    candidate; the returned options include them."""
+    base = dict(opts_kw or {})
+    cands = [dict(base, **kw) for kw in (candidates or default_candidates())]
     sample = api.make_instances(_scaled(items, sample_histories))
     table = []
     for kw in cands:

@@ -47,3 +47,18 @@ def test_autotune_shapes_give_identical_results():
         res, spec = api.gadep_run_batch(b, mats, api.make_instances(items), api.make_opts(**cand))
         assert [r["n_fep"] for r in res] == [r["n_fep"] for r in base]
         assert np.array_equal(spec, base_spec)
+
+
+def test_autotune_keeps_caller_options():
+    """The caller's options (here charged-particle tracks) go into every candidate,
+    so the tuned batch computes what was asked for."""
+    m = api.detmesh_build(W.BATCH_DET)
+    b = api.gadep_bvh_build(m, 0)
+    mats = api.Materials.default()
+    items = _items(k=4)
+    kw, table = batch.autotune(b, mats, items, sample_histories=100_000, repeats=1, opts_kw=dict(e_model=1))
+    assert kw["e_model"] == 1 and all(c["e_model"] == 1 for c, _ in table)
+    ref, _ = api.gadep_run_batch(b, mats, api.make_instances(items), api.make_opts(e_model=1))
+    res, _ = api.gadep_run_batch(b, mats, api.make_instances(items), api.make_opts(**kw))
+    assert [r["n_fep"] for r in res] == [r["n_fep"] for r in ref]
+    assert [r["n_zero"] for r in res] == [r["n_zero"] for r in ref]
