@@ -258,9 +258,9 @@ constexpr int kMaxTrackCrossings = 256;
 // Below e_T_min the rest is deposited where they are; vacuum takes nothing; what
 // leaves the mesh escapes.  Active deposits go to edep, all to dep_all.
 template <bool COUNT>
-__device__ __noinline__ void e_track(const Params &P, const int4 *s_reg, const float *scale, float px, float py, float pz,
-                        float ux, float uy, float uz, float T, float w, int region, float &edep, float &dep_all,
-                        float &esc, uint32_t &herr, TravStats &ts)
+__device__ __noinline__ void e_track(const Params &P, const int4 *s_reg, const float *scale, float px, float py,
+                                     float pz, float ux, float uy, float uz, float T, float w, int region,
+                                     float &edep, float &dep_all, float &esc, uint32_t &herr, TravStats &ts)
 {
     float t_cur = 0.0f;
     int last = -1;
