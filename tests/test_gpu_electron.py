@@ -134,3 +134,29 @@ def test_full_size_coax_tracks_against_oracle(orc, otab, mats):
     o = ro.edep[:n_trace]
     assert np.mean(np.abs(g - o) <= 0.05 + 1e-4 * np.abs(o)) >= 0.999
     assert r["sum_dep_all"] + r["sum_esc"] == pytest.approx(n * E, rel=1e-5)
+
+
+def test_batched_tracks_equal_individual_runs(orc, mats):
+    """Tracks in one batched launch (instances with their own density scales) give
+    the tallies of the individual runs exactly."""
+    m, b, _ = scene(orc, "BATCH_DET")
+    items = []
+    for i, (E, s, n, sm) in enumerate(W.batch_instances()[10:40:5]):
+        items.append((E, W.BATCH_SOURCES[s], 20_000 + 991 * i, 5 * i + s, [1, 1, 1, sm]))
+    res, spec = api.gadep_run_batch(b, mats, api.make_instances(items), api.make_opts(e_model=1))
+    for i, (E, src, n, iid, sc) in enumerate(items):
+        r, sp = api.gadep_run(b, mats, src, E, n, instance=iid, opts=api.make_opts(e_model=1, group_scale=sc))
+        for k in ("n_hist", "n_fep", "n_zero", "n_over", "n_err", "n_segments", "n_interactions"):
+            assert r[k] == res[i][k], (i, k)
+        assert np.array_equal(sp, spec[i])
+
+
+@pytest.mark.parametrize("E", [W.STRESS_ENERGIES[3], W.STRESS_ENERGIES[7]])
+def test_stress_small_tracks_parity(orc, otab, mats, E):
+    """Tracks through the groove, the bolted flange and the volume source."""
+    r, spec, ro, same = run_both(orc, otab, mats, "STRESS_SMALL", W.STRESS_SOURCE, E, 100_000)
+    assert r["n_err"] == 0 and ro.tally["n_err"] == 0
+    assert same.mean() >= 0.999, same.mean()
+    assert abs(r["fepe"] - ro.fepe) <= 3 * math.hypot(r["sigma"], ro.sigma)
+    assert chi2_two_sample(spec, ro.spectrum) > 0.01
+    assert r["sum_dep_all"] + r["sum_esc"] == pytest.approx(100_000 * E, rel=1e-5)
