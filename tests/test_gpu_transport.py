@@ -311,3 +311,38 @@ def test_full_size_coax_against_oracle(orc, otab, mats):
         o = ro.edep[:n_trace]
         assert np.mean(np.abs(g - o) <= 1e-3 + 1e-6 * np.abs(o)) >= 0.999
         assert r["sum_dep_all"] + r["sum_esc"] == pytest.approx(n * E, rel=1e-6)
+
+
+@pytest.mark.parametrize("bvh_kw", [dict(split_alpha=1e-5, max_dup=2.0), dict(max_leaf=1), dict(max_leaf=7, c_trav=2.0)])
+def test_bvh_options_change_no_result(orc, mats, bvh_kw):
+    """The tree only accelerates the queries: spatial splits (triangle records
+    duplicated across leaves), one-triangle leaves or large leaves give the same
+    nearest hits and the same histories as the default tree."""
+    m, b_def, _ = scene(orc, "COAX_P")
+    b = api.gadep_bvh_build(m, 0, **bvh_kw)
+    b.validate()
+    rng = np.random.default_rng(5)
+    n = 20000
+    rays = np.zeros((n, 8), np.float32)
+    rays[:, 0:3] = np.column_stack([rng.uniform(-40, 40, n), rng.uniform(-40, 40, n), rng.uniform(-125, 30, n)])
+    d = rng.normal(size=(n, 3))
+    rays[:, 4:7] = d / np.linalg.norm(d, axis=1, keepdims=True)
+    rays[:, 7] = np.array([-1] * n, np.int32).view(np.float32)
+    rt = torch.from_numpy(rays).cuda()
+    t0, k0, e0 = (x.cpu().numpy() for x in api.gadep_nearest_hit(b_def, rt))
+    t1, k1, e1 = (x.cpu().numpy() for x in api.gadep_nearest_hit(b, rt))
+    # ties between triangles that share an edge may resolve to either one
+    assert np.mean((k0 == k1) & (e0 == e1)) >= 0.999
+    assert np.all(np.isinf(t0) == np.isinf(t1))
+    fin = np.isfinite(t0)
+    assert np.allclose(t0[fin], t1[fin], rtol=1e-6, atol=1e-6)
+    n_h = 300_001
+    tr0 = torch.empty(n_h, dtype=torch.float32, device="cuda")
+    tr1 = torch.empty(n_h, dtype=torch.float32, device="cuda")
+    for variant in (1, 2):
+        o = api.make_opts(variant=variant, wf_slots=65536)
+        r0, s0 = api.gadep_run(b_def, mats, W.COAX_POINT_25, 1332.0, n_h, edep_trace=tr0, opts=o)
+        r1, s1 = api.gadep_run(b, mats, W.COAX_POINT_25, 1332.0, n_h, edep_trace=tr1, opts=o)
+        assert r1["n_err"] == 0
+        assert np.mean(tr0.cpu().numpy() == tr1.cpu().numpy()) >= 0.9999
+        assert abs(r0["n_fep"] - r1["n_fep"]) <= 2
