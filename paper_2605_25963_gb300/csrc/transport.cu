@@ -919,8 +919,11 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
     if (variant == GADEP_VARIANT_WAVEFRONT) {
         int slots = opts->wf_slots;
         if (slots <= 0) {
+            // every photon that reaches the scene in flight at once where that fits:
+            // the sorted queue's buckets fill and the iterations are fewer (coax,
+            // 2.5e7 reaching per run: 2^25 slots 4.9 % faster than 2^24)
             slots = 1 << 20;
-            while (slots < (1 << 24) && (double)slots * 2.0 <= reaching) slots <<= 1;
+            while (slots < (1 << 25) && (double)slots < reaching) slots <<= 1;
         }
         gadep_bvh *bm = const_cast<gadep_bvh *>(b);
         {

@@ -1121,7 +1121,7 @@ static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 gadep_status wavefront_create(int device, int slots, bool grad, WavefrontBuffers **out)
 {
     *out = nullptr;
-    if (slots < 1024 || slots > (1 << 24)) return fail(GADEP_E_INVAL, "wavefront: slots must be in [1024, 2^24]");
+    if (slots < 1024 || slots > (1 << 26)) return fail(GADEP_E_INVAL, "wavefront: slots must be in [1024, 2^26]");
     WavefrontBuffers *w = new (std::nothrow) WavefrontBuffers();
     if (!w) return fail(GADEP_E_NOMEM, "wavefront: out of host memory");
     int n_sm = 0, bps = 0;
