@@ -73,6 +73,11 @@ struct gadep_bvh {
     gadep::WavefrontBuffers *wf_cache = nullptr;
     int wf_cache_slots = 0;
     bool wf_cache_busy = false;
+    // device scratch of the plan that holds wf_cache (tables, instances, tallies,
+    // spectra, counters): the same addresses run after run, so the kernel
+    // arguments repeat and the cached CUDA graph of the wavefront loop is reused
+    void *plan_scratch = nullptr;
+    size_t plan_scratch_bytes = 0;
     gadep_bvh_stats stats{};
     void *d_nodes = nullptr, *d_tris = nullptr, *d_tri_orig = nullptr, *d_regions = nullptr,
          *d_planes = nullptr;

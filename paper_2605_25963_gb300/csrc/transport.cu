@@ -500,6 +500,9 @@ void free_bvh_device(gadep_bvh *b)
     DeviceGuard g(b->device);
     wavefront_destroy(b->wf_cache);
     b->wf_cache = nullptr;
+    cudaFree(b->plan_scratch);
+    b->plan_scratch = nullptr;
+    b->plan_scratch_bytes = 0;
     cudaFree(b->d_nodes);
     cudaFree(b->d_tris);
     cudaFree(b->d_regions);
@@ -521,6 +524,8 @@ struct gadep_plan {
     int n_bins = 0;
     std::vector<gadep::dev::InstDev> inst;
     std::vector<unsigned long long> inst_end;
+    void *scratch = nullptr;                 // one device block holding the buffers below
+    bool scratch_cached = false;             // scratch borrowed from the BVH (with wf)
     float4 *d_xs = nullptr;
     float *d_erange = nullptr;
     int4 *d_regions = nullptr;
@@ -667,15 +672,7 @@ extern "C" void gadep_plan_destroy(gadep_plan *p)
     if (!p) return;
     {
         DeviceGuard g(p->device);
-        cudaFree(p->d_xs);
-        cudaFree(p->d_erange);
-        cudaFree(p->d_regions);
-        cudaFree(p->d_inst);
-        cudaFree(p->d_end);
-        cudaFree(p->d_tally);
-        cudaFree(p->d_spectra);
-        cudaFree(p->d_work);
-        cudaFree(p->d_counters);
+        if (!p->scratch_cached) cudaFree(p->scratch);
         p->timer.release();
         if (p->wf_cached) {
             gadep_bvh *bm = const_cast<gadep_bvh *>(p->bvh);
@@ -951,19 +948,60 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
         }
         p->grid = wavefront_trace_grid(p->wf);
     }
-    // device buffers
-    if ((st = dalloc(&p->d_xs, std::max<size_t>(xs.size(), 1), "plan tables")) != GADEP_OK ||
-        (!er.empty() && (st = dalloc(&p->d_erange, er.size(), "plan electron ranges")) != GADEP_OK) ||
-        (st = dalloc((int32_t **)&p->d_regions, regions.size(), "plan regions")) != GADEP_OK ||
-        (st = dalloc(&p->d_inst, (size_t)n_inst, "plan instances")) != GADEP_OK ||
-        (st = dalloc(&p->d_end, (size_t)n_inst, "plan prefix")) != GADEP_OK ||
-        (st = dalloc(&p->d_tally, (size_t)n_inst * (p->n_stripes = std::max(1, std::min(256, 65536 / n_inst))),
-                     "plan tallies")) != GADEP_OK ||
-        (st = dalloc(&p->d_spectra, (size_t)n_inst * p->n_bins, "plan spectra")) != GADEP_OK ||
-        (st = dalloc(&p->d_work, 1, "plan work counter")) != GADEP_OK ||
-        (st = dalloc(&p->d_counters, 4, "plan counters")) != GADEP_OK) {
+    // device buffers: one block (the BVH's, run after run, when the plan holds the
+    // BVH's wavefront buffers)
+    p->n_stripes = std::max(1, std::min(256, 65536 / n_inst));
+    size_t need = 0;
+    auto carve = [&need](size_t bytes) {
+        const size_t at = need;
+        need += (std::max<size_t>(bytes, 1) + 255) & ~(size_t)255;
+        return at;
+    };
+    const size_t o_xs = carve(xs.size() * sizeof(float4));
+    const size_t o_er = carve(er.size() * sizeof(float));
+    const size_t o_reg = carve(regions.size() * sizeof(int32_t));
+    const size_t o_inst = carve((size_t)n_inst * sizeof(dev::InstDev));
+    const size_t o_end = carve((size_t)n_inst * sizeof(unsigned long long));
+    const size_t o_tally = carve((size_t)n_inst * p->n_stripes * sizeof(dev::TallyDev));
+    const size_t o_spec = carve((size_t)n_inst * p->n_bins * sizeof(uint32_t));
+    const size_t o_work = carve(sizeof(unsigned long long));
+    const size_t o_cnt = carve(4 * sizeof(unsigned long long));
+    if (p->wf_cached) {
+        gadep_bvh *bm = const_cast<gadep_bvh *>(b);
+        std::lock_guard<std::mutex> lock(bm->wf_mutex);   // this plan holds the cache (busy)
+        if (bm->plan_scratch_bytes < need) {
+            cudaFree(bm->plan_scratch);
+            bm->plan_scratch = nullptr;
+            bm->plan_scratch_bytes = 0;
+            if ((e = cudaMalloc(&bm->plan_scratch, need)) != cudaSuccess) {
+                cudaGetLastError();
+                bm->plan_scratch = nullptr;
+            } else {
+                bm->plan_scratch_bytes = need;
+            }
+        }
+        if (bm->plan_scratch) {
+            p->scratch = bm->plan_scratch;
+            p->scratch_cached = true;
+        }
+    }
+    if (!p->scratch && (e = cudaMalloc(&p->scratch, need)) != cudaSuccess) {
+        cudaGetLastError();
+        p->scratch = nullptr;
         gadep_plan_destroy(p);
-        return st;
+        return fail(GADEP_E_NOMEM, "plan: cudaMalloc of %zu bytes failed", need);
+    }
+    {
+        char *base = (char *)p->scratch;
+        p->d_xs = (float4 *)(base + o_xs);
+        p->d_erange = er.empty() ? nullptr : (float *)(base + o_er);
+        p->d_regions = (int4 *)(base + o_reg);
+        p->d_inst = (dev::InstDev *)(base + o_inst);
+        p->d_end = (unsigned long long *)(base + o_end);
+        p->d_tally = (dev::TallyDev *)(base + o_tally);
+        p->d_spectra = (uint32_t *)(base + o_spec);
+        p->d_work = (unsigned long long *)(base + o_work);
+        p->d_counters = (unsigned long long *)(base + o_cnt);
     }
     if ((!xs.empty() && (e = cudaMemcpy(p->d_xs, xs.data(), xs.size() * sizeof(float4), cudaMemcpyHostToDevice)) != cudaSuccess) ||
         (!er.empty() && (e = cudaMemcpy(p->d_erange, er.data(), er.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) ||
