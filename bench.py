@@ -351,6 +351,8 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--variant", default="auto", choices=["auto", "mega", "wavefront"])
+    ap.add_argument("--e-model", type=int, default=0, choices=[0, 1],
+                    help="charged particles: 0 deposit at the interaction point, 1 CSDA tracks")
     ap.add_argument("--bvh", default="", help="BVH build options, e.g. split_alpha=0,max_leaf=3 "
                                              "(max_leaf, c_trav, c_tri, split_alpha, max_dup)")
     ap.add_argument("--wf-slots", type=int, default=0)
@@ -396,7 +398,8 @@ def main():
     from paper_2605_25963_gb300 import dist as shard
     offset = shard.history_offset(rank, n)   # disjoint history ids per rank
     opts = api.make_opts(history_offset=offset, block=args.block, chunk=args.chunk,
-                         variant={"auto": 0, "mega": 1, "wavefront": 2}[args.variant], wf_slots=args.wf_slots)
+                         variant={"auto": 0, "mega": 1, "wavefront": 2}[args.variant], wf_slots=args.wf_slots,
+                         e_model=args.e_model)
     plans = [api.Plan(bvh, mats, api.make_instances([(E, cfg["src"], n, i, [])]), opts)
              for i, E in enumerate(cfg["energies"])]
     stream = torch.cuda.current_stream()
@@ -552,6 +555,7 @@ def main():
                                  "gpu_launches from a second, instrumented pass over the same K steps "
                                  "(host-issued iterations, CUDA events around every kernel)",
                        "instrumented_ms_per_step": instrumented_ms / args.steps,
+                       "e_model": args.e_model,
                        "paper_rtx4090_s_all_energies": cfg.get("paper_s"),
                        "mesh_build_s": round(t_mesh, 4), "bvh_build_s": round(t_bvh, 4),
                        "bvh": bvh.stats()["opts"]},
