@@ -207,16 +207,6 @@ gadep_status gadep_bvh_build(const detmesh_mesh *m, int32_t device, gadep_bvh **
 gadep_status gadep_bvh_build_opts(const detmesh_mesh *m, const gadep_bvh_opts *opts, int32_t device,
                                   gadep_bvh **out);
 gadep_status gadep_bvh_get_stats(const gadep_bvh *b, gadep_bvh_stats *out);
-/* Lower bound on the distance (mm) from each of n host points [n][3] to the
- * nearest triangle of the mesh, from a grid of cells over the mesh's bounds
- * (about 1/128 of the largest extent): the FP64 distance from the cell's centre
- * to the nearest triangle less the cell's half-diagonal and a rounding margin,
- * capped at max(2 mm, 3 cells); 0 outside the grid.  Charged-particle tracks
- * (gadep_opts.e_model = 1) skip the traversal when their range from the birth
- * point is within this bound.  The grid is built on first use (host memory,
- * ~4 bytes per cell).  out: host float [n]. */
-gadep_status gadep_bvh_distance_bound(gadep_bvh *b, const float *points, int64_t n, float *out);
-
 /* Host-side invariant check of every tree: each of its triangles held by at
  * least one leaf and never twice by one leaf, child boxes inside parents, every
  * leaf box meeting the bounds of the triangles it holds, and the leaf boxes of

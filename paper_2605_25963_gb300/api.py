@@ -176,14 +176,6 @@ class Bvh:
     def validate(self):
         check(capi.load().gadep_bvh_validate(self._h))
 
-    def distance_bound(self, points):
-        """Lower bounds (mm) on the distance from host points [n, 3] to the nearest
-        triangle (the grid charged-particle tracks consult)."""
-        pts = np.ascontiguousarray(points, dtype=np.float32).reshape(-1, 3)
-        out = np.zeros(len(pts), dtype=np.float32)
-        check(capi.load().gadep_bvh_distance_bound(self._h, _ptr(pts, C.c_float), len(pts), _ptr(out, C.c_float)))
-        return out
-
 
 def bvh_opts(**kw) -> "capi.gadep_bvh_opts":
     """gadep_bvh_opts with the library defaults, then the given fields

@@ -20,7 +20,7 @@ MAX_GROUPS = 8
 EXPORTS = (
     "gadep_last_error", "gadep_abi_version", "detmesh_build", "detmesh_from_arrays", "detmesh_get",
     "detmesh_solid_stats", "detmesh_locate", "detmesh_destroy", "gadep_xs_build", "gadep_erange_build", "gadep_bvh_build",
-    "gadep_bvh_build_opts", "gadep_bvh_opts_default", "gadep_bvh_get_stats", "gadep_bvh_distance_bound", "gadep_bvh_validate", "gadep_bvh_destroy", "gadep_nearest_hit",
+    "gadep_bvh_build_opts", "gadep_bvh_opts_default", "gadep_bvh_get_stats", "gadep_bvh_validate", "gadep_bvh_destroy", "gadep_nearest_hit",
     "gadep_opts_default", "gadep_run", "gadep_run_batch", "gadep_grad", "gadep_plan_create",
     "gadep_plan_launch", "gadep_plan_results", "gadep_plan_shape", "gadep_plan_destroy",
     "gadep_count_work", "gadep_philox_words", "gadep_run_noalloc", "gadep_plan_set_timing",
@@ -142,7 +142,6 @@ def load(build_if_missing: bool = True):
         "gadep_bvh_opts_default": (None, [P(gadep_bvh_opts)]),
         "gadep_bvh_get_stats": (st, [vp, P(gadep_bvh_stats)]),
         "gadep_bvh_validate": (st, [vp]),
-        "gadep_bvh_distance_bound": (st, [vp, P(C.c_float), C.c_int64, P(C.c_float)]),
         "gadep_bvh_destroy": (None, [vp]),
         "gadep_nearest_hit": (st, [vp, vp, vp, C.c_int64, vp, vp, vp, vp]),
         "gadep_opts_default": (None, [P(gadep_opts)]),

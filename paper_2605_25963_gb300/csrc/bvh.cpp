@@ -17,7 +17,6 @@
 #include <cmath>
 #include <cstring>
 #include <new>
-#include <thread>
 
 #include "gadep_internal.h"
 
@@ -676,160 +675,5 @@ extern "C" gadep_status gadep_bvh_validate(const gadep_bvh *b)
             i = j;
         }
     }
-    return GADEP_OK;
-}
-
-// ---------------------------------------------------------------- distance bound
-//
-// A grid over the mesh's bounds holding, per cell, a lower bound on the distance
-// from any point of the cell to the nearest triangle: the FP64 distance from the
-// cell's centre to the nearest triangle within reach, minus the cell's
-// half-diagonal, capped at `cap` (a cell farther than cap + half-diagonal from
-// every triangle keeps cap), less a rounding margin.  A charged particle whose
-// range from its birth point is within this bound meets no surface, so its track
-// needs no traversal (the result is the one the traversal would give).
-
-namespace {
-
-// Squared distance from p to triangle (a, b, c): closest point by the triangle's
-// Voronoi regions (vertices, edges, face), all in FP64.
-double point_triangle_dist2(const double p[3], const double a[3], const double b[3], const double c[3])
-{
-    auto sub = [](const double *x, const double *y, double *r) { for (int k = 0; k < 3; ++k) r[k] = x[k] - y[k]; };
-    auto dot = [](const double *x, const double *y) { return x[0] * y[0] + x[1] * y[1] + x[2] * y[2]; };
-    double ab[3], ac[3], ap[3], bp[3], cp[3], q[3];
-    sub(b, a, ab); sub(c, a, ac); sub(p, a, ap);
-    const double d1 = dot(ab, ap), d2 = dot(ac, ap);
-    auto dist2_to = [&](const double *x) { double r[3]; sub(p, x, r); return dot(r, r); };
-    if (d1 <= 0.0 && d2 <= 0.0) return dist2_to(a);
-    sub(p, b, bp);
-    const double d3 = dot(ab, bp), d4 = dot(ac, bp);
-    if (d3 >= 0.0 && d4 <= d3) return dist2_to(b);
-    const double vc = d1 * d4 - d3 * d2;
-    if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) {
-        const double v = d1 / (d1 - d3);
-        for (int k = 0; k < 3; ++k) q[k] = a[k] + v * ab[k];
-        return dist2_to(q);
-    }
-    sub(p, c, cp);
-    const double d5 = dot(ab, cp), d6 = dot(ac, cp);
-    if (d6 >= 0.0 && d5 <= d6) return dist2_to(c);
-    const double vb = d5 * d2 - d1 * d6;
-    if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {
-        const double w = d2 / (d2 - d6);
-        for (int k = 0; k < 3; ++k) q[k] = a[k] + w * ac[k];
-        return dist2_to(q);
-    }
-    const double va = d3 * d6 - d5 * d4;
-    if (va <= 0.0 && (d4 - d3) >= 0.0 && (d5 - d6) >= 0.0) {
-        const double w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
-        for (int k = 0; k < 3; ++k) q[k] = b[k] + w * (c[k] - b[k]);
-        return dist2_to(q);
-    }
-    const double den = 1.0 / (va + vb + vc);
-    const double v = vb * den, w = vc * den;
-    for (int k = 0; k < 3; ++k) q[k] = a[k] + ab[k] * v + ac[k] * w;
-    return dist2_to(q);
-}
-
-}  // namespace
-
-namespace gadep {
-
-gadep_status build_distance_grid(gadep_bvh *b)
-{
-    if (!b->dgrid.empty()) return GADEP_OK;
-    const MeshData &g = b->geo;
-    const int32_t nt = g.n_tri();
-    if (nt == 0) return fail(GADEP_E_MESH, "distance grid: empty mesh");
-    // triangle vertices as stored (binary32), from the first tree's records
-    std::vector<double> v((size_t)nt * 9);
-    std::vector<char> seen((size_t)nt, 0);
-    for (size_t r = 0; r < b->tri_orig.size(); ++r) {
-        const int32_t t = b->tri_orig[r];
-        if (seen[(size_t)t]) continue;
-        seen[(size_t)t] = 1;
-        for (int j = 0; j < 3; ++j)
-            for (int c = 0; c < 3; ++c) v[(size_t)t * 9 + 3 * j + c] = b->tris[r * 12 + 4 * j + c];
-    }
-    double lo[3] = { INFINITY, INFINITY, INFINITY }, hi[3] = { -INFINITY, -INFINITY, -INFINITY };
-    for (size_t i = 0; i < v.size(); i += 3)
-        for (int c = 0; c < 3; ++c) { lo[c] = std::min(lo[c], v[i + c]); hi[c] = std::max(hi[c], v[i + c]); }
-    const double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
-    const double h = std::max(ext / 128.0, 1e-3);
-    const double cap = std::max(2.0, 3.0 * h);
-    const double half_diag = 0.5 * std::sqrt(3.0) * h;
-    int n[3];
-    for (int c = 0; c < 3; ++c) {
-        lo[c] -= h;
-        n[c] = (int)std::ceil((hi[c] + h - lo[c]) / h);
-    }
-    const size_t cells = (size_t)n[0] * n[1] * n[2];
-    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    std::vector<std::vector<double>> part(hw, std::vector<double>(cells, cap));
-    auto work = [&](unsigned id) {
-        std::vector<double> &d = part[id];
-        const double reach = cap + half_diag;
-        for (int32_t t = (int32_t)id; t < nt; t += (int32_t)hw) {
-            const double *a = &v[(size_t)t * 9], *bb = a + 3, *cc = a + 6;
-            int i0[3], i1[3];
-            for (int c = 0; c < 3; ++c) {
-                const double tl = std::min(a[c], std::min(bb[c], cc[c])) - reach;
-                const double th = std::max(a[c], std::max(bb[c], cc[c])) + reach;
-                i0[c] = std::max(0, (int)std::floor((tl - lo[c]) / h - 0.5));
-                i1[c] = std::min(n[c] - 1, (int)std::ceil((th - lo[c]) / h - 0.5));
-            }
-            for (int z = i0[2]; z <= i1[2]; ++z)
-                for (int y = i0[1]; y <= i1[1]; ++y)
-                    for (int x = i0[0]; x <= i1[0]; ++x) {
-                        const double p[3] = { lo[0] + (x + 0.5) * h, lo[1] + (y + 0.5) * h, lo[2] + (z + 0.5) * h };
-                        const double dd = std::sqrt(point_triangle_dist2(p, a, bb, cc)) - half_diag;
-                        double &cell = d[((size_t)z * n[1] + y) * n[0] + x];
-                        if (dd < cell) cell = dd;
-                    }
-        }
-    };
-    std::vector<std::thread> th;
-    for (unsigned i = 1; i < hw; ++i) th.emplace_back(work, i);
-    work(0);
-    for (auto &t : th) t.join();
-    b->dgrid.assign(cells, 0.0f);
-    const double scale = std::max(std::fabs(lo[0]), std::max(std::fabs(lo[1]), std::fabs(lo[2]))) + ext;
-    const double margin = 1e-4 + 1e-6 * scale;       // rounding of the FP32 query point and comparison
-    for (size_t i = 0; i < cells; ++i) {
-        double m = part[0][i];
-        for (unsigned k = 1; k < hw; ++k) m = std::min(m, part[k][i]);
-        b->dgrid[i] = (float)std::max(0.0, m - margin);
-    }
-    for (int c = 0; c < 3; ++c) { b->dgrid_lo[c] = (float)lo[c]; b->dgrid_n[c] = n[c]; }
-    b->dgrid_h = (float)h;
-    return GADEP_OK;
-}
-
-float distance_bound(const gadep_bvh *b, const float p[3])
-{
-    int i[3];
-    for (int c = 0; c < 3; ++c) {
-        const float f = std::floor((p[c] - b->dgrid_lo[c]) / b->dgrid_h);
-        if (!(f >= 0.0f) || !(f < (float)b->dgrid_n[c])) return 0.0f;
-        i[c] = (int)f;
-    }
-    return b->dgrid[((size_t)i[2] * b->dgrid_n[1] + i[1]) * b->dgrid_n[0] + i[0]];
-}
-
-}  // namespace gadep
-
-extern "C" gadep_status gadep_bvh_distance_bound(gadep_bvh *b, const float *points, int64_t n, float *out)
-{
-    gadep::clear_error();
-    if (!b || n < 0 || (n > 0 && (!points || !out)))
-        return gadep::fail(GADEP_E_INVAL, "gadep_bvh_distance_bound: bad arguments");
-    gadep_status st;
-    {
-        std::lock_guard<std::mutex> lock(b->wf_mutex);
-        st = gadep::build_distance_grid(b);
-    }
-    if (st != GADEP_OK) return st;
-    for (int64_t i = 0; i < n; ++i) out[i] = gadep::distance_bound(b, points + 3 * i);
     return GADEP_OK;
 }

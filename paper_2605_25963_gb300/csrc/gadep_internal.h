@@ -78,12 +78,6 @@ struct gadep_bvh {
     // arguments repeat and the cached CUDA graph of the wavefront loop is reused
     void *plan_scratch = nullptr;
     size_t plan_scratch_bytes = 0;
-    // lower bounds on the distance to the nearest triangle on a grid over the mesh
-    // (built on first use by charged-particle tracks; see build_distance_grid)
-    std::vector<float> dgrid;
-    float dgrid_lo[3] = { 0, 0, 0 }, dgrid_h = 0.0f;
-    int dgrid_n[3] = { 0, 0, 0 };
-    void *d_dgrid = nullptr;
     gadep_bvh_stats stats{};
     void *d_nodes = nullptr, *d_tris = nullptr, *d_tri_orig = nullptr, *d_regions = nullptr,
          *d_planes = nullptr;
@@ -93,6 +87,4 @@ namespace gadep {
 std::vector<std::vector<int32_t>> region_triangle_sets(const MeshData &g);
 gadep_status upload_bvh(gadep_bvh *b);
 void free_bvh_device(gadep_bvh *b);
-gadep_status build_distance_grid(gadep_bvh *b);      // host grid, once (caller holds wf_mutex)
-float distance_bound(const gadep_bvh *b, const float p[3]);
 }  // namespace gadep

@@ -503,8 +503,6 @@ void free_bvh_device(gadep_bvh *b)
     cudaFree(b->plan_scratch);
     b->plan_scratch = nullptr;
     b->plan_scratch_bytes = 0;
-    cudaFree(b->d_dgrid);
-    b->d_dgrid = nullptr;
     cudaFree(b->d_nodes);
     cudaFree(b->d_tris);
     cudaFree(b->d_regions);
@@ -1051,29 +1049,6 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
     P.e_T_min = electrons ? (float)mat->T_min : 0.0f;
     P.e_lnT_min = electrons ? (float)std::log(mat->T_min) : 0.0f;
     P.e_inv_dlnT = electrons ? (float)((mat->e_n - 1) / (std::log(mat->T_max) - std::log(mat->T_min))) : 0.0f;
-    P.dgrid = nullptr;
-    if (electrons) {
-        // the distance bounds of the mesh, built and copied to the device once
-        gadep_bvh *bm = const_cast<gadep_bvh *>(b);
-        std::lock_guard<std::mutex> lock(bm->wf_mutex);
-        if (build_distance_grid(bm) == GADEP_OK && !bm->d_dgrid) {
-            void *d = nullptr;
-            if (cudaMalloc(&d, bm->dgrid.size() * sizeof(float)) == cudaSuccess &&
-                cudaMemcpy(d, bm->dgrid.data(), bm->dgrid.size() * sizeof(float), cudaMemcpyHostToDevice) ==
-                    cudaSuccess) {
-                bm->d_dgrid = d;
-            } else {
-                cudaGetLastError();
-                cudaFree(d);
-            }
-        }
-        clear_error();                  // without the bounds the tracks only run slower
-        if (bm->d_dgrid) {
-            P.dgrid = (const float *)bm->d_dgrid;
-            for (int c = 0; c < 3; ++c) { P.dg_lo[c] = bm->dgrid_lo[c]; P.dg_n[c] = bm->dgrid_n[c]; }
-            P.dg_inv_h = 1.0f / bm->dgrid_h;
-        }
-    }
     // scene bounds seen from the world (births outside it whose ray misses it end at once)
     scene_box(b, P.root_lo, P.root_hi);
     *out = p;

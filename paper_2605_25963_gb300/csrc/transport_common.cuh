@@ -60,10 +60,6 @@ struct Params {
     const float *erange;                // [n_mat][e_n]
     int e_model, e_n;
     float e_T_min, e_lnT_min, e_inv_dlnT;
-    // lower bounds on the distance to the nearest triangle (gadep_bvh_distance_bound)
-    const float *dgrid;                 // [nz][ny][nx]; NULL = none
-    float dg_lo[3], dg_inv_h;
-    int dg_n[3];
 };
 
 // Slab test of the ray (t >= 0) against an axis-aligned box.
@@ -279,19 +275,6 @@ __device__ __noinline__ void e_track(const Params &P, const int4 *s_reg, const f
         const float sc = group >= 0 ? scale[group] : 1.0f;
         const float rn = R.x >= 0 ? erange_at(P, R.x, T) : INFINITY;
         const float reach = rn / sc;
-        if (k == 0 && P.dgrid && reach < INFINITY) {
-            // no surface within the distance bound of the birth point: the track
-            // stops in this region (what the traversal below would find)
-            const int ix = (int)floorf((px - P.dg_lo[0]) * P.dg_inv_h);
-            const int iy = (int)floorf((py - P.dg_lo[1]) * P.dg_inv_h);
-            const int iz = (int)floorf((pz - P.dg_lo[2]) * P.dg_inv_h);
-            if (ix >= 0 && iy >= 0 && iz >= 0 && ix < P.dg_n[0] && iy < P.dg_n[1] && iz < P.dg_n[2] &&
-                reach <= __ldg(P.dgrid + ((size_t)iz * P.dg_n[1] + iy) * P.dg_n[0] + ix)) {
-                dep_all += w * T;
-                if (R.y & 1) edep += w * T;
-                return;
-            }
-        }
         float t_hit = INFINITY;
         bool entering = false;
         int hit = traverse<COUNT>(P.nodes, P.tris, P.planes, R.w, px, py, pz, ux, uy, uz, t_cur, last, t_hit,

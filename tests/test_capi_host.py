@@ -206,50 +206,3 @@ def test_opts_defaults():
     assert o.seed == 1 and o.n_bins == 4096 and o.step_cap == 10000
     assert abs(o.e_cut_keV - 10.0) < 1e-6 and abs(o.fep_delta_keV - 0.01) < 1e-9
     assert list(o.group_scale) == [1.0] * 8
-
-
-def _point_triangle_distance(p, A, B, C):
-    """Exact distance from point p to every triangle (A, B, C: [m, 3]): the foot of
-    the perpendicular when it falls inside the triangle, else the nearest point of
-    the three edges (written independently of the library's Voronoi-region form)."""
-    n = np.cross(B - A, C - A)
-    nn = np.linalg.norm(n, axis=1)
-    u = n / nn[:, None]
-    h = np.einsum("ij,ij->i", p - A, u)
-    f = p - h[:, None] * u
-    inside = ((np.einsum("ij,ij->i", np.cross(B - A, f - A), n) >= 0)
-              & (np.einsum("ij,ij->i", np.cross(C - B, f - B), n) >= 0)
-              & (np.einsum("ij,ij->i", np.cross(A - C, f - C), n) >= 0))
-
-    def seg(P0, P1):
-        d = P1 - P0
-        t = np.clip(np.einsum("ij,ij->i", p - P0, d) / np.einsum("ij,ij->i", d, d), 0.0, 1.0)
-        return np.linalg.norm(p - (P0 + t[:, None] * d), axis=1)
-
-    edge = np.minimum(np.minimum(seg(A, B), seg(B, C)), seg(C, A))
-    return np.where(inside, np.abs(h), edge)
-
-
-@pytest.mark.parametrize("name", ["COAX_P", "STRESS_SMALL"])
-def test_distance_bound_is_a_lower_bound(name):
-    m = api.detmesh_build(getattr(W, name))
-    b = api.gadep_bvh_build(m, device=-1)
-    X, T = m.arrays()[0].astype(np.float32).astype(np.float64), m.arrays()[1]
-    A, B, C = X[T[:, 0]], X[T[:, 1]], X[T[:, 2]]
-    rng = np.random.default_rng(3)
-    lo, hi = X.min(0), X.max(0)
-    pts = [rng.uniform(lo, hi, size=(300, 3))]
-    # points close to the surfaces: triangle centroids pushed off along random directions
-    k = rng.integers(0, len(T), 300)
-    cen = (A[k] + B[k] + C[k]) / 3.0
-    pts.append(cen + rng.normal(scale=0.7, size=(300, 3)))
-    pts = np.concatenate(pts).astype(np.float32)
-    bound = b.distance_bound(pts)
-    exact = np.array([_point_triangle_distance(p.astype(np.float64), A, B, C).min() for p in pts])
-    assert np.all(bound <= exact + 1e-6), np.max(bound - exact)
-    # and not vacuous: within reach of the grid the bound trails the distance by at most a
-    # cell diagonal (cells ~1/128 of the largest extent) plus the margin
-    diag = np.sqrt(3.0) * (hi - lo).max() / 128.0
-    near = exact < 1.5
-    assert np.all(bound[near] >= exact[near] - diag - 1e-3)
-    assert (bound > 0.5).mean() > 0.3
