@@ -417,16 +417,17 @@ void gadep_plan_destroy(gadep_plan *p);
 gadep_status gadep_measure_peaks(int32_t device, double *fp32_tflops, double *l2_read_gbs);
 
 /* Kernel launches of a plan since the last reset, per kind: the persistent
- * megakernel, or the six kernels of each wavefront iteration plus the slot-list
- * initialisation.  With timing on, gadep_plan_launch records a CUDA event pair
- * on the launching stream around every launch and ms[] sums their elapsed
- * times (device time of the kernels alone, without host gaps). */
+ * megakernel, or the kernels of each wavefront iteration (with e_model 1 also the
+ * deferred charged-particle tracks, ETRACK) plus the slot-list initialisation.
+ * With timing on, gadep_plan_launch records a CUDA event pair on the launching
+ * stream around every launch and ms[] sums their elapsed times (device time of
+ * the kernels alone, without host gaps).  Entries past the last kind are 0. */
 enum { GADEP_KERNEL_MEGA = 0, GADEP_KERNEL_SPAWN = 1, GADEP_KERNEL_TRACE = 2, GADEP_KERNEL_PHYSICS = 3,
        GADEP_KERNEL_GEN = 4, GADEP_KERNEL_CTRL = 5, GADEP_KERNEL_INIT = 6, GADEP_KERNEL_SORT = 7,
-       GADEP_N_KERNEL_KINDS = 8 };
+       GADEP_KERNEL_ETRACK = 8, GADEP_N_KERNEL_KINDS = 9 };
 typedef struct {
-    uint64_t launches[8];     /* [GADEP_KERNEL_*] */
-    double   ms[8];           /* [GADEP_KERNEL_*], 0 unless timing was on */
+    uint64_t launches[16];    /* [GADEP_KERNEL_*] */
+    double   ms[16];          /* [GADEP_KERNEL_*], 0 unless timing was on */
 } gadep_kernel_stats;
 /* on != 0 turns per-launch event timing on for later launches of the plan. */
 gadep_status gadep_plan_set_timing(gadep_plan *p, int32_t on);

@@ -27,7 +27,7 @@ EXPORTS = (
     "gadep_plan_kernel_stats", "gadep_measure_peaks",
 )
 # kernel kinds of gadep_kernel_stats
-KERNEL_KINDS = ("mega", "spawn", "trace", "physics", "gen", "ctrl", "init", "sort")
+KERNEL_KINDS = ("mega", "spawn", "trace", "physics", "gen", "ctrl", "init", "sort", "etrack")
 
 
 class GadepError(RuntimeError):
@@ -95,7 +95,7 @@ class gadep_result(C.Structure):
 
 
 class gadep_kernel_stats(C.Structure):
-    _fields_ = [("launches", C.c_uint64 * 8), ("ms", C.c_double * 8)]
+    _fields_ = [("launches", C.c_uint64 * 16), ("ms", C.c_double * 16)]
 
 
 class gadep_instance(C.Structure):

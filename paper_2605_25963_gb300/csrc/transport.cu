@@ -1242,7 +1242,7 @@ extern "C" gadep_status gadep_plan_kernel_stats(gadep_plan *p, gadep_kernel_stat
     DeviceGuard g(p->device);
     const cudaError_t e = p->timer.resolve();
     std::memset(out, 0, sizeof(*out));
-    for (int k = 0; k < gadep::KK_N && k < 8; ++k) {
+    for (int k = 0; k < gadep::KK_N && k < 16; ++k) {
         out->launches[k] = p->timer.launches[k];
         out->ms[k] = p->timer.ms[k];
     }

@@ -258,9 +258,9 @@ constexpr int kMaxTrackCrossings = 256;
 // Below e_T_min the rest is deposited where they are; vacuum takes nothing; what
 // leaves the mesh escapes.  Active deposits go to edep, all to dep_all.
 template <bool COUNT>
-__device__ __noinline__ void e_track(const Params &P, const int4 *s_reg, const float *scale, float px, float py,
-                                     float pz, float ux, float uy, float uz, float T, float w, int region,
-                                     float &edep, float &dep_all, float &esc, uint32_t &herr, TravStats &ts)
+__device__ void e_track(const Params &P, const int4 *s_reg, const float *scale, float px, float py, float pz,
+                        float ux, float uy, float uz, float T, float w, int region, float &edep, float &dep_all,
+                        float &esc, uint32_t &herr, TravStats &ts)
 {
     float t_cur = 0.0f;
     int last = -1;
@@ -313,7 +313,7 @@ __device__ __noinline__ void e_track(const Params &P, const int4 *s_reg, const f
 
 // Kernel launches of a plan, counted per kind, and optionally timed with CUDA
 // events recorded on the launching stream around every launch.
-enum KernelKind { KK_MEGA = 0, KK_SPAWN, KK_TRACE, KK_PHYSICS, KK_GEN, KK_CTRL, KK_INIT, KK_SORT, KK_N };
+enum KernelKind { KK_MEGA = 0, KK_SPAWN, KK_TRACE, KK_PHYSICS, KK_GEN, KK_CTRL, KK_INIT, KK_SORT, KK_ETRACK, KK_N };
 struct KernelTimer {
     bool timing = false;
     unsigned long long launches[KK_N] = {};

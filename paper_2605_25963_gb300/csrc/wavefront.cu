@@ -63,6 +63,14 @@ struct __align__(16) Hit {      // by queue position, written by trace
 };
 constexpr int kBeyond = -3;
 static_assert(sizeof(Slot) == 64, "slot record is one 64-byte DRAM fetch");
+// A charged-particle track (e_model 1) whose history goes on after the physics
+// visit that set it going: traced by etrack_kernel before the slot's next visit.
+struct __align__(16) Track {
+    float4 p;                   // start point, w = kinetic energy
+    float4 u;                   // unit direction, w = number of particles on the line
+    unsigned int slot, tag;     // tag = region | instance << 8
+    unsigned int pad[2];
+};
 struct __align__(32) Sec {      // second annihilation photon, waiting for the first
     float4 p;                   // position
     float4 d;                   // direction, w = region bits
@@ -289,6 +297,7 @@ struct Ctrl {
     unsigned long long sp_head;
     unsigned long long gen_live;   // ring entries left once the next spawn has run
     unsigned long long max_iter;
+    unsigned int t_count;          // deferred charged-particle tracks of this iteration
 };
 
 struct State {
@@ -304,6 +313,7 @@ struct State {
     unsigned int *base;            // bucket starts of the sort
     unsigned int *qsort;           // the queue in key order: what trace and physics walk
     unsigned int *free_slots;      // stack of free slots: spawn pops, physics pushes
+    Track *trk;                    // deferred tracks (e_model 1), one per slot at most
     unsigned long long *pend;      // ring of global history indices waiting for a slot
     unsigned long long pend_mask;  // ring size - 1 (a power of two)
     unsigned long long gen_target; // ring fill at which gen stops claiming ids
@@ -382,6 +392,7 @@ __global__ void init_kernel(State S, unsigned long long max_iter)
         c.sp_head = 0;
         c.gen_live = 0;
         c.max_iter = max_iter;
+        c.t_count = 0;
     }
 }
 
@@ -407,6 +418,7 @@ __device__ __forceinline__ void ctrl_step(Ctrl &c, int cur, unsigned long long t
     c.free_top = n_free - filled;
     c.q_count[nxt] = n_alive + filled;
     c.q_count[cur] = 0;
+    c.t_count = 0;                 // etrack has run
     c.trace_head = 0;
     c.gen_live = avail - filled;
     c.iter++;
@@ -815,7 +827,7 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
     const int nxt = cur ^ 1;
     // shared: region table (material slot, flags, parent, root), then block tallies
     extern __shared__ int4 s_reg[];
-    __shared__ unsigned int s_cnt[2], s_base[2];
+    __shared__ unsigned int s_cnt[3], s_base[3];    // queue, free slots, deferred tracks
     for (int i = threadIdx.x; i < P.n_region; i += blockDim.x) s_reg[i] = P.regions[i];
     BlockTally<GRAD> bt;
     bt.init(s_reg + P.n_region, P.n_inst);
@@ -824,7 +836,7 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
         reinterpret_cast<char *>(s_reg + P.n_region) + block_tally_bytes<GRAD>(P.n_inst));
     const int n_keys = P.n_keys;
     for (int k = threadIdx.x; k < n_keys; k += blockDim.x) s_hist[k] = 0u;
-    if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
+    if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     const unsigned int n = S.ctrl->q_count[cur];
     const int lane = threadIdx.x & 31;
@@ -845,6 +857,8 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
         bool fep_out = false;
         float dep_all_out = 0.0f, esc_out = 0.0f;
         uint32_t segs_out = 0;
+        bool defer = false;             // EM: a track left to etrack_kernel
+        Track tr;
         if (mine) {
             const Hit ht = S.hit[j];
             const Slot sl = S.slot[slot];
@@ -974,11 +988,21 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
                     }
                     if (R.y & 1) edep += dep;
                     dep_all += dep;
-                    if (eT > 0.0f && !herr) {
-                        float e_esc = 0.0f;
-                        e_track<COUNT>(P, s_reg, I.scale, px, py, pz, eux, euy, euz, eT, ew, region, edep, dep_all,
-                                       e_esc, herr, ts);
-                        esc_now += e_esc;
+                    if (EM && eT > 0.0f && !herr) {
+                        if (!photon_done || (flags & kFlagSec)) {
+                            // the history goes on: etrack_kernel adds the track's deposits
+                            // to the slot before its next visit, with full warps
+                            defer = true;
+                            tr.p = make_float4(px, py, pz, eT);
+                            tr.u = make_float4(eux, euy, euz, ew);
+                            tr.slot = slot;
+                            tr.tag = (uint32_t)region | ((uint32_t)inst << 8);
+                        } else {
+                            float e_esc = 0.0f;
+                            e_track<COUNT>(P, s_reg, I.scale, px, py, pz, eux, euy, euz, eT, ew, region, edep,
+                                           dep_all, e_esc, herr, ts);
+                            esc_now += e_esc;
+                        }
                     }
                     ry.o = make_float4(px, py, pz, 0.0f);
                     last_tri = -1;
@@ -1059,22 +1083,28 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
         if (binned && lane == __ffs(peers) - 1)
             atomicAdd(&P.spectra[(size_t)inst * P.n_bins + bin], (uint32_t)__popc(peers));
         // ---- queue / free-list appends: one global atomic per list, block and pass ----
+        const bool dt = EM && defer && alive_slot;     // the history goes on (no error either)
         const uint32_t ma = __ballot_sync(FULL, alive_slot), mf = __ballot_sync(FULL, finished);
-        unsigned int oa = 0, of = 0;
+        const uint32_t mt = EM ? __ballot_sync(FULL, dt) : 0u;
+        unsigned int oa = 0, of = 0, ot = 0;
         if (lane == 0) {
             if (ma) oa = atomicAdd(&s_cnt[0], (unsigned int)__popc(ma));
             if (mf) of = atomicAdd(&s_cnt[1], (unsigned int)__popc(mf));
+            if (EM && mt) ot = atomicAdd(&s_cnt[2], (unsigned int)__popc(mt));
         }
         const uint32_t below = (1u << lane) - 1u;
         oa = __shfl_sync(FULL, oa, 0) + __popc(ma & below);
         of = __shfl_sync(FULL, of, 0) + __popc(mf & below);
+        if (EM) ot = __shfl_sync(FULL, ot, 0) + __popc(mt & below);
         __syncthreads();
         if (threadIdx.x == 0) {
             s_base[0] = s_cnt[0] ? atomicAdd(&S.ctrl->q_count[nxt], s_cnt[0]) : 0u;
             s_base[1] = s_cnt[1] ? atomicAdd(&S.ctrl->free_top, s_cnt[1]) : 0u;
-            s_cnt[0] = s_cnt[1] = 0;
+            if (EM) s_base[2] = s_cnt[2] ? atomicAdd(&S.ctrl->t_count, s_cnt[2]) : 0u;
+            s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
         }
         __syncthreads();
+        if (EM && dt) S.trk[s_base[2] + ot] = tr;
         if (alive_slot) {
             S.queue[nxt][s_base[0] + oa] = slot;
             S.qkey[nxt][s_base[0] + oa] = key;
@@ -1086,6 +1116,44 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
     bt.flush(block_tally(P));     // starts with a barrier
     for (int k = threadIdx.x; k < n_keys; k += blockDim.x)
         if (s_hist[k]) atomicAdd(&S.hist[nxt][k], s_hist[k]);
+    if (COUNT) {
+        if (ts.nodes) atomicAdd(&counters[0], (unsigned long long)ts.nodes);
+        if (ts.tris) atomicAdd(&counters[1], (unsigned long long)ts.tris);
+        if (ts.relocated) atomicAdd(&counters[2], (unsigned long long)ts.relocated);
+    }
+}
+
+// ---------------------------------------------------------------- etrack
+// The charged-particle tracks physics deferred in this iteration (e_model 1), one
+// per thread: their deposits and escapes join the history in its slot, and an
+// error of the track becomes the history's, before the slot's next physics visit.
+template <bool COUNT>
+__global__ void __launch_bounds__(256) etrack_kernel(const Params P, State S, unsigned long long *counters)
+{
+    __shared__ int4 s_reg[256];
+    for (int i = threadIdx.x; i < P.n_region; i += blockDim.x) s_reg[i] = P.regions[i];
+    __syncthreads();
+    const unsigned int n = S.ctrl->t_count;
+    TravStats ts{ 0u, 0u, 0u };
+    for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Track t = S.trk[i];
+        const int region = (int)(t.tag & 255u), inst = (int)(t.tag >> 8);
+        float edep = 0.0f, dep_all = 0.0f, esc = 0.0f;
+        uint32_t herr = 0;
+        e_track<COUNT>(P, s_reg, P.inst[inst].scale, t.p.x, t.p.y, t.p.z, t.u.x, t.u.y, t.u.z, t.p.w, t.u.w, region,
+                       edep, dep_all, esc, herr, ts);
+        Phot &ph = S.slot[t.slot].p;
+        ph.f.z += edep;
+        ph.f.w += dep_all;
+        uint32_t uz = ph.u.z;
+        if (esc != 0.0f) {
+            const bool had = ((uz >> 24) & kFlagEsc) != 0u;
+            S.esc[t.slot] = (had ? S.esc[t.slot] : 0.0f) + esc;
+            uz |= (uint32_t)kFlagEsc << 24;
+        }
+        uz |= (herr & 0xffu) << 16;
+        ph.u.z = uz;
+    }
     if (COUNT) {
         if (ts.nodes) atomicAdd(&counters[0], (unsigned long long)ts.nodes);
         if (ts.tris) atomicAdd(&counters[1], (unsigned long long)ts.tris);
@@ -1107,6 +1175,7 @@ struct WavefrontBuffers {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<unsigned char> graph_key;
+    void *trk = nullptr;             // deferred-track records, allocated by the first e_model 1 run
 };
 
 int wavefront_trace_grid(const WavefrontBuffers *w) { return w ? w->trace_grid : 0; }
@@ -1194,6 +1263,7 @@ void wavefront_destroy(WavefrontBuffers *w)
     if (!w) return;
     if (w->exec) cudaGraphExecDestroy(w->exec);
     if (w->graph) cudaGraphDestroy(w->graph);
+    cudaFree(w->trk);
     cudaFree(w->block);
     cudaFreeHost(w->host_ctrl);
     delete w;
@@ -1203,6 +1273,15 @@ void wavefront_destroy(WavefrontBuffers *w)
 gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P0, bool grad, bool count,
                            unsigned long long *counters, KernelTimer *timer, cudaStream_t s)
 {
+    if (P0.e_model && !w->trk) {
+        void *t = nullptr;
+        if (cudaMalloc(&t, (size_t)w->S.slots * sizeof(wf::Track)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(GADEP_E_NOMEM, "wavefront: cudaMalloc of the track records failed");
+        }
+        w->trk = t;
+        w->S.trk = (wf::Track *)t;
+    }
     wf::State S = w->S;
     dev::Params P = P0;
     P.face_bins = wf::face_bins_for(P.n_region);
@@ -1272,6 +1351,8 @@ gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P0, bool grad
                 fn = count ? (const void *)wf::physics_kernel<false, true, false>
                            : (const void *)wf::physics_kernel<false, false, false>;
             grid = dim3(w->work_grid); smem = rsm; args[0] = &P; args[1] = &S; args[2] = &c; args[3] = &counters; break;
+        case KK_ETRACK: fn = count ? (const void *)wf::etrack_kernel<true> : (const void *)wf::etrack_kernel<false>;
+            grid = dim3(w->work_grid); args[0] = &P; args[1] = &S; args[2] = &counters; break;
         default: return cudaErrorInvalidValue;
         }
         if (!g) return cudaLaunchKernel(fn, grid, block, args, smem, s);
@@ -1284,7 +1365,16 @@ gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P0, bool grad
         kp.extra = nullptr;
         return cudaGraphAddKernelNode(node, g, dep, n_dep, &kp);
     };
-    static const int kIteration[] = { KK_SPAWN, KK_N, KK_SORT, KK_TRACE, KK_PHYSICS, KK_GEN, KK_CTRL };
+    // the kernels of one iteration; the deferred charged-particle tracks run right
+    // after physics
+    int kIteration[8] = { KK_SPAWN, KK_N, KK_SORT, KK_TRACE, KK_PHYSICS, KK_GEN, KK_CTRL, KK_CTRL };
+    int n_iter = 7;
+    if (P.e_model) {
+        kIteration[5] = KK_ETRACK;
+        kIteration[6] = KK_GEN;
+        kIteration[7] = KK_CTRL;
+        n_iter = 8;
+    }
     KernelTimer none;
     KernelTimer &T = timer ? *timer : none;
 
@@ -1342,7 +1432,7 @@ gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P0, bool grad
                 cudaGraph_t body = cp.conditional.phGraph_out[0];
                 cudaGraphNode_t bprev = nullptr;
                 for (int cur = 0; cur < 2 && e == cudaSuccess; ++cur)
-                    for (int k = 0; k < 7 && e == cudaSuccess; ++k) {
+                    for (int k = 0; k < n_iter && e == cudaSuccess; ++k) {
                         e = launch(kIteration[k], cur, body, bprev ? &bprev : nullptr, bprev ? 1 : 0, &node, loop, 1);
                         bprev = node;
                     }
@@ -1373,7 +1463,7 @@ gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P0, bool grad
     const int check_every = 16;
     for (unsigned long long it = 0;; ++it) {
         const int cur = (int)(it & 1);
-        for (int k = 0; k < 7; ++k) {
+        for (int k = 0; k < n_iter; ++k) {
             const int kind = kIteration[k];
             if (kind != KK_SORT) T.before(s);      // the prefix and the sort are timed together
             const cudaError_t e = launch(kind, cur, nullptr, nullptr, 0, nullptr, 0, 0);

@@ -84,7 +84,9 @@ def test_wavefront_equals_megakernel_with_tracks(mats, orc):
     rw, sw = api.gadep_run(b, mats, W.COAX_POINT_25, 1332.0, n, edep_trace=tw,
                            opts=api.make_opts(variant=WAVEFRONT, wf_slots=32768, e_model=1))
     assert rw["n_err"] == 0 and rw["n_hist"] == n
-    assert np.mean(tm.cpu().numpy() == tw.cpu().numpy()) >= 0.9999
+    # the wavefront form adds a track's deposits after the photon's segment when the
+    # history goes on (etrack kernel), the megakernel at once: FP32 sums in another order
+    assert np.mean(np.abs(tm.cpu().numpy() - tw.cpu().numpy()) <= 1e-3) >= 0.9999
     for k in ("n_fep", "n_zero", "n_over"):
         assert abs(rm[k] - rw[k]) <= 2, k
     assert rw["sum_dep_all"] + rw["sum_esc"] == pytest.approx(n * 1332.0, rel=1e-5)
