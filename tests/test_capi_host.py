@@ -206,3 +206,37 @@ def test_opts_defaults():
     assert o.seed == 1 and o.n_bins == 4096 and o.step_cap == 10000
     assert abs(o.e_cut_keV - 10.0) < 1e-6 and abs(o.fep_delta_keV - 0.01) < 1e-9
     assert list(o.group_scale) == [1.0] * 8
+
+
+STRUCTS = ("detmesh_params", "gadep_solid", "gadep_bvh_opts", "gadep_bvh_stats", "gadep_materials",
+           "gadep_source", "gadep_opts", "gadep_result", "gadep_kernel_stats", "gadep_instance")
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors in capi.py have the sizes and field offsets the C compiler
+    gives the structs of include/gadep.h (gcc, the host ABI the library is built with)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gadep.h"', "int main(void) {"]
+    for name in STRUCTS:
+        cls = getattr(capi, name)
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for field, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, field, name, field))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in filter(None, out):
+        name, key, val = line.split()
+        got[(name, key)] = int(val)
+    for name in STRUCTS:
+        cls = getattr(capi, name)
+        assert C.sizeof(cls) == got[(name, "size")], name
+        for field, _ in cls._fields_:
+            assert getattr(cls, field).offset == got[(name, field)], (name, field)

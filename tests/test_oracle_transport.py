@@ -213,3 +213,34 @@ def test_history_offset_partitions_exactly(orc):
     for k in ("n_fep", "n_zero", "n_over", "n_crossings", "n_interactions"):
         assert full.tally[k] == a.tally[k] + b.tally[k]
     assert np.array_equal(full.spectrum, a.spectrum + b.spectrum)
+
+
+def test_oracle_struct_layouts_match_header(orc, tmp_path):
+    """The oracle's ctypes mirrors have the sizes and offsets gcc gives oracle.h."""
+    import ctypes as C
+    import os
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    pairs = (("orc_detparams", orc.DetParams), ("orc_mesh", orc.MeshC), ("orc_tables", orc.TablesC),
+             ("orc_source", orc.SourceC), ("orc_opts", orc.OptsC), ("orc_tally", orc.TallyC))
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "oracle.h"', "int main(void) {"]
+    for name, cls in pairs:
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for field, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, field, name, field))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.dirname(os.path.abspath(orc.__file__))
+    subprocess.run(["gcc", "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in filter(None, subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")):
+        name, key, val = line.split()
+        got[(name, key)] = int(val)
+    for name, cls in pairs:
+        assert C.sizeof(cls) == got[(name, "size")], name
+        for field, _ in cls._fields_:
+            assert getattr(cls, field).offset == got[(name, field)], (name, field)
