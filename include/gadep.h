@@ -291,7 +291,9 @@ typedef struct {
     float    e_max_keV;       /* spectrum range [0, e_max) (default 3000) */
     int32_t  n_bins;          /* spectrum bins (default 4096) */
     int32_t  step_cap;        /* segments per history before it is ended as an error (1e4) */
-    int32_t  variant;         /* GADEP_VARIANT_* */
+    int32_t  variant;         /* GADEP_VARIANT_*; AUTO: the wavefront form when >= 2^18 histories are
+                                 expected to reach the scene (the mesh's bounding box), else the
+                                 megakernel */
     int32_t  block;           /* threads per block (0 = default) */
     int32_t  chunk;           /* histories a warp takes from the work counter at once (0 = default) */
     int32_t  blocks_per_sm;   /* persistent grid = SMs x this (0 = occupancy maximum) */

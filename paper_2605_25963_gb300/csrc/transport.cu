@@ -904,10 +904,13 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
     int variant = opts->variant;
     const bool wf_ok = n_inst <= kWavefrontMaxInstances &&
                        wavefront_supports((int)(regions.size() / 4), (long long)b->geo.n_tri());
+    // The wavefront form has a fixed cost per run (~2.5 ms: slot set, iterations of
+    // small queues) and ~1.5 ns per history that reaches the scene; the megakernel
+    // ~1 ms and ~6.7 ns (coax and Table 4 detector at 2e6 .. 1e7 histories per run):
+    // break-even near 2.9e5 reaching histories.  Histories that miss the scene cost
+    // little in either form.
     if (variant == GADEP_VARIANT_AUTO)
-        variant = wf_ok && ((total >= (1ull << 23) && reaching >= (double)(1u << 20)) || total >= (1ull << 26))
-                      ? GADEP_VARIANT_WAVEFRONT
-                      : GADEP_VARIANT_MEGA;
+        variant = wf_ok && reaching >= (double)(1u << 18) ? GADEP_VARIANT_WAVEFRONT : GADEP_VARIANT_MEGA;
     if (variant == GADEP_VARIANT_WAVEFRONT && !wf_ok) {
         gadep_plan_destroy(p);
         return fail(GADEP_E_INVAL, "plan: the wavefront form takes at most %d instances, 256 regions and "
