@@ -145,9 +145,10 @@ def test_batched_tracks_equal_individual_runs(orc, mats):
     items = []
     for i, (E, s, n, sm) in enumerate(W.batch_instances()[10:40:5]):
         items.append((E, W.BATCH_SOURCES[s], 20_000 + 991 * i, 5 * i + s, [1, 1, 1, sm]))
-    res, spec = api.gadep_run_batch(b, mats, api.make_instances(items), api.make_opts(e_model=1))
+    res, spec = api.gadep_run_batch(b, mats, api.make_instances(items), api.make_opts(e_model=1, variant=MEGA))
     for i, (E, src, n, iid, sc) in enumerate(items):
-        r, sp = api.gadep_run(b, mats, src, E, n, instance=iid, opts=api.make_opts(e_model=1, group_scale=sc))
+        r, sp = api.gadep_run(b, mats, src, E, n, instance=iid,
+                              opts=api.make_opts(e_model=1, group_scale=sc, variant=MEGA))
         for k in ("n_hist", "n_fep", "n_zero", "n_over", "n_err", "n_segments", "n_interactions"):
             assert r[k] == res[i][k], (i, k)
         assert np.array_equal(sp, spec[i])
