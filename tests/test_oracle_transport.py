@@ -177,6 +177,32 @@ def test_source_moments(orc):
     assert abs(dirs[:, 2].mean()) < 0.02 and dirs[:, 2].var() == pytest.approx(1 / 3, rel=0.03)
 
 
+def test_point_and_pencil_sources(orc):
+    """Point: birth at the point, directions uniform on the sphere -- every
+    octant holds 1/8 of them and each Cartesian component has mean 0 and
+    variance 1/3 (a half-range azimuth or a sign slip fails the octant count).
+    Pencil: birth at its origin along its direction, exactly."""
+    N = 40000
+    pt = orc.Source(kind=W.SRC_POINT, pos=(3.0, -4.0, 25.0))
+    B = [orc.sample_birth(pt, 5, h) for h in range(N)]
+    P = np.array([b[0] for b in B])
+    D = np.array([b[1] for b in B])
+    assert np.all(P == np.array([3.0, -4.0, 25.0]))
+    assert np.allclose(np.linalg.norm(D, axis=1), 1.0, atol=1e-12)
+    for c in range(3):
+        assert abs(D[:, c].mean()) < 0.015
+        assert D[:, c].var() == pytest.approx(1 / 3, rel=0.03)
+    octant = (D[:, 0] > 0) * 4 + (D[:, 1] > 0) * 2 + (D[:, 2] > 0)
+    counts = np.bincount(octant, minlength=8)
+    assert np.all(np.abs(counts - N / 8) < 5 * math.sqrt(N / 8 * 7 / 8))
+    u = np.array([1.0, 2.0, -2.0]) / 3.0
+    pen = orc.Source(kind=W.SRC_PENCIL, pos=(0.5, 0.25, -7.0), dir=tuple(u))
+    for h in (0, 1, 77, 123456):
+        p, d = orc.sample_birth(pen, 5, h)
+        assert np.all(p == np.array([0.5, 0.25, -7.0]))
+        assert np.allclose(d, u, rtol=0, atol=1e-15)
+
+
 def test_dos_gradient_slab_identity(orc):
     """Al slab (group 0) in front of a Ge slab: FEPE(s) = exp(-s mu x) K,
     so dFEPE/ds = -mu x FEPE exactly."""
