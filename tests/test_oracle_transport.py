@@ -6,6 +6,8 @@
   * Kahn sampler: chi-square against bin integrals of the Klein-Nishina
     angular distribution;
   * first-interaction process frequencies = mu_i / mu_tot;
+  * Compton angle in transport: backscatter fraction and energies against
+    the textbook Klein-Nishina formula;
   * pair production: deposit E - 2 mc^2 and two 511 keV photons;
   * energy conservation per history, parity rule == nesting-tree rule;
   * density-perturbation gradient: the slab identity dFEPE/ds = -mu x FEPE
@@ -108,6 +110,53 @@ def test_first_interaction_frequencies(orc):
     assert sum(obs) == N
     chi = stats.chisquare(obs, mu / mu.sum() * N)
     assert chi.pvalue > 0.001, (obs, mu / mu.sum() * N)
+
+
+def kn_textbook(k, c):
+    """Klein-Nishina dsigma/dOmega over r_e^2/2 (Klein & Nishina 1929), written
+    here from the textbook: P^2 (P + 1/P - sin^2 theta), P = E'/E."""
+    P = 1.0 / (1.0 + k * (1.0 - c))
+    return P * P * (P + 1.0 / P - (1.0 - c * c))
+
+
+@pytest.mark.parametrize("E", [59.5, 662.0, 1332.0])
+def test_compton_angle_backscatter_fraction(orc, E):
+    """The scattering angle inside transport (not the sampler alone): a pencil
+    beam crosses a thin Compton-only slab whose cross section vanishes below
+    0.98 E (so every photon scatters at most once) and a black, active catcher
+    10 m wide sits 2 mm behind the beam's origin.  A history deposits in the
+    catcher exactly when its photon scattered backward, with E' = E / (1 + k (1
+    - cos theta)) deposited: the fraction of scattered histories that deposit
+    is the Klein-Nishina backward fraction, every deposit lies in
+    [E/(1+2k), E/(1+k)], and their mean is the backward average of E'."""
+    k = E / MEC2
+    lnE = np.linspace(math.log(10.0), math.log(3000.0), 1000)
+    Eg = np.exp(lnE)
+    mu = np.zeros((3, 3, 1000), np.float32)
+    mu[1, 1, Eg > 0.98 * E] = 0.02               # scatterer: Compton only, 0.1 mm -> 0.2 %
+    mu[2, 0, :] = 1e3                            # catcher: photoabsorption, 1 um mean free path
+    t = orc.Tables.from_array(mu)
+    m = slab_mesh(orc, [(-50, -50, 0.0, 50, 50, 0.1), (-5e3, -5e3, -100.0, 5e3, 5e3, -2.0)],
+                  [1, 2], [0, 1])
+    src = orc.Source(kind=W.SRC_PENCIL, pos=(0, 0, -1.0), dir=(0, 0, 1.0))
+    N = 10_000_000
+    r = orc.transport(m, t, src, E, N, want_edep=True)
+    T = r.tally
+    assert T["n_err"] == 0 and T["n_first_pe"] == 0 and T["n_first_pair"] == 0
+    n_c = T["n_first_compton"]
+    assert n_c > 10_000
+    w = lambda c: kn_textbook(k, c)
+    tot = integrate.quad(w, -1, 1)[0]
+    back = integrate.quad(w, -1, 0)[0]
+    F = back / tot
+    dep = r.edep[r.edep > 0]
+    f = len(dep) / n_c
+    assert abs(f - F) < 4 * math.sqrt(F * (1 - F) / n_c), (f, F)
+    assert dep.min() >= E / (1 + 2 * k) * (1 - 1e-12) and dep.max() <= E / (1 + k) * (1 + 1e-12)
+    Ep = lambda c: E / (1 + k * (1 - c))
+    mean = integrate.quad(lambda c: Ep(c) * w(c), -1, 0)[0] / back
+    sd = math.sqrt(integrate.quad(lambda c: (Ep(c) - mean) ** 2 * w(c), -1, 0)[0] / back)
+    assert abs(dep.mean() - mean) < 4 * sd / math.sqrt(len(dep)), (dep.mean(), mean)
 
 
 def test_pair_production_deposits(orc):
