@@ -119,26 +119,36 @@ def kn_textbook(k, c):
     return P * P * (P + 1.0 / P - (1.0 - c * c))
 
 
-@pytest.mark.parametrize("E", [59.5, 662.0, 1332.0])
-def test_compton_angle_backscatter_fraction(orc, E):
+@pytest.mark.parametrize("E,alpha", [(59.5, 0.0), (662.0, 0.0), (1332.0, 0.0), (59.5, 1.0), (662.0, 1.0)])
+def test_compton_angle_backscatter_fraction(orc, E, alpha):
     """The scattering angle inside transport (not the sampler alone): a pencil
-    beam crosses a thin Compton-only slab whose cross section vanishes below
-    0.98 E (so every photon scatters at most once) and a black, active catcher
-    10 m wide sits 2 mm behind the beam's origin.  A history deposits in the
-    catcher exactly when its photon scattered backward, with E' = E / (1 + k (1
-    - cos theta)) deposited: the fraction of scattered histories that deposit
-    is the Klein-Nishina backward fraction, every deposit lies in
-    [E/(1+2k), E/(1+k)], and their mean is the backward average of E'."""
+    beam at angle alpha to +z crosses a thin Compton-only slab z in [0, 0.1]
+    whose cross section vanishes just below E (so every photon scatters once at
+    most); a black, active catcher 10 m wide fills z < -2, behind the beam's
+    origin.  A history deposits in the catcher exactly when its scattered
+    photon heads to -z, with E' = E / (1 + k (1 - cos theta)) deposited.  For
+    uniform azimuth the probability of heading to -z at polar cosine c about a
+    beam at alpha is arccos(cot(alpha) c / sin(theta)) / pi (a step at c = 0
+    for alpha = 0), so the deposit fraction is that weighted by Klein-Nishina
+    over c; the tilted beam (with a y component) takes the general branch of
+    the direction rotation.  Every deposit lies in [E/(1+2k), E]; for alpha = 0
+    in [E/(1+2k), E/(1+k)] with the backward average of E' as mean."""
     k = E / MEC2
-    lnE = np.linspace(math.log(10.0), math.log(3000.0), 1000)
-    Eg = np.exp(lnE)
-    mu = np.zeros((3, 3, 1000), np.float32)
-    mu[1, 1, Eg > 0.98 * E] = 0.02               # scatterer: Compton only, 0.1 mm -> 0.2 %
+    # 200,000 log-spaced grid points: the slab's cross section is 0.02 / mm from
+    # the grid point below E up and zero below the one before it, so only a
+    # photon scattered by less than ~6e-5 in relative energy could scatter again
+    n_grid = 200_000
+    Eg = np.exp(np.linspace(math.log(10.0), math.log(3000.0), n_grid))
+    j = int(np.searchsorted(Eg, E)) - 1
+    mu = np.zeros((3, 3, n_grid), np.float32)
+    mu[1, 1, j:] = 0.02                          # scatterer: Compton only, 0.1 mm -> 0.2 %
     mu[2, 0, :] = 1e3                            # catcher: photoabsorption, 1 um mean free path
     t = orc.Tables.from_array(mu)
     m = slab_mesh(orc, [(-50, -50, 0.0, 50, 50, 0.1), (-5e3, -5e3, -100.0, 5e3, 5e3, -2.0)],
                   [1, 2], [0, 1])
-    src = orc.Source(kind=W.SRC_PENCIL, pos=(0, 0, -1.0), dir=(0, 0, 1.0))
+    beta = 0.7
+    d = (math.sin(alpha) * math.cos(beta), math.sin(alpha) * math.sin(beta), math.cos(alpha))
+    src = orc.Source(kind=W.SRC_PENCIL, pos=(-d[0] / d[2], -d[1] / d[2], -1.0), dir=d)
     N = 10_000_000
     r = orc.transport(m, t, src, E, N, want_edep=True)
     T = r.tally
@@ -146,17 +156,24 @@ def test_compton_angle_backscatter_fraction(orc, E):
     n_c = T["n_first_compton"]
     assert n_c > 10_000
     w = lambda c: kn_textbook(k, c)
+    if alpha == 0.0:
+        heads_down = lambda c: 1.0 if c < 0 else 0.0
+    else:
+        heads_down = lambda c: math.acos(min(1.0, max(-1.0, c / math.tan(alpha) /
+                                                       math.sqrt(max(1e-300, 1 - c * c))))) / math.pi
     tot = integrate.quad(w, -1, 1)[0]
-    back = integrate.quad(w, -1, 0)[0]
-    F = back / tot
+    down = integrate.quad(lambda c: w(c) * heads_down(c), -1, 1, points=[0.0], limit=200)[0]
+    F = down / tot
     dep = r.edep[r.edep > 0]
     f = len(dep) / n_c
     assert abs(f - F) < 4 * math.sqrt(F * (1 - F) / n_c), (f, F)
-    assert dep.min() >= E / (1 + 2 * k) * (1 - 1e-12) and dep.max() <= E / (1 + k) * (1 + 1e-12)
-    Ep = lambda c: E / (1 + k * (1 - c))
-    mean = integrate.quad(lambda c: Ep(c) * w(c), -1, 0)[0] / back
-    sd = math.sqrt(integrate.quad(lambda c: (Ep(c) - mean) ** 2 * w(c), -1, 0)[0] / back)
-    assert abs(dep.mean() - mean) < 4 * sd / math.sqrt(len(dep)), (dep.mean(), mean)
+    assert dep.min() >= E / (1 + 2 * k) * (1 - 1e-12) and dep.max() <= E * (1 + 1e-12)
+    if alpha == 0.0:
+        assert dep.max() <= E / (1 + k) * (1 + 1e-12)
+        Ep = lambda c: E / (1 + k * (1 - c))
+        mean = integrate.quad(lambda c: Ep(c) * w(c), -1, 0)[0] / down
+        sd = math.sqrt(integrate.quad(lambda c: (Ep(c) - mean) ** 2 * w(c), -1, 0)[0] / down)
+        assert abs(dep.mean() - mean) < 4 * sd / math.sqrt(len(dep)), (dep.mean(), mean)
 
 
 def test_pair_production_deposits(orc):
