@@ -64,7 +64,7 @@ def test_two_rank_partition_equals_single_run(orc):
         for k, v in out.items():
             assert v == ref.tally[k], (rank, k)
         assert np.array_equal(np.array(spec), ref.spectrum)
-        assert fepe == ref.fepe and sigma == pytest.approx(ref.sigma, rel=1e-12)
+        assert fepe == ref.fepe and sigma == pytest.approx(ref.sigma, rel=1e-12, abs=0)
 
 
 def test_split_range_covers_everything():

@@ -1,6 +1,7 @@
 """Pins of the oracle's transport against closed forms (CPU only).
 
-  * narrow-beam slab transmission: P(E_dep > 0) = 1 - exp(-mu_tot x);
+  * narrow-beam slab transmission: P(E_dep > 0) = 1 - exp(-mu_tot x), and
+    across two density-scaled slabs;
   * black absorber: FEPE = (solid angle of the meshed top face) / 4 pi, from
     the Van Oosterom-Strackee formula summed over the fan triangles;
   * Kahn sampler: chi-square against bin integrals of the Klein-Nishina
@@ -50,6 +51,30 @@ def test_slab_transmission(orc):
         sig = math.sqrt(expect * (1 - expect) / N)
         assert abs(p_int - expect) < 4 * sig, (E, p_int, expect)
         assert r.tally["n_err"] == 0
+
+
+@pytest.mark.parametrize("s1,s2", [(1.0, 1.0), (1.7, 1.0), (0.4, 2.5)])
+def test_density_scaled_two_slab_transmission(orc, s1, s2):
+    """Free flight across a boundary with density scales (Sec. 2.4.1 free
+    flight; the scales of the gradient's density groups): photoabsorption-only
+    slabs, the first inactive (group 0, scale s1, thickness x1), the second
+    active (group 1, scale s2, thickness x2).  A photon deposits exactly when it
+    crosses the first slab and is absorbed in the second:
+    P = exp(-s1 mu1 x1) (1 - exp(-s2 mu2 x2))."""
+    x1, x2, mu1, mu2 = 3.0, 2.0, 0.2, 0.35
+    mu = np.zeros((3, 3, 1000), np.float32)
+    mu[1, 0, :] = mu1
+    mu[2, 0, :] = mu2
+    t = orc.Tables.from_array(mu)
+    m = slab_mesh(orc, [(-50, -50, -x1, 50, 50, 0.0), (-50, -50, -x1 - 1.0 - x2, 50, 50, -x1 - 1.0)],
+                  [1, 2], [0, 1], groups=[0, 1])
+    src = orc.Source(kind=W.SRC_PENCIL, pos=(0, 0, 5.0), dir=(0, 0, -1.0))
+    N = 400_000
+    r = orc.transport(m, t, src, 662.0, N, group_scale=(s1, s2))
+    p = 1 - r.tally["n_zero"] / N
+    expect = math.exp(-s1 * mu1 * x1) * (1 - math.exp(-s2 * mu2 * x2))
+    assert abs(p - expect) < 4 * math.sqrt(expect * (1 - expect) / N), (p, expect)
+    assert r.tally["n_first_pe"] == N - r.tally["n_first_none"]
 
 
 def vos_solid_angle(obs, tri_pts):
@@ -176,6 +201,92 @@ def test_compton_angle_backscatter_fraction(orc, E, alpha):
         assert abs(dep.mean() - mean) < 4 * sd / math.sqrt(len(dep)), (dep.mean(), mean)
 
 
+def _box_hit_fraction(E, d, box, mu_s, slab_t, n_c=1000, n_phi=1000, n_depth=4):
+    """Klein-Nishina-weighted fraction of single scatterings of a beam along d
+    (through the origin; scattering points weighted exp(-mu_s s) along its path
+    through the slab z in [0, slab_t]) whose ray hits the box, and the mean
+    E' of those: midpoint quadrature over cos(theta), azimuth and depth, with
+    the test's own frame and ray-box slab test."""
+    k = E / MEC2
+    d = np.asarray(d, float)
+    e1 = np.cross(d, [0.0, 0.0, 1.0])
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(d, e1)
+    c = -1 + (np.arange(n_c) + 0.5) * 2 / n_c
+    w = kn_textbook(k, c)
+    phi = (np.arange(n_phi) + 0.5) * 2 * math.pi / n_phi
+    sn = np.sqrt(1 - c * c)
+    n = c[:, None, None] * d + sn[:, None, None] * (np.cos(phi)[None, :, None] * e1 +
+                                                   np.sin(phi)[None, :, None] * e2)
+    lo, hi = np.array(box[:3], float), np.array(box[3:], float)
+    path = slab_t / d[2]
+    hits = e_sum = total = 0.0
+    for j in range(n_depth):
+        sd = (j + 0.5) / n_depth * path
+        wd = math.exp(-mu_s * sd)
+        p = d * sd
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t1, t2 = (lo - p) / n, (hi - p) / n
+        t_in = np.nanmax(np.minimum(t1, t2), axis=-1)
+        t_out = np.nanmin(np.maximum(t1, t2), axis=-1)
+        h = (w[:, None] * (t_out >= np.maximum(t_in, 0.0))).sum(axis=1)
+        hits += wd * h.sum()
+        e_sum += wd * (h * E / (1 + k * (1 - c))).sum()
+        total += wd * w.sum() * n_phi
+    return hits / total, e_sum / hits
+
+
+def test_compton_direction_into_a_finite_catcher(orc):
+    """The full scattered direction, not only its hemisphere: the tilted beam
+    of the test above (alpha = 1, with a y component) scatters once in the thin
+    slab, and a black, active 40 mm cube off the beam's plane, 30-70 mm below
+    the slab, catches the photons whose rays meet it.  The fraction that
+    deposits and their mean energy match the Klein-Nishina quadrature over
+    the directions that hit the cube (about 2.5 % of the scatterings)."""
+    E = 662.0
+    n_grid = 200_000
+    Eg = np.exp(np.linspace(math.log(10.0), math.log(3000.0), n_grid))
+    j = int(np.searchsorted(Eg, E)) - 1
+    mu = np.zeros((3, 3, n_grid), np.float32)
+    mu[1, 1, j:] = 0.1
+    mu[2, 0, :] = 1e3
+    t = orc.Tables.from_array(mu)
+    box = (-40.0, 20.0, -70.0, 0.0, 60.0, -30.0)
+    m = slab_mesh(orc, [(-50, -50, 0.0, 50, 50, 0.1), box], [1, 2], [0, 1])
+    alpha, beta = 1.0, 0.7
+    d = (math.sin(alpha) * math.cos(beta), math.sin(alpha) * math.sin(beta), math.cos(alpha))
+    src = orc.Source(kind=W.SRC_PENCIL, pos=(-d[0] / d[2], -d[1] / d[2], -1.0), dir=d)
+    r = orc.transport(m, t, src, E, 10_000_000, want_edep=True)
+    T = r.tally
+    assert T["n_err"] == 0 and T["n_first_pe"] == 0
+    n_c = T["n_first_compton"]
+    F, mean = _box_hit_fraction(E, d, box, 0.1, 0.1)
+    dep = r.edep[r.edep > 0]
+    f = len(dep) / n_c
+    assert abs(f - F) < 4 * math.sqrt(F * (1 - F) / n_c), (f, F)
+    assert abs(dep.mean() - mean) < 4 * dep.std() / math.sqrt(len(dep)), (dep.mean(), mean)
+
+
+def test_dos_gradient_interaction_term(orc):
+    """The interaction part of the density-perturbation score: an active slab
+    that only photoabsorbs (group 0, mu x = 0.6), so every interacting photon
+    is in the full-energy peak and FEPE(s) = 1 - exp(-s mu x); hence
+    dFEPE/ds = mu x exp(-s mu x), carried entirely by the score 1/s - mu d of
+    the absorbing step."""
+    x, mu0 = 2.0, 0.3
+    mu = np.zeros((2, 3, 1000), np.float32)
+    mu[1, 0, :] = mu0
+    t = orc.Tables.from_array(mu)
+    m = slab_mesh(orc, [(-50, -50, -x, 50, 50, 0.0)], [1], [1], groups=[0])
+    src = orc.Source(kind=W.SRC_PENCIL, pos=(0, 0, 5.0), dir=(0, 0, -1.0))
+    for s_ in (1.0, 1.5):
+        r = orc.transport(m, t, src, 662.0, 400_000, group_scale=(s_,))
+        fe = 1 - math.exp(-s_ * mu0 * x)
+        assert abs(r.fepe - fe) < 4 * math.sqrt(fe * (1 - fe) / 400_000)
+        expect = mu0 * x * math.exp(-s_ * mu0 * x)
+        assert abs(r.dfepe(0) - expect) < 4 * r.dfepe_sigma(0), (s_, r.dfepe(0), expect)
+
+
 def test_pair_production_deposits(orc):
     """Pair-only above threshold, black absorber below 600 keV: every interacting
     1332 keV photon deposits E - 2 mc^2 and both 511 keV photons are absorbed."""
@@ -261,6 +372,13 @@ def test_point_and_pencil_sources(orc):
     octant = (D[:, 0] > 0) * 4 + (D[:, 1] > 0) * 2 + (D[:, 2] > 0)
     counts = np.bincount(octant, minlength=8)
     assert np.all(np.abs(counts - N / 8) < 5 * math.sqrt(N / 8 * 7 / 8))
+    # transport draws from the pinned stream layout: a point source takes words
+    # 0 and 1 of history (seed, hid, inst) as cos(theta) = 2 u - 1, phi = 2 pi u
+    for seed, hid, inst in ((5, 0, 0), (0x1122334455667788, 0x0000000A00000003, 7), (1, 2 ** 40 + 5, 3)):
+        w = orc.stream_words(seed, hid, inst, 2)
+        d = orc.sample_birth(pt, seed, hid, inst)[1]
+        assert d[2] == 2.0 * orc.u01(w[0]) - 1.0
+        assert math.atan2(d[1], d[0]) % (2 * math.pi) == pytest.approx(2 * math.pi * orc.u01(w[1]), abs=1e-12)
     u = np.array([1.0, 2.0, -2.0]) / 3.0
     pen = orc.Source(kind=W.SRC_PENCIL, pos=(0.5, 0.25, -7.0), dir=tuple(u))
     for h in (0, 1, 77, 123456):
