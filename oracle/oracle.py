@@ -247,6 +247,13 @@ class Tables:
         return np.ctypeslib.as_array(self._p.contents.mu, shape=(n,)).reshape(
             self.n_mat, 3, self.n_grid).copy()
 
+    def set_mu(self, mu):
+        """Replace the photon table in place (same [n_mat][3][n_grid] shape), keeping
+        the charged-particle ranges of tables built from material codes."""
+        a = np.ascontiguousarray(mu, dtype=np.float32)
+        assert a.shape == (self.n_mat, 3, self.n_grid)
+        C.memmove(self._p.contents.mu, a.ctypes.data, a.nbytes)
+
     def eval(self, m, E):
         out = (C.c_double * 3)()
         lib().orc_tables_eval(self._p, m, E, out)

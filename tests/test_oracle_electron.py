@@ -164,3 +164,51 @@ def test_transport_invariants_with_tracks(orc, tab, coax):
         assert r1.tally["sum_dep_all"] + r1.tally["sum_esc"] == pytest.approx(20000 * E, rel=1e-12)
     with pytest.raises(ValueError):
         orc.transport(coax, orc.Tables.from_array(tab.array()), src, 662.0, 10, e_model=1)
+
+
+def test_compton_electron_direction_in_a_thin_slab(orc):
+    """The recoil electron of a Compton scattering runs along E d - E' d'
+    (momentum conservation), at cos(phi_e) = (E - E' c) / |E d - E' d'| to the
+    photon: a pencil beam along +z enters a 0.3 mm active Ge slab whose photon
+    table is Compton-only just at E (so the photon scatters once and leaves);
+    the electron of T = E - E' born at depth z0 runs forward and, if its range
+    allows, leaves through the top face after L = (h - z0) / cos(phi_e) with
+    T'(T, L) (the range functions pinned above).  The mean active deposit per
+    scattering matches the Klein-Nishina quadrature over cos(theta) and depth."""
+    E, h, mu_c = 662.0, 0.3, 0.05
+    k = E / 510.99895
+    n_grid = 200_000
+    t = orc.Tables.build(W.MATERIAL_CODES, n_grid)
+    Eg = np.exp(np.linspace(math.log(10.0), math.log(3000.0), n_grid))
+    j = int(np.searchsorted(Eg, E)) - 1
+    mu = np.zeros((len(W.MATERIAL_CODES), 3, n_grid), np.float32)
+    mu[GE, 1, j:] = mu_c
+    t.set_mu(mu)
+    xyz, tri, ts = W.box_mesh([(-50, -50, 0.0, 50, 50, h)])
+    m = orc.Mesh.from_arrays(xyz, tri, ts, [GE], [1], [-1], [-1])
+    src = orc.Source(kind=W.SRC_PENCIL, pos=(0, 0, -1.0), dir=(0, 0, 1.0))
+    r = orc.transport(m, t, src, E, 2_000_000, want_edep=True, e_model=1)
+    T_ = r.tally
+    assert T_["n_err"] == 0 and T_["n_first_pe"] == 0
+    dep = r.edep[r.edep > 0]
+    assert len(dep) == T_["n_first_compton"] > 20_000
+    # quadrature: midpoints in cos(theta) (Klein-Nishina weight) and depth (exp(-mu z0))
+    nc, nz = 1000, 40
+    c = -1 + (np.arange(nc) + 0.5) * 2 / nc
+    P = 1 / (1 + k * (1 - c))
+    w = P * P * (P + 1 / P - (1 - c * c))
+    Ep = E * P
+    Te = E - Ep
+    cos_e = (E - Ep * c) / np.sqrt(E * E + Ep * Ep - 2 * E * Ep * c)
+    z0 = (np.arange(nz) + 0.5) * h / nz
+    wz = np.exp(-mu_c * z0)
+    mean_c = np.empty(nc)
+    for i in range(nc):
+        if Te[i] < orc.E_TMIN:
+            mean_c[i] = Te[i]
+            continue
+        d_i = [Te[i] - t.e_energy_after(GE, Te[i], (h - z) / cos_e[i]) for z in z0]
+        mean_c[i] = np.dot(wz, d_i) / wz.sum()
+    expect = np.dot(w, mean_c) / w.sum()
+    assert abs(dep.mean() - expect) < 4 * dep.std() / math.sqrt(len(dep)) + 1e-4 * expect, (dep.mean(), expect)
+    assert 0.2 * (E - E / (1 + k)) < expect < E - E / (1 + 2 * k)    # a real fraction escapes

@@ -83,6 +83,8 @@ MUTANTS = [
      "*edep += weight * (T - T2);",
      ("test_oracle_electron", "test_track_from_active_volume_into_dead_layer"),
      lambda o: {"tab": _tab(o), "coax": _mesh(o, W.COAX_P)}),
+    ("compton_electron_momentum_sign", "orc_transport.c", "E * eu[2] - Ep * dir[2]", "E * eu[2] + Ep * dir[2]",
+     ("test_oracle_electron", "test_compton_electron_direction_in_a_thin_slab"), None),
     # sampling
     ("kahn_branch_probability", "orc_transport.c", "(1.0 + 2.0 * k) / (9.0 + 2.0 * k)",
      "(1.0 + 2.0 * k) / (8.0 + 2.0 * k)",
