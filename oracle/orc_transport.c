@@ -215,7 +215,7 @@ static int collect_hits(const scene_t *s, const double *o, const double *d, hit_
         }
     }
     hit_t *h = *buf;
-    qsort(h, (size_t)n, sizeof(hit_t), cmp_hit);
+    if (n > 1) qsort(h, (size_t)n, sizeof(hit_t), cmp_hit);     /* h is NULL before the first hit */
     int w = 0;
     for (int i = 0; i < n; ++i) {
         int dup = 0;
