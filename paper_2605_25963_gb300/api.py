@@ -37,20 +37,38 @@ def _ptr(a, ctype):
 
 # ---------------- DetMesh ----------------
 
-class Mesh:
-    """Triangulated detector surfaces (library-owned handle)."""
+class _Handle:
+    """Owner of one library handle, released by close(), at the end of a
+    with-block, or when the object is collected.  The destroy function is bound
+    at construction, so release needs no module globals (interpreter exit)."""
+    _destroy_name = ""
 
     def __init__(self, handle):
+        self._destroy = getattr(capi.load(), self._destroy_name)
         self._h = handle
 
+    def close(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h:
+            self._destroy(h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
     def __del__(self):
-        if getattr(self, "_h", None):
-            capi.load().detmesh_destroy(self._h)
-            self._h = None
+        self.close()
 
     @property
     def handle(self):
         return self._h
+
+
+class Mesh(_Handle):
+    """Triangulated detector surfaces (library-owned handle)."""
+    _destroy_name = "detmesh_destroy"
 
     def arrays(self):
         L = capi.load()
@@ -153,18 +171,9 @@ class Materials:
 
 # ---------------- BVH ----------------
 
-class Bvh:
-    def __init__(self, handle):
-        self._h = handle
-
-    def __del__(self):
-        if getattr(self, "_h", None):
-            capi.load().gadep_bvh_destroy(self._h)
-            self._h = None
-
-    @property
-    def handle(self):
-        return self._h
+class Bvh(_Handle):
+    """BVH of a mesh on one device (library-owned handle)."""
+    _destroy_name = "gadep_bvh_destroy"
 
     def stats(self):
         s = capi.gadep_bvh_stats()
@@ -352,10 +361,12 @@ def gadep_count_work(bvh: Bvh, mat: Materials, instances, opts=None, stream=None
     return [result_dict(r) for r in res], nodes.value, tris.value, reloc.value
 
 
-class Plan:
+class Plan(_Handle):
     """Device-resident batched run: create once, launch repeatedly (graph-capturable)."""
+    _destroy_name = "gadep_plan_destroy"
 
     def __init__(self, bvh: Bvh, mat: Materials, instances, opts=None, grad=False):
+        super().__init__(None)
         self._keep = (bvh, mat, instances)
         self.opts = opts if opts is not None else make_opts()
         self.n_inst = len(instances)
@@ -364,11 +375,6 @@ class Plan:
         check(capi.load().gadep_plan_create(bvh.handle, C.byref(mat.c), self.n_inst, instances,
                                             C.byref(self.opts), 1 if grad else 0, C.byref(h)))
         self._h = h
-
-    def __del__(self):
-        if getattr(self, "_h", None):
-            capi.load().gadep_plan_destroy(self._h)
-            self._h = None
 
     def shape(self):
         g, b, s = C.c_int32(), C.c_int32(), C.c_int32()

@@ -240,3 +240,18 @@ def test_struct_layouts_match_header(tmp_path):
         assert C.sizeof(cls) == got[(name, "size")], name
         for field, _ in cls._fields_:
             assert getattr(cls, field).offset == got[(name, field)], (name, field)
+
+
+def test_handles_release_once():
+    """close() releases a handle once; a with-block closes it; later closes and
+    collection do nothing."""
+    with api.detmesh_build(W.BARE_CYLINDER) as m:
+        assert m.handle
+        b = api.gadep_bvh_build(m, -1)
+        assert b.stats()["n_tri"] == 192
+        b.close()
+        assert b.handle is None
+        b.close()
+    assert m.handle is None
+    m.close()
+    del m, b
