@@ -315,6 +315,34 @@ def test_pair_production_deposits(orc):
     assert r2.tally["sum_esc"] == pytest.approx(5_000 * 2 * MEC2, rel=1e-12)
 
 
+def _peak_excess(spec, E, n_bins=4096, e_max=3000.0):
+    """Counts in the bin of energy E above the mean of the bins 3-12 away on both
+    sides, in units of that mean's Poisson sigma."""
+    b = int(E * n_bins / e_max)
+    side = np.r_[spec[b - 12:b - 2], spec[b + 3:b + 13]].astype(float)
+    mu = side.mean()
+    return (spec[b] - mu) / math.sqrt(max(mu, 1.0))
+
+
+def test_escape_peaks_in_the_coax_spectrum(orc):
+    """Pair production in the coax at 1332 keV leaves single- and double-escape
+    peaks at E - 511 and E - 1022 keV in the pulse-height spectrum (one or both
+    annihilation photons leave the crystal); at 662 keV, below the threshold,
+    there is none at E - 511.  A pencil beam parallel to the axis at r = 15 mm
+    (between the bore and the crystal's side) crosses the whole crystal length."""
+    m = orc.Mesh.build(orc.Det(**W.COAX_P.as_dict()))
+    t = orc.Tables.build(W.MATERIAL_CODES)
+    src = orc.Source(kind=W.SRC_PENCIL, pos=(15.0, 0, 25.0), dir=(0, 0, -1.0))
+    r = orc.transport(m, t, src, 1332.0, 300_000)
+    assert r.tally["n_first_pair"] > 0 and r.tally["n_err"] == 0
+    assert _peak_excess(r.spectrum, 1332.0 - MEC2) > 5
+    assert _peak_excess(r.spectrum, 1332.0 - 2 * MEC2) > 5
+    assert abs(_peak_excess(r.spectrum, 1000.0)) < 4              # no peak where none belongs
+    r6 = orc.transport(m, t, src, 662.0, 100_000)
+    assert r6.tally["n_first_pair"] == 0
+    assert _peak_excess(r6.spectrum, 662.0 - MEC2) < 4
+
+
 @pytest.mark.parametrize("E", [59.5, 1332.0])
 def test_coax_energy_conservation_and_parity(orc, E):
     m = orc.Mesh.build(orc.Det(**W.GRAD_DET.as_dict()))
