@@ -134,6 +134,22 @@ MUTANTS = [
     # mesh generation
     ("side_quad_winding", "orc_mesh.c", "add_tri(b, A1, B0, B1, solid);", "add_tri(b, A1, B1, B0, solid);",
      ("test_oracle_mesh", "test_bare_cylinder_counts_volume_topology"), None),
+    ("active_volume_grows", "orc_mesh.c", "add_rounded_g(&b, 4, D[1] - D[3], rch_a,",
+     "add_rounded_g(&b, 4, D[1] + D[3], rch_a,",
+     ("test_oracle_mesh", "test_coax_solids"), None),
+    ("active_rounding_not_shrunk", "orc_mesh.c", "double rch_a = D[2] - D[3] > 0.0 ? D[2] - D[3] : 0.0;",
+     "double rch_a = D[2];",
+     ("test_oracle_mesh", "test_coax_solids"), None),
+    ("bore_vacuum_not_separated", "orc_mesh.c", "z_back + 3.0 * sep, N, nphi, 1);", "z_back + 2.0 * sep, N, nphi, 1);",
+     ("test_oracle_mesh", "test_coax_solids"), None),
+    ("bore_contact_parent", "orc_mesh.c", "set_solid(m, 5, ORC_MAT_GE, 0, -1, 4);",
+     "set_solid(m, 5, ORC_MAT_GE, 0, -1, 3);",
+     ("test_oracle_transport", "test_coax_energy_conservation_and_parity"), lambda o: {"E": 1332.0}),
+    ("active_flag_dropped", "orc_mesh.c", "set_solid(m, 4, ORC_MAT_GE, 1, 2, 3);", "set_solid(m, 4, ORC_MAT_GE, 0, 2, 3);",
+     ("test_oracle_mesh", "test_coax_solids"), None),
+    ("rounding_z_sign", "orc_mesh.c", "double zz = z_front - rch * (1.0 - sin(phi));",
+     "double zz = z_front - rch * (1.0 - cos(phi));",
+     ("test_oracle_mesh", "test_coax_solids"), None),
     ("ring_angle_half_step", "orc_mesh.c",
      "double th = 2.0 * ORC_PI * (double)i / (double)N;\n                add_vertex(b, rho[k]",
      "double th = 2.0 * ORC_PI * ((double)i + 0.5) / (double)N;\n                add_vertex(b, rho[k]",
