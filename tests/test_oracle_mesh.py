@@ -234,3 +234,19 @@ def test_stress_groove_and_flange(orc, name):
             n = np.array(dd, dtype=float)
             n /= np.linalg.norm(n)
             assert m.locate(p, n) == want, (p, dd)
+
+
+def test_detector2_triangle_counts_in_the_paper_range(orc):
+    """Sec. 3.3 prints the triangle count of detector #2 at two mesh densities:
+    4416 at (N_theta, N_phi) = (32, 10) and 13440 at (64, 20).  The paper does not
+    list the components behind them, so they bound a sanity range, not an exact
+    value: ours (endcap, holder cup, crystal, active volume, bore contact and
+    bore vacuum) are within 30 % of both and grow by a similar factor."""
+    import dataclasses
+    counts = []
+    for (nt, nphi), paper in (((32, 10), 4416), ((64, 20), 13440)):
+        m = det(orc, dataclasses.replace(W.DET2, n_theta=nt, n_phi=nphi))
+        counts.append(m.n_tri)
+        assert 0.7 * paper <= m.n_tri <= 1.3 * paper, (nt, nphi, m.n_tri, paper)
+    assert counts == [3456, 12032]
+    assert 0.7 * 13440 / 4416 <= counts[1] / counts[0] <= 1.3 * 13440 / 4416
