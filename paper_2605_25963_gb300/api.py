@@ -8,7 +8,6 @@ buffers and the current CUDA stream.
 from __future__ import annotations
 
 import ctypes as C
-from dataclasses import dataclass
 
 import numpy as np
 

@@ -27,7 +27,7 @@ closed-form synthetic cross sections instead of evaluated data):
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 

@@ -8,7 +8,6 @@
   * invalid inputs fail with status codes, broken meshes with GADEP_E_MESH.
 """
 import ctypes as C
-import math
 import os
 import re
 
