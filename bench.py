@@ -341,22 +341,24 @@ def run_reference(args, cfg, rank, world):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="gadep", choices=["gadep", "reference"])
+    ap.add_argument("--gpus", type=int, default=1, help="GPUs, one process each (launch with torchrun when > 1)")
+    ap.add_argument("--steps", type=int, default=5, help="timed steps")
+    ap.add_argument("--warmup", type=int, default=3, help="untimed warm-up steps")
+    ap.add_argument("--impl", default="gadep", choices=["gadep", "reference"],
+                    help="gadep: the CUDA path; reference: the FP64 CPU oracle on a bounded sample")
     ap.add_argument("--workload", default="coax", choices=["coax", "bare", "table4", "stress"])
     ap.add_argument("--hist", type=int, default=0, help="histories per energy (default: the workload's)")
-    ap.add_argument("--block", type=int, default=0)
-    ap.add_argument("--chunk", type=int, default=0)
-    ap.add_argument("--variant", default="auto", choices=["auto", "mega", "wavefront"])
+    ap.add_argument("--block", type=int, default=0, help="threads per block (0: the library default)")
+    ap.add_argument("--chunk", type=int, default=0, help="histories a warp takes from the work counter at once (0: the library default)")
+    ap.add_argument("--variant", default="auto", choices=["auto", "mega", "wavefront"],
+                    help="transport form (auto: by the histories expected to reach the scene)")
     ap.add_argument("--e-model", type=int, default=0, choices=[0, 1],
                     help="charged particles: 0 deposit at the interaction point, 1 CSDA tracks")
     ap.add_argument("--bvh", default="", help="BVH build options, e.g. split_alpha=0,max_leaf=3 "
                                              "(max_leaf, c_trav, c_tri, split_alpha, max_dup)")
-    ap.add_argument("--wf-slots", type=int, default=0)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--wf-slots", type=int, default=0, help="wavefront photon slots (0: sized from the run)")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip timing the oracle on the host cores")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run through gadep_run with host buffers")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / gradient comparison")
     ap.add_argument("--forms-scale", type=float, default=1.0, help="history-count scale of the form runs")
     ap.add_argument("--mesh-sweep", action="store_true",
