@@ -346,7 +346,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3, help="untimed warm-up steps")
     ap.add_argument("--impl", default="gadep", choices=["gadep", "reference"],
                     help="gadep: the CUDA path; reference: the FP64 CPU oracle on a bounded sample")
-    ap.add_argument("--workload", default="coax", choices=["coax", "bare", "table4", "stress"])
+    ap.add_argument("--workload", default="coax", choices=["coax", "bare", "table4", "stress"],
+                    help="coax: the headline (4 energies x 1e8); bare: Ge cylinder; table4: detector #2, "
+                         "13 energies at 250 mm; stress: ~1e6-triangle mesh with a volume source")
     ap.add_argument("--hist", type=int, default=0, help="histories per energy (default: the workload's)")
     ap.add_argument("--block", type=int, default=0, help="threads per block (0: the library default)")
     ap.add_argument("--chunk", type=int, default=0, help="histories a warp takes from the work counter at once (0: the library default)")
