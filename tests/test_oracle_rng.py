@@ -41,6 +41,18 @@ def test_philox_matches_curand_host_generator(orc, seed):
         assert orc.philox(ctr, key) == list(blocks[b]), (seed, b)
 
 
+def test_philox_million_words_match_curand(orc):
+    """2^20 consecutive words of cuRAND's host generator (blocks 0 .. 2^18 - 1),
+    all of them: block b = r + 65536 j has counter (j, 0, r, 0), which is word
+    4j.. of the oracle's stream of history r * 2^32, instance 0."""
+    seed = 0x0123456789ABCDEF
+    blocks = _curand_host_words(seed, 4 * 262144)
+    for r in range(65536):
+        w = orc.stream_words(seed, r << 32, 0, 16).reshape(4, 4)
+        if not np.array_equal(w, blocks[r::65536]):
+            raise AssertionError("block %d + 65536 j differs" % r)
+
+
 def test_uniform_exact_and_open_interval(orc):
     for x in (0, 1, 511, 512, 0x7FFFFFFF, 0xFFFFFFFF):
         u = orc.u01(x)
