@@ -110,19 +110,22 @@ def test_black_absorber_solid_angle(orc):
 
 @pytest.mark.parametrize("E", [59.5, 662.0, 1332.0, 2900.0])
 def test_kahn_sampler_klein_nishina(orc, E):
+    """1e7 samples of cos(theta) per energy against the bin integrals of the
+    Klein-Nishina distribution; the four energies form one family of tests, so
+    each must reach p > 0.01 / 4 (Bonferroni)."""
     k = E / MEC2
-    n = 200_000
+    n = 10_000_000
     x = orc.kahn_samples(k, n, seed=5)
     assert np.all(x >= 1.0) and np.all(x <= 1 + 2 * k + 1e-12)
     c = 1 - (x - 1) / k
     edges = np.linspace(-1, 1, 41)
     obs, _ = np.histogram(c, bins=edges)
     tot = orc.sigma_kn(k)
-    p = np.array([integrate.quad(lambda cc: orc.dsigma_kn_dcos(k, cc), a, b)[0] / tot
+    p = np.array([integrate.quad(lambda cc: orc.dsigma_kn_dcos(k, cc), a, b, epsabs=0, epsrel=1e-12)[0] / tot
                   for a, b in zip(edges[:-1], edges[1:])])
     assert p.sum() == pytest.approx(1.0, rel=1e-9)
     chi = stats.chisquare(obs, p * n)
-    assert chi.pvalue > 0.001, chi
+    assert chi.pvalue > 0.01 / 4, chi
 
 
 def test_first_interaction_frequencies(orc):
@@ -130,13 +133,13 @@ def test_first_interaction_frequencies(orc):
     m = slab_mesh(orc, [(-1e4, -1e4, -1e4, 1e4, 1e4, 0.0)], [W.MAT_GE], [1])
     t = orc.Tables.build(W.MATERIAL_CODES)
     src = orc.Source(kind=W.SRC_PENCIL, pos=(0, 0, 1.0), dir=(0, 0, -1.0))
-    N = 300_000
+    N = 10_000_000
     r = orc.transport(m, t, src, E, N)
     mu = np.array(t.eval(W.MAT_GE, E))
     obs = [r.tally["n_first_pe"], r.tally["n_first_compton"], r.tally["n_first_pair"]]
     assert sum(obs) == N
     chi = stats.chisquare(obs, mu / mu.sum() * N)
-    assert chi.pvalue > 0.001, (obs, mu / mu.sum() * N)
+    assert chi.pvalue > 0.01, (obs, mu / mu.sum() * N)
 
 
 def kn_textbook(k, c):
