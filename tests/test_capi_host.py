@@ -76,6 +76,32 @@ def test_detmesh_locate_matches_oracle(orc):
         assert m.locate(p) == o.locate(p, (0.2672612, 0.5345225, 0.8017837)), p
 
 
+@pytest.mark.parametrize("name", ["GRAD_DET", "STRESS_SMALL"])
+def test_detmesh_locate_matches_oracle_near_surfaces(orc, name):
+    """The host parity rule that localises birth points, against the oracle's,
+    on both sides of 300 random triangles (0.003 and 0.2 mm along the normal,
+    past every 1e-4 mm separation and the 0.01 mm source gap) and inside the
+    0.3 um bore contact (1.5e-4 mm in from its side wall, midway to the bore
+    vacuum's aligned facets).  Every solid and the world are reached."""
+    d = getattr(W, name)
+    m, o = det_pair(orc, d)
+    xyz, tri, ts, _ = o.arrays()
+    v = xyz[tri]
+    nrm = np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0])
+    nrm /= np.linalg.norm(nrm, axis=1)[:, None]
+    cen = v.mean(1)
+    pick = np.random.default_rng(11).choice(len(tri), 300, replace=False)
+    pts = [cen[pick] + s * nrm[pick] for s in (0.003, -0.003, 0.2, -0.2)]
+    wall = np.where((ts == 5) & (np.abs(nrm[:, 2]) < 0.5))[0][::16]
+    pts.append(cen[wall] - 1.5e-4 * nrm[wall])
+    seen = set()
+    for p in np.concatenate(pts):
+        want = o.locate(tuple(p), (0.2672612, 0.5345225, 0.8017837))
+        assert m.locate(p) == want, p
+        seen.add(want)
+    assert len(wall) > 0 and seen == set(range(-1, o.n_solid))
+
+
 def test_electron_ranges_match_oracle(orc):
     """The library's CSDA range tables (Gauss-Legendre, FP32) against the oracle's
     independent ones (Simpson, FP64, pinned to ESTAR in test_oracle_electron)."""
