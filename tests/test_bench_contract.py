@@ -36,3 +36,25 @@ def test_reference_arm_other_ranks_do_nothing():
     r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_gpu_arm_fails_loudly_without_a_gpu():
+    """No CPU fallback: without a CUDA device the benchmark's GPU arm exits
+    non-zero and prints no result line, and the API raises."""
+    import torch
+    if torch.cuda.is_available():
+        return
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--steps", "1", "--warmup", "3"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0
+    assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+    from paper_2605_25963_gb300 import api, capi
+    from paper_2605_25963_gb300 import workloads as W
+    m = api.detmesh_build(W.BARE_CYLINDER)
+    try:
+        api.gadep_bvh_build(m, 0)
+    except capi.GadepError as e:
+        assert "no CUDA device" in str(e)
+    else:
+        raise AssertionError("gadep_bvh_build on device 0 succeeded without a GPU")
