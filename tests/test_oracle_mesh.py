@@ -250,3 +250,60 @@ def test_detector2_triangle_counts_in_the_paper_range(orc):
         assert 0.7 * paper <= m.n_tri <= 1.3 * paper, (nt, nphi, m.n_tri, paper)
     assert counts == [3456, 12032]
     assert 0.7 * 13440 / 4416 <= counts[1] / counts[0] <= 1.3 * 13440 / 4416
+
+
+def _prism_clip(o, d, N, R, z_lo, z_hi):
+    """Cyrus-Beck clipping of the line o + t d against the regular N-gon prism
+    (vertex i at angle 2 pi i / N, radius R) between z_lo and z_hi: (t_in, t_out)."""
+    apo = R * math.cos(math.pi / N)
+    planes = [(np.array([math.cos(2 * math.pi * (i + 0.5) / N), math.sin(2 * math.pi * (i + 0.5) / N), 0.0]), apo)
+              for i in range(N)]
+    planes += [(np.array([0.0, 0.0, 1.0]), z_hi), (np.array([0.0, 0.0, -1.0]), -z_lo)]
+    t_in, t_out = -math.inf, math.inf
+    for n, off in planes:
+        dn, num = n @ d, off - n @ o
+        if dn == 0.0:
+            if num < 0:
+                return math.inf, -math.inf
+            continue
+        t = num / dn
+        if dn < 0:
+            t_in = max(t_in, t)
+        else:
+            t_out = min(t_out, t)
+    return t_in, t_out
+
+
+def test_nearest_hit_against_prism_clipping(orc):
+    """The FP64 brute-force nearest hit (the reference of the GPU distance tests)
+    against the closed-form clipping of rays by the convex 48-gon prism of the
+    bare cylinder: from outside the first hit enters at t_in, from inside it
+    leaves at t_out; with t_min past t_in the next hit is the exit; the
+    excluded triangle is skipped."""
+    m = det(orc, W.BARE_CYLINDER)
+    N, R, L = 48, 30.0, 60.0
+    rng = np.random.default_rng(3)
+    n_in = n_out = 0
+    for _ in range(1500):
+        if rng.random() < 0.5:                       # outside, aimed at a point inside
+            u = rng.normal(size=3)
+            o = np.array([0.0, 0.0, -30.0]) + 120.0 * u / np.linalg.norm(u)
+            tgt = np.array([*(rng.uniform(-20, 20, 2)), rng.uniform(-55, -5)])
+            d = (tgt - o) / np.linalg.norm(tgt - o)
+        else:                                        # inside, any direction
+            o = np.array([*(rng.uniform(-20, 20, 2)), rng.uniform(-55, -5)])
+            d = rng.normal(size=3)
+            d /= np.linalg.norm(d)
+        t_in, t_out = _prism_clip(o, d, N, R, -L, 0.0)
+        k, t, ent = m.nearest_hit(tuple(o), tuple(d), 0.0, -1)
+        if t_in > 0:
+            n_out += 1
+            assert k >= 0 and ent == 1 and t == pytest.approx(t_in, rel=1e-12, abs=1e-12)
+            k2, t2, ent2 = m.nearest_hit(tuple(o), tuple(d), t_in + 1e-6, -1)
+            assert ent2 == 0 and t2 == pytest.approx(t_out, rel=1e-12, abs=1e-12)
+            k3, t3, _ = m.nearest_hit(tuple(o), tuple(d), 0.0, k)
+            assert k3 != k and t3 >= t - 1e-9
+        else:
+            n_in += 1
+            assert k >= 0 and ent == 0 and t == pytest.approx(t_out, rel=1e-12, abs=1e-12)
+    assert n_in > 500 and n_out > 500

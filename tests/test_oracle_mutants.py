@@ -128,6 +128,10 @@ MUTANTS = [
      ("test_oracle_transport", "test_black_absorber_solid_angle"), None),
     ("entering_sign", "orc_transport.c", "*entering = dn < 0;", "*entering = dn > 0;",
      ("test_oracle_transport", "test_coax_energy_conservation_and_parity"), lambda o: {"E": 59.5}),
+    ("nearest_hit_entering_inverted", "orc_transport.c", "*entering = be;", "*entering = !be;",
+     ("test_oracle_mesh", "test_nearest_hit_against_prism_clipping"), None),
+    ("nearest_hit_ignores_t_min", "orc_transport.c", "if (th > t_min && th < bt)", "if (th > 0.0 && th < bt)",
+     ("test_oracle_mesh", "test_nearest_hit_against_prism_clipping"), None),
     ("parity_any_crossing", "orc_transport.c", "if ((count[i] & 1) && first[i] < bt)",
      "if ((count[i] > 0) && first[i] < bt)",
      ("test_oracle_mesh", "test_parity_rule_locates_known_points"), None),
