@@ -307,3 +307,16 @@ def test_nearest_hit_against_prism_clipping(orc):
             n_in += 1
             assert k >= 0 and ent == 0 and t == pytest.approx(t_out, rel=1e-12, abs=1e-12)
     assert n_in > 500 and n_out > 500
+
+
+def test_open_edges_detects_holes_and_flips(orc):
+    """The closedness check is not vacuous: a box with one triangle removed has
+    its three edges unmatched; a box with one triangle flipped has directed
+    edges that repeat instead of reversing."""
+    xyz, tri, ts = W.box_mesh([(-1, -2, -3, 1, 2, 3)])
+    holed = orc.Mesh.from_arrays(xyz, tri[1:], ts[1:], [1], [1], [0], [-1])
+    assert holed.open_edges(0) == 3
+    flipped_tri = tri.copy()
+    flipped_tri[0] = flipped_tri[0][::-1]
+    flipped = orc.Mesh.from_arrays(xyz, flipped_tri, ts, [1], [1], [0], [-1])
+    assert flipped.open_edges(0) > 0

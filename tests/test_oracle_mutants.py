@@ -136,6 +136,9 @@ MUTANTS = [
      "if ((count[i] > 0) && first[i] < bt)",
      ("test_oracle_mesh", "test_parity_rule_locates_known_points"), None),
     # mesh generation
+    ("open_edges_always_zero", "orc_mesh.c", "    free(e);\n    return bad;\n}\n\nint orc_mesh_euler",
+     "    free(e);\n    return 0 * bad;\n}\n\nint orc_mesh_euler",
+     ("test_oracle_mesh", "test_open_edges_detects_holes_and_flips"), None),
     ("side_quad_winding", "orc_mesh.c", "add_tri(b, A1, B0, B1, solid);", "add_tri(b, A1, B1, B0, solid);",
      ("test_oracle_mesh", "test_bare_cylinder_counts_volume_topology"), None),
     ("active_volume_grows", "orc_mesh.c", "add_rounded_g(&b, 4, D[1] - D[3], rch_a,",
