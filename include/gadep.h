@@ -330,7 +330,10 @@ typedef struct {
     uint32_t dev_err;
 } gadep_result;
 
-/* One transport instance: n_hist histories of energy energy_keV from `src`,
+/* One transport instance (the GPU transport and host scoring of Fig. 4, Sec. 2.4;
+ * physics of Sec. 2.4.1 with the partial cross-section free flight, region
+ * identification of Sec. 2.4.2, BVH traversal of Sec. 2.4.3; FEPE and its sigma
+ * as the efficiencies of Sec. 3.2): n_hist histories of energy energy_keV from `src`,
  * history ids opts.history_offset + [0, n_hist), Philox instance id `instance`.
  * spectrum: n_bins uint32 counts, host or device (zeroed by the call).
  * edep_trace: optional device float [n_trace] receiving the active deposit of the
@@ -343,18 +346,22 @@ gadep_status gadep_run(const gadep_bvh *b, const gadep_materials *mat, const gad
 
 /* gadep_run without device allocation.  The paper has no counterpart: this entry
  * point exists for callers that cannot let a library allocate device memory while
- * they run -- work issued while a stream is being captured (cudaMalloc is not
- * permitted then), applications whose own allocator owns all device memory, and
- * loops that cannot take the device-wide synchronisation that cudaFree implies.
- * It computes the same histories as gadep_run with the same arguments (n_trace 0)
- * and returns the same result.
+ * they run -- applications whose own allocator (a framework's caching allocator,
+ * a memory pool sized at start-up) owns all device memory, and loops that cannot
+ * take the device-wide synchronisation that cudaFree implies.
+ * It runs the megakernel form (variant AUTO or MEGA; WAVEFRONT is refused with
+ * GADEP_E_INVAL, since that form's photon slots are allocated) and computes the
+ * same histories as gadep_run with the same arguments (n_trace 0) in that form;
+ * it returns the same result as gadep_run whenever gadep_run also runs the
+ * megakernel (variant MEGA, or AUTO below its wavefront threshold).
  * Scratch: instead of allocating, the call keeps the staged tables, region table,
  * instance record, tallies and work counter in one fixed device array of 345,472
  * bytes (337 KiB) that every GPU loading the library holds until the process exits.
  * Limits (GADEP_E_INVAL beyond them): at most 63 solids, and (materials with
  * non-zero tables used by the mesh) x n_grid <= 12288, n_grid <= 12288.
  * spectrum_dev: caller's device buffer of opts->n_bins uint32 (zeroed by the call);
- * result: host.  Synchronises `stream` before returning.
+ * result: host.  The call copies its inputs from host memory and synchronises
+ * `stream` before it returns.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
  * capture.  All calls share the one array and leave the last call's contents in
@@ -365,7 +372,9 @@ gadep_status gadep_run_noalloc(const gadep_bvh *b, const gadep_materials *mat, c
                                const gadep_opts *opts, uint32_t *spectrum_dev, gadep_result *result,
                                void *stream);
 
-/* Batched: n_inst instances, each with its own energy, source, history count,
+/* Batched (the paper runs one energy at a time, Sec. 3.2 / Table 3; here the
+ * instances of that loop share one launch, the transport of each being that of
+ * gadep_run: Fig. 4, Sec. 2.4, 2.4.1): n_inst instances, each with its own energy, source, history count,
  * Philox instance id and density scales, in one persistent launch drawing
  * histories from a device work counter.  spectra [n_inst][n_bins] host or device;
  * results [n_inst] host. */
@@ -381,7 +390,10 @@ gadep_status gadep_run_batch(const gadep_bvh *b, const gadep_materials *mat, int
                              const gadep_instance *inst, const gadep_opts *opts,
                              uint32_t *spectra, gadep_result *results, void *stream);
 
-/* Density-perturbation gradient: for each instance and group p,
+/* Density-perturbation gradient (no counterpart in the paper: the derivative of
+ * the FEPE of Sec. 3.2 with respect to the densities of the materials of Sec. 2.4.1,
+ * for the dead-layer characterisation the paper motivates in Sec. 1 and Sec. 4;
+ * the transport is gadep_run's): for each instance and group p,
  * dfepe[i][p] = d FEPE_i / d s_p = mean over histories of FEP * score_p with
  * score_p = (collisions in group p)/s_p - sum over segments in group p of
  * mu_unit(E) * length, accumulated on the fly (no stored tracks);

@@ -306,10 +306,12 @@ def gadep_run(bvh: Bvh, mat: Materials, src: W.Source, energy, n_hist, instance=
 def gadep_run_noalloc(bvh: Bvh, mat: Materials, src: W.Source, energy, n_hist, spectrum, instance=0, opts=None,
                       stream=None):
     """gadep_run for callers that cannot have the library allocate device memory
-    (stream capture, an application-owned allocator, no cudaFree syncs): scratch
-    lives in a fixed device array inside the library.  spectrum: the caller's
-    CUDA uint32/int32 tensor of n_bins counts.  Calls that overlap on the GPU race
-    on that array; the first call on a device should precede any stream capture."""
+    (an application-owned allocator holds the device memory, or a loop cannot take
+    cudaFree's device synchronisation): scratch lives in a fixed device array inside
+    the library.  Runs the megakernel form (a wavefront variant is refused).
+    spectrum: the caller's CUDA uint32/int32 tensor of n_bins counts.  The call
+    synchronises its stream.  Calls that overlap on the GPU race on that array;
+    the first call on a device should precede any stream capture."""
     o = opts if opts is not None else make_opts()
     s = make_source(src)
     r = capi.gadep_result()

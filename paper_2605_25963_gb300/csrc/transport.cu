@@ -1433,6 +1433,9 @@ extern "C" gadep_status gadep_run_noalloc(const gadep_bvh *b, const gadep_materi
     gadep_status st = check_opts(opts);
     if (st != GADEP_OK) return st;
     if (opts->e_model != 0) return fail(GADEP_E_INVAL, "gadep_run_noalloc: e_model 1 needs gadep_run");
+    if (opts->variant == GADEP_VARIANT_WAVEFRONT)
+        return fail(GADEP_E_INVAL, "gadep_run_noalloc: the wavefront form needs gadep_run (its photon slots are "
+                                   "allocated); this call runs the megakernel");
     if (n_hist >= (1ull << 32)) return fail(GADEP_E_INVAL, "gadep_run_noalloc: n_hist must be < 2^32");
     if (!(energy_keV > 0.0f) || !std::isfinite(energy_keV) || energy_keV > 1e5f)
         return fail(GADEP_E_INVAL, "gadep_run_noalloc: energy must be in (0, 1e5] keV");
@@ -1513,7 +1516,7 @@ extern "C" gadep_status gadep_run_noalloc(const gadep_bvh *b, const gadep_materi
     }
     const unsigned long long ends[2] = { n_hist, n_hist };
 
-    // launch shape (same kernel and shape rule as gadep_run)
+    // launch shape: the megakernel with gadep_run's megakernel shape rule
     const int block = opts->block ? opts->block : 256;
     const size_t smem = (size_t)n_region * sizeof(int4) + 8;
     int dev_smem = 0, n_sm = 0, bps = 0;
@@ -1584,6 +1587,7 @@ extern "C" gadep_status gadep_run_noalloc(const gadep_bvh *b, const gadep_materi
     std::memset(result, 0, sizeof(*result));
     result->n_hist = t.n_hist; result->n_fep = t.n_fep; result->n_zero = t.n_zero; result->n_over = t.n_over;
     result->n_err = t.n_err; result->n_segments = t.n_segments; result->n_interactions = t.n_interactions;
+    result->n_culled = t.n_culled;
     result->fepe = t.n_hist ? (double)t.n_fep / (double)t.n_hist : 0.0;
     result->sigma = t.n_hist ? std::sqrt(result->fepe * (1.0 - result->fepe) / (double)t.n_hist) : 0.0;
     result->sum_dep_active = t.sum_dep_active; result->sum_dep_all = t.sum_dep_all; result->sum_esc = t.sum_esc;
