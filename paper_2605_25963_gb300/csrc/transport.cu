@@ -1347,11 +1347,10 @@ extern "C" gadep_status gadep_count_work(const gadep_bvh *b, const gadep_materia
 // ---------------------------------------------------------------------------
 // Single-instance run without any device allocation (gadep_run_noalloc).
 //
-// For callers that must not allocate device memory during a run: code that
-// issues work while a stream is being captured (cudaMalloc is not allowed
-// then), applications that hand all device memory to their own allocator and
-// forbid libraries from taking more, and loops that cannot afford the device
-// synchronisation cudaFree implies.  Everything gadep_run keeps in allocated
+// For callers that must not allocate device memory during a run: applications
+// that hand all device memory to their own allocator and forbid libraries from
+// taking more, and loops that cannot afford the device synchronisation cudaFree
+// implies.  Everything gadep_run keeps in allocated
 // scratch -- the staged attenuation tables, the region table, the instance
 // record, the tallies and the work counter -- lives here in one file-scope
 // device array of fixed size, owned by every GPU that loads the library until
