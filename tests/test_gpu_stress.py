@@ -69,12 +69,15 @@ def test_stress_small_parity(orc, otab, mats, E):
 
 
 def test_stress_full_mesh_sampled_histories(orc, otab, mats):
-    """~1e6 triangles: the first histories of a GPU run, one by one, against the
-    oracle's brute force over every triangle (same Philox streams)."""
+    """~1e6 triangles: the first 5,000 histories of a GPU run at each of the eight
+    stress energies, one by one, against the oracle's brute force over every
+    triangle (same Philox streams).  40,000 histories in all, so a 0.1 % class of
+    disagreement would show."""
     m, b, om = scene(orc, "STRESS_DET")
     assert b.stats()["n_tri"] >= 1_000_000 or len(m.arrays()[1]) >= 1_000_000
-    n, n_check = 400_000, 240
-    for E in (W.STRESS_ENERGIES[1], W.STRESS_ENERGIES[6]):
+    n, n_check = 400_000, 5_000
+    agree = []
+    for E in W.STRESS_ENERGIES:
         trace = torch.empty(n, dtype=torch.float32, device="cuda")
         r, _ = api.gadep_run(b, mats, W.STRESS_SOURCE, E, n, edep_trace=trace)
         assert r["n_hist"] == n and r["n_err"] == 0 and r["dev_err"] == 0
@@ -82,8 +85,10 @@ def test_stress_full_mesh_sampled_histories(orc, otab, mats):
         assert ro.tally["n_err"] == 0 and ro.tally["n_parity_mismatch"] == 0
         g = trace.cpu().numpy()[:n_check].astype(np.float64)
         same = np.abs(g - ro.edep[:n_check]) <= 1e-3 + 1e-6 * np.abs(ro.edep[:n_check])
-        assert same.mean() >= 0.99, same.mean()
+        agree.append(same.mean())
+        assert same.mean() >= 0.997, (E, same.mean())
         assert r["sum_dep_all"] + r["sum_esc"] == pytest.approx(n * E, rel=1e-6)
+    assert np.mean(agree) >= 0.999, agree
 
 
 def test_stress_full_mesh_forms_agree(orc, mats):
