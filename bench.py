@@ -39,14 +39,15 @@ from paper_2605_25963_gb300 import workloads as W  # noqa: E402
 METRIC = "photon histories/s on 1 GB300, FEPE within 3σ of oracle; batched/grad vs plain"
 UNIT = "histories/s"
 # FP32 operations per traversal unit (counted from the kernel's arithmetic):
-# node visit = 12 slab FMAs (2 FLOP) + 12 min/max -> 36; triangle test = 9 vertex
-# translations + 6 shear FMAs (12) + 6 mul + 3 sub (edge functions) + 2 add (det)
-# + 3 mul + 2 FMA (T, 5) + 1 div + 2 compares -> ~45.
-FLOP_PER_NODE = 36.0
+# child box test = 6 slab FMAs (2 FLOP) + 6 min/max -> 18 (a 4-wide node visit
+# tests its 2..4 children); triangle test = 9 vertex translations + 6 shear FMAs
+# (12) + 6 mul + 3 sub (edge functions) + 2 add (det) + 3 mul + 2 FMA (T, 5) + 1 div
+# + 2 compares -> ~45.
+FLOP_PER_BOX = 18.0
 FLOP_PER_TRI = 45.0
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-NODE_BYTES, TRI_BYTES = 64, 48        # BVH node record; three float4 vertices of a triangle
+NODE_BYTES, TRI_BYTES = 128, 48       # 4-wide BVH node record; three float4 vertices of a triangle
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -357,7 +358,7 @@ def main():
     ap.add_argument("--e-model", type=int, default=0, choices=[0, 1],
                     help="charged particles: 0 deposit at the interaction point, 1 CSDA tracks")
     ap.add_argument("--bvh", default="", help="BVH build options, e.g. split_alpha=0,max_leaf=3 "
-                                             "(max_leaf, c_trav, c_tri, split_alpha, max_dup)")
+                                             "(max_leaf, c_trav, c_tri, split_alpha, max_dup, clip_ratio, clip_pieces)")
     ap.add_argument("--wf-slots", type=int, default=0, help="wavefront photon slots (0: sized from the run)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip timing the oracle on the host cores")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run through gadep_run with host buffers")
@@ -389,7 +390,7 @@ def main():
     bvh_kw = {}
     for item in filter(None, args.bvh.split(",")):
         k, v = item.split("=")
-        bvh_kw[k.strip()] = int(v) if k.strip() == "max_leaf" else float(v)
+        bvh_kw[k.strip()] = int(v) if k.strip() in ("max_leaf", "clip_pieces") else float(v)
     t0 = time.perf_counter()
     mesh = api.detmesh_build(cfg["det"])
     t_mesh = time.perf_counter() - t0
@@ -470,13 +471,14 @@ def main():
         f["E_keV"] = E
 
     # algorithmic work of one step (instrumented copy of the kernel, untimed)
-    nodes = tris = relocated = 0
+    nodes = tris = relocated = boxes = 0
     for i, E in enumerate(cfg["energies"]):
-        _, nv, nt, nr = api.gadep_count_work(bvh, mats, api.make_instances([(E, cfg["src"], n, i, [])]), opts)
+        _, nv, nt, nr, nb = api.gadep_count_work(bvh, mats, api.make_instances([(E, cfg["src"], n, i, [])]), opts)
         nodes += nv
         tris += nt
         relocated += nr
-    flops_per_step = FLOP_PER_NODE * nodes + FLOP_PER_TRI * tris
+        boxes += nb
+    flops_per_step = FLOP_PER_BOX * boxes + FLOP_PER_TRI * tris
     # launches and device time per kernel kind over the timed steps
     kstats = {}
     for p in plans:
@@ -500,7 +502,7 @@ def main():
     # nearest-hit queries: every segment but the one of a history that ends at birth
     # (born in the world aimed away from the scene box), which is counted without a query
     queries = segs - sum(f["culled"] for f in fepe)
-    # algorithmic node and triangle bytes of the traversal (64 B per node visit, 48 B per
+    # algorithmic node and triangle bytes of the traversal (128 B per node visit, 48 B per
     # triangle test), served by L1 and L2, per second of the dominant kernel
     l1l2_gbs = (NODE_BYTES * nodes + TRI_BYTES * tris) * args.steps / (dom_ms / 1e3) / 1e9
     # the timed plans hold the mesh's cached wavefront buffers; release them so the
@@ -575,7 +577,8 @@ def main():
                                              "frac_of_measured_l2": l1l2_gbs / l2_meas if l2_meas else None,
                                              "note": "library microbenchmarks: independent FMA chains on every "
                                                      "SM; 64 MB re-read from L2"},
-                         "per_query": {"nodes": nodes / max(queries, 1), "tris": tris / max(queries, 1),
+                         "per_query": {"nodes": nodes / max(queries, 1), "boxes": boxes / max(queries, 1),
+                                       "tris": tris / max(queries, 1),
                                        "relocated": relocated / max(queries, 1)},
                          "queries_per_step": queries, "segments_per_step": segs},
             "cpu_baseline": cb,

@@ -176,13 +176,22 @@ typedef struct gadep_bvh gadep_bvh;
  * a box as long as the wall.  On the coaxial detector meshes, though, spatial
  * splits trade triangle tests for more node visits and the transport runs
  * slower, so they are off by default; they stay available for meshes with
- * large triangles. */
+ * large triangles.
+ * clip_ratio > 0 turns on early split clipping (Ernst and Greiner 2007) before
+ * the build: a triangle whose bounding box, seen along its dominant normal axis,
+ * covers more than clip_ratio times its own projected area (a sliver at an angle
+ * to the axes, such as the centre-fan triangles of a flat end face) is stored as
+ * up to clip_pieces references, each bounding the part of the triangle in one
+ * half of the previous piece's box, so that each reference box fits its piece;
+ * each reference is a copy of the 48-byte record. */
 typedef struct {
     int32_t max_leaf;   /* 1..7 triangles per leaf at most; default 4 */
     float c_trav;       /* >= 0; default 1.5 */
     float c_tri;        /* > 0; default 1 */
     float split_alpha;  /* >= 0, 0 = no spatial splits; default 0 (1e-5 is the usual value when on) */
     float max_dup;      /* 1..16; default 2 */
+    float clip_ratio;   /* 0 = off, else >= 1: early split clipping of loose triangles (below) */
+    int32_t clip_pieces;/* 1..256 references per triangle at most; default 16 */
 } gadep_bvh_opts;
 void gadep_bvh_opts_default(gadep_bvh_opts *o);
 
@@ -450,16 +459,18 @@ gadep_status gadep_plan_set_timing(gadep_plan *p, int32_t on);
 gadep_status gadep_plan_kernel_stats(gadep_plan *p, gadep_kernel_stats *out, int32_t reset);
 
 /* Work counters of the traversal for one batch (same histories as gadep_run_batch):
- * BVH nodes visited and triangles tested, summed over all segment queries, and the
- * number of queries that found no surface in their region's tree and were
- * relocated through the tree of every triangle (photons a rounding error past a
- * boundary; `relocated` may be NULL).  Runs an instrumented copy of the transport
- * kernel; used to turn the measured time into algorithmic bytes and FLOPs per
- * query.  results: host [n_inst]. */
+ * 4-wide BVH nodes visited, child boxes tested in them (a node's empty slots not
+ * counted) and triangles tested, summed over all segment queries, and the number
+ * of queries that found no surface in their region's tree and were relocated
+ * through the tree of every triangle (photons a rounding error past a boundary).
+ * `relocated` and `boxes_tested` may be NULL.  Runs an instrumented copy of the
+ * transport kernels; used to turn the measured time into algorithmic bytes and
+ * FLOPs per query.  results: host [n_inst]. */
 gadep_status gadep_count_work(const gadep_bvh *b, const gadep_materials *mat, int32_t n_inst,
                               const gadep_instance *inst, const gadep_opts *opts,
                               gadep_result *results, uint64_t *nodes_visited,
-                              uint64_t *tris_tested, uint64_t *relocated, void *stream);
+                              uint64_t *tris_tested, uint64_t *relocated, uint64_t *boxes_tested,
+                              void *stream);
 
 /* Philox4x32-10 stream words of one history computed on the GPU (layout:
  * key = (seed lo, seed hi), counter = (block, hid lo, hid hi, instance)).

@@ -187,7 +187,7 @@ class Bvh(_Handle):
 
 def bvh_opts(**kw) -> "capi.gadep_bvh_opts":
     """gadep_bvh_opts with the library defaults, then the given fields
-    (max_leaf, c_trav, c_tri, split_alpha, max_dup)."""
+    (max_leaf, c_trav, c_tri, split_alpha, max_dup, clip_ratio, clip_pieces)."""
     o = capi.gadep_bvh_opts()
     capi.load().gadep_bvh_opts_default(C.byref(o))
     for k, v in kw.items():
@@ -351,15 +351,18 @@ def gadep_grad(bvh: Bvh, mat: Materials, instances, opts, spectra=None, stream=N
 
 
 def gadep_count_work(bvh: Bvh, mat: Materials, instances, opts=None, stream=None):
+    """Traversal work of a batch: (results, 4-wide nodes visited, triangles tested,
+    relocated queries, child boxes tested)."""
     o = opts if opts is not None else make_opts()
     n = len(instances)
     res = (capi.gadep_result * n)()
-    nodes, tris, reloc = C.c_uint64(), C.c_uint64(), C.c_uint64()
+    nodes, tris, reloc, boxes = C.c_uint64(), C.c_uint64(), C.c_uint64(), C.c_uint64()
     st = capi.load().gadep_count_work(bvh.handle, C.byref(mat.c), n, instances, C.byref(o), res,
-                                      C.byref(nodes), C.byref(tris), C.byref(reloc), _stream(stream))
+                                      C.byref(nodes), C.byref(tris), C.byref(reloc), C.byref(boxes),
+                                      _stream(stream))
     if st != capi.GADEP_E_DEVICE:
         check(st)
-    return [result_dict(r) for r in res], nodes.value, tris.value, reloc.value
+    return [result_dict(r) for r in res], nodes.value, tris.value, reloc.value, boxes.value
 
 
 class Plan(_Handle):

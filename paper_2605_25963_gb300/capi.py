@@ -55,7 +55,7 @@ class gadep_solid(C.Structure):
 
 class gadep_bvh_opts(C.Structure):
     _fields_ = [("max_leaf", C.c_int32), ("c_trav", C.c_float), ("c_tri", C.c_float), ("split_alpha", C.c_float),
-                ("max_dup", C.c_float)]
+                ("max_dup", C.c_float), ("clip_ratio", C.c_float), ("clip_pieces", C.c_int32)]
 
 
 class gadep_bvh_stats(C.Structure):
@@ -161,7 +161,8 @@ def load(build_if_missing: bool = True):
         "gadep_measure_peaks": (st, [C.c_int32, P(C.c_double), P(C.c_double)]),
         "gadep_plan_kernel_stats": (st, [vp, P(gadep_kernel_stats), C.c_int32]),
         "gadep_count_work": (st, [vp, P(gadep_materials), C.c_int32, P(gadep_instance), P(gadep_opts),
-                                  P(gadep_result), P(C.c_uint64), P(C.c_uint64), P(C.c_uint64), vp]),
+                                  P(gadep_result), P(C.c_uint64), P(C.c_uint64), P(C.c_uint64), P(C.c_uint64),
+                                  vp]),
         "gadep_philox_words": (st, [C.c_uint64, C.c_uint64, C.c_uint32, C.c_int32, vp, vp]),
         "gadep_run_noalloc": (st, [vp, P(gadep_materials), P(gadep_source), C.c_float, C.c_uint64, C.c_uint32,
                                    P(gadep_opts), vp, P(gadep_result), vp]),

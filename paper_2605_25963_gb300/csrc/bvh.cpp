@@ -9,10 +9,11 @@
 // Optionally (split_alpha > 0) spatial splits cut triangle references too.
 // The costs, the leaf limit and the split threshold are build options
 // (gadep_bvh_opts); C_trav = 1.5 C_tri measured fastest on the coaxial meshes.
-// The tree is then compacted into the 64-byte two-child node layout documented
-// in gadep_internal.h (both child boxes stored in the parent, depth-first order,
-// the left child of an inner node right after it) with the triangles reordered
-// so that every leaf is one contiguous run of 48-byte triangles.
+// The binary tree is then collapsed into the 128-byte 4-wide node layout
+// documented in gadep_internal.h (the four child boxes stored in the parent,
+// depth-first order) with the triangles reordered so that every leaf is one
+// contiguous run of 48-byte triangles.  A wide node halves the dependent node
+// steps of a query and gives each step four independent box tests.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -106,6 +107,115 @@ AABB clip_box(const double v[3][3], int k, double lo, double hi)
             b.hi[c] = std::max(b.hi[c], round_up(poly[i][c]));
         }
     return b;
+}
+
+// Part of triangle v inside the box [lo, hi] (Sutherland-Hodgman against its six
+// planes): up to 9 vertices in `poly`, returns the count (0 if none).
+int clip_to_box(const double v[3][3], const double lo[3], const double hi[3], double poly[9][3])
+{
+    double buf[2][9][3];
+    int n = 3;
+    std::memcpy(buf[0], v, sizeof(double) * 9);
+    int cur = 0;
+    for (int k = 0; k < 3 && n > 0; ++k)
+        for (int side = 0; side < 2 && n > 0; ++side) {
+            const double plane = side == 0 ? lo[k] : hi[k];
+            double(*in)[3] = buf[cur];
+            double(*out)[3] = buf[cur ^ 1];
+            int m = 0;
+            for (int i = 0; i < n; ++i) {
+                const double *p = in[i], *q = in[(i + 1) % n];
+                const double dp = side == 0 ? p[k] - plane : plane - p[k];
+                const double dq = side == 0 ? q[k] - plane : plane - q[k];
+                if (dp >= 0.0 && m < 9) std::memcpy(out[m++], p, sizeof(double) * 3);
+                if ((dp >= 0.0) != (dq >= 0.0) && m < 9) {
+                    const double t = dp / (dp - dq);
+                    for (int c = 0; c < 3; ++c) out[m][c] = p[c] + t * (q[c] - p[c]);
+                    out[m][k] = plane;
+                    ++m;
+                }
+            }
+            n = m;
+            cur ^= 1;
+        }
+    std::memcpy(poly, buf[cur], sizeof(double) * 3 * (size_t)n);
+    return n;
+}
+
+// Early split clipping (Ernst and Greiner 2007).  A sliver at an angle to the
+// axes -- the centre-fan triangles of a detector's flat end faces run from the
+// axis to the rim -- has a bounding box far larger than itself, and every such
+// box near the axis contains the axis: a ray crossing the face there would test
+// most of the fan.  Such a triangle is stored as several references instead,
+// each bounding the part of the triangle inside one half of the previous piece's
+// box (halved across its longest axis), until each piece is tight -- its box,
+// seen along the triangle's dominant normal axis, at most `ratio` times the
+// piece's own projected area -- or the triangle has `max_pieces` pieces.  The
+// pieces of a triangle cover it (boxes rounded outward), so the tree still finds
+// every hit; a query may meet the same triangle in two leaves, with the same
+// distance both times.
+void clip_loose(const double v[3][3], int32_t tri, float ratio, int max_pieces, std::vector<Ref> &out)
+{
+    const double e1[3] = { v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2] };
+    const double e2[3] = { v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2] };
+    const double nrm[3] = { e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0] };
+    const int kz = (std::fabs(nrm[0]) > std::fabs(nrm[1])) ? (std::fabs(nrm[0]) > std::fabs(nrm[2]) ? 0 : 2)
+                                                           : (std::fabs(nrm[1]) > std::fabs(nrm[2]) ? 1 : 2);
+    const int kx = (kz + 1) % 3, ky = (kz + 2) % 3;
+    struct Piece { double lo[3], hi[3]; AABB box; double looseness; };
+    // the part of the triangle in [lo, hi]: its outward-rounded box and how loose
+    // that box is around it (box area over polygon area, both projected along kz)
+    auto make = [&](const double lo[3], const double hi[3], Piece &pc) -> bool {
+        double poly[9][3];
+        const int n = clip_to_box(v, lo, hi, poly);
+        if (n < 3) return false;
+        std::memcpy(pc.lo, lo, sizeof(pc.lo));
+        std::memcpy(pc.hi, hi, sizeof(pc.hi));
+        double plo[3] = { INFINITY, INFINITY, INFINITY }, phi[3] = { -INFINITY, -INFINITY, -INFINITY };
+        double area2 = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const double *p = poly[i], *q = poly[(i + 1) % n];
+            area2 += p[kx] * q[ky] - q[kx] * p[ky];
+            for (int c = 0; c < 3; ++c) { plo[c] = std::min(plo[c], p[c]); phi[c] = std::max(phi[c], p[c]); }
+        }
+        for (int c = 0; c < 3; ++c) { pc.box.lo[c] = round_down(plo[c]); pc.box.hi[c] = round_up(phi[c]); }
+        const double box_area = (phi[kx] - plo[kx]) * (phi[ky] - plo[ky]);
+        const double a = 0.5 * std::fabs(area2);
+        pc.looseness = a > 0.0 ? box_area / a : (box_area > 0.0 ? INFINITY : 1.0);
+        return true;
+    };
+    std::vector<Piece> pieces(1);
+    double lo[3], hi[3];
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = std::min(v[0][c], std::min(v[1][c], v[2][c]));
+        hi[c] = std::max(v[0][c], std::max(v[1][c], v[2][c]));
+    }
+    if (!make(lo, hi, pieces[0])) return;
+    // split the loosest piece until all are tight or the budget is spent
+    while ((int)pieces.size() < max_pieces) {
+        size_t w = 0;
+        for (size_t i = 1; i < pieces.size(); ++i)
+            if (pieces[i].looseness > pieces[w].looseness) w = i;
+        if (!(pieces[w].looseness > ratio)) break;
+        const Piece p = pieces[w];
+        int ax = 0;
+        for (int c = 1; c < 3; ++c)
+            if (p.box.hi[c] - p.box.lo[c] > p.box.hi[ax] - p.box.lo[ax]) ax = c;
+        const double mid = 0.5 * ((double)p.box.lo[ax] + (double)p.box.hi[ax]);
+        double llo[3], lhi[3], rlo[3], rhi[3];
+        for (int c = 0; c < 3; ++c) {
+            llo[c] = rlo[c] = std::max(p.lo[c], (double)p.box.lo[c]);
+            lhi[c] = rhi[c] = std::min(p.hi[c], (double)p.box.hi[c]);
+        }
+        lhi[ax] = mid;
+        rlo[ax] = mid;
+        Piece a, b;
+        const bool ha = make(llo, lhi, a), hb = make(rlo, rhi, b);
+        if (!ha || !hb) { pieces[w].looseness = 0.0; continue; }   // a sliver of a piece: keep it whole
+        pieces[w] = a;
+        pieces.push_back(b);
+    }
+    for (const Piece &p : pieces) out.push_back(make_ref(p.box, tri));
 }
 
 struct Split {
@@ -291,9 +401,15 @@ struct Builder {
         bool make_leaf = (N <= max_leaf && leaf_cost <= best_cost) || N == 1 || depth >= kMaxDepth;
         if (make_leaf && N > max_leaf && depth < kMaxDepth) make_leaf = false;
         if (make_leaf) {
+            // pieces of one clipped triangle that meet in a leaf become one record
+            // (the leaf box already bounds all of them)
             nodes[id].start = (int32_t)leaf_refs.size();
-            nodes[id].count = N;
-            leaf_refs.insert(leaf_refs.end(), refs.begin(), refs.end());
+            for (const Ref &r : refs) {
+                bool dup = false;
+                for (size_t i = (size_t)nodes[id].start; i < leaf_refs.size() && !dup; ++i) dup = leaf_refs[i].tri == r.tri;
+                if (!dup) leaf_refs.push_back(r);
+            }
+            nodes[id].count = (int32_t)leaf_refs.size() - nodes[id].start;
             return id;
         }
         std::vector<Ref> L, R;
@@ -356,15 +472,22 @@ int32_t append_tree(const detmesh_mesh *m, const std::vector<int32_t> &ids, cons
     B.c_trav = o.c_trav;
     B.c_tri = o.c_tri;
     B.alpha = o.split_alpha;
-    B.n_refs = n_ids;
-    B.ref_budget = (int64_t)((double)o.max_dup * n_ids);
-    std::vector<Ref> refs(n_ids);
+    std::vector<Ref> refs;
+    refs.reserve(n_ids);
     for (int32_t i = 0; i < n_ids; ++i) {
-        AABB box;
         const int32_t t = ids[i];
+        if (o.clip_ratio > 0.0f && o.clip_pieces > 1) {
+            double v[3][3];
+            B.verts(t, v);
+            clip_loose(v, t, o.clip_ratio, o.clip_pieces, refs);
+            continue;
+        }
+        AABB box;
         for (int j = 0; j < 3; ++j) box.grow(&m->xyz_f[3 * g.tri[3 * t + j]]);
-        refs[i] = make_ref(box, t);
+        refs.push_back(make_ref(box, t));
     }
+    B.n_refs = (int64_t)refs.size();
+    B.ref_budget = (int64_t)((double)o.max_dup * (double)refs.size());
     B.nodes.reserve(2 * (size_t)n_ids / o.max_leaf + 8);
     B.build(refs, 0);
     if (B.max_depth >= kMaxDepth) {
@@ -379,7 +502,7 @@ int32_t append_tree(const detmesh_mesh *m, const std::vector<int32_t> &ids, cons
     ts.depth = std::max(ts.depth, B.max_depth);
     ts.refs += nt;
     const int32_t tri_base = (int32_t)(out->tris.size() / 12);
-    const int32_t node_base = (int32_t)(out->nodes.size() / 16);
+    const int32_t node_base = (int32_t)(out->nodes.size() / kNodeFloats);
     // triangles in leaf order: (v0, region), (v1, mesh triangle id), (v2, 0)
     for (int32_t i = 0; i < nt; ++i) {
         const int32_t t = B.leaf_refs[i].tri;
@@ -394,56 +517,80 @@ int32_t append_tree(const detmesh_mesh *m, const std::vector<int32_t> &ids, cons
         std::memcpy(&rec[7], &t, 4);
         out->tris.insert(out->tris.end(), rec, rec + 12);
     }
-    // compaction: one device node per inner build node (root always a device node)
+    // Collapse into 4-wide nodes: a wide node takes the two children of a binary
+    // node and opens its largest-area inner child (replacing it by that child's
+    // two children) until it holds four children or only leaves.  Wide nodes are
+    // stored depth-first; the root of the tree is always a wide node (a root that
+    // is a leaf becomes a wide node with one child).
+    auto collapse = [&](int32_t bnode, int32_t kids[4]) -> int {
+        const BNode &nb = B.nodes[bnode];
+        if (nb.leaf()) { kids[0] = bnode; return 1; }
+        int n = 0;
+        kids[n++] = nb.child[0];
+        kids[n++] = nb.child[1];
+        while (n < 4) {
+            int open = -1;
+            float open_area = -1.0f;
+            for (int i = 0; i < n; ++i) {
+                const BNode &c = B.nodes[kids[i]];
+                if (!c.leaf() && c.box.area() > open_area) { open_area = c.box.area(); open = i; }
+            }
+            if (open < 0) break;
+            const BNode &c = B.nodes[kids[open]];
+            kids[open] = c.child[0];
+            kids[n++] = c.child[1];
+        }
+        return n;
+    };
     std::vector<int32_t> dev_of(B.nodes.size(), -1);
-    std::vector<int32_t> order;   // build ids of device nodes, depth-first
+    std::vector<int32_t> order;   // build ids of the wide nodes, depth-first
     {
         std::vector<int32_t> stack{ 0 };
         while (!stack.empty()) {
-            int32_t b = stack.back();
+            const int32_t bn = stack.back();
             stack.pop_back();
-            dev_of[b] = node_base + (int32_t)order.size();
-            order.push_back(b);
-            const BNode &n = B.nodes[b];
-            if (n.leaf()) continue;
-            if (!B.nodes[n.child[1]].leaf()) stack.push_back(n.child[1]);
-            if (!B.nodes[n.child[0]].leaf()) stack.push_back(n.child[0]);
+            dev_of[bn] = node_base + (int32_t)order.size();
+            order.push_back(bn);
+            int32_t kids[4];
+            const int n = collapse(bn, kids);
+            for (int i = n - 1; i >= 0; --i)
+                if (kids[i] != bn && !B.nodes[kids[i]].leaf()) stack.push_back(kids[i]);
         }
     }
     const double root_area = std::max((double)B.nodes[0].box.area(), 1e-30);
-    for (size_t di = 0; di < order.size(); ++di) {
-        const BNode &n = B.nodes[order[di]];
-        float lo[2][3], hi[2][3];
-        int32_t child[2];
-        if (n.leaf()) {
-            // the root is a single leaf: slot 0 holds it, slot 1 is empty
-            pad_box(n.box, lo[0], hi[0]);
-            child[0] = leaf_ref(tri_base + n.start, n.count);
-            for (int k = 0; k < 3; ++k) { lo[1][k] = 1.0f; hi[1][k] = -1.0f; }
-            child[1] = leaf_ref(0, 0);
-            ts.leaves++; ts.max_leaf = std::max(ts.max_leaf, n.count);
-            ts.sah += n.box.area() / root_area * n.count * o.c_tri;
-        } else {
-            ts.sah += n.box.area() / root_area * o.c_trav;
-            for (int c = 0; c < 2; ++c) {
-                const BNode &ch = B.nodes[n.child[c]];
-                pad_box(ch.box, lo[c], hi[c]);
-                if (ch.leaf()) {
-                    child[c] = leaf_ref(tri_base + ch.start, ch.count);
-                    ts.leaves++; ts.max_leaf = std::max(ts.max_leaf, ch.count);
-                    ts.sah += ch.box.area() / root_area * ch.count * o.c_tri;
-                } else {
-                    child[c] = dev_of[n.child[c]];
-                }
+    for (const int32_t bn : order) {
+        int32_t kids[4];
+        const int n = collapse(bn, kids);
+        float f[kNodeFloats];
+        int32_t w[8] = { 0, 0, 0, 0, n, 0, 0, 0 };
+        ts.sah += B.nodes[bn].leaf() ? 0.0 : B.nodes[bn].box.area() / root_area * o.c_trav;
+        for (int c = 0; c < 4; ++c) {
+            if (c >= n) {
+                // empty slot: a box at +infinity on every axis, which the slab test of
+                // any ray misses (both planes of an axis give the same infinite
+                // distance), holding a leaf of no triangles
+                for (int k = 0; k < 6; ++k) f[4 * k + c] = INFINITY;
+                w[c] = leaf_ref(0, 0);
+                continue;
+            }
+            const BNode &ch = B.nodes[kids[c]];
+            float lo[3], hi[3];
+            pad_box(ch.box, lo, hi);
+            for (int k = 0; k < 3; ++k) {
+                f[8 * k + c] = lo[k];
+                f[8 * k + 4 + c] = hi[k];
+            }
+            if (ch.leaf()) {
+                w[c] = leaf_ref(tri_base + ch.start, ch.count);
+                ts.leaves++;
+                ts.max_leaf = std::max(ts.max_leaf, ch.count);
+                ts.sah += ch.box.area() / root_area * ch.count * o.c_tri;
+            } else {
+                w[c] = dev_of[kids[c]];
             }
         }
-        float f[16];
-        f[0] = lo[0][0]; f[1] = hi[0][0]; f[2] = lo[0][1]; f[3] = hi[0][1];
-        f[4] = lo[1][0]; f[5] = hi[1][0]; f[6] = lo[1][1]; f[7] = hi[1][1];
-        f[8] = lo[0][2]; f[9] = hi[0][2]; f[10] = lo[1][2]; f[11] = hi[1][2];
-        const int32_t w[4] = { child[0], child[1], 0, 0 };
-        std::memcpy(&f[12], w, 16);
-        out->nodes.insert(out->nodes.end(), f, f + 16);
+        std::memcpy(&f[24], w, 32);
+        out->nodes.insert(out->nodes.end(), f, f + kNodeFloats);
     }
     return node_base;
 }
@@ -472,9 +619,10 @@ gadep_status build_bvh_host(const detmesh_mesh *m, const gadep_bvh_opts &o, gade
     const int32_t nt = g.n_tri();
     if (nt >= (1 << 26)) return fail(GADEP_E_INVAL, "bvh: at most 2^26 triangles");
     if (o.max_leaf < 1 || o.max_leaf > 7 || !(o.c_trav >= 0.0f) || !(o.c_tri > 0.0f) || !(o.split_alpha >= 0.0f) ||
-        !(o.max_dup >= 1.0f) || !(o.max_dup <= 16.0f))
+        !(o.max_dup >= 1.0f) || !(o.max_dup <= 16.0f) || !(o.clip_ratio == 0.0f || o.clip_ratio >= 1.0f) ||
+        o.clip_pieces < 1 || o.clip_pieces > 256)
         return fail(GADEP_E_INVAL, "bvh: bad options (max_leaf 1..7, c_tri > 0, c_trav >= 0, split_alpha >= 0, "
-                                   "max_dup in [1, 16])");
+                                   "max_dup in [1, 16], clip_ratio 0 or >= 1, clip_pieces 1..256)");
     out->nodes.clear();
     out->tris.clear();
     out->tri_orig.clear();
@@ -523,14 +671,14 @@ gadep_status build_bvh_host(const detmesh_mesh *m, const gadep_bvh_opts &o, gade
     }
     out->geo = g;
     gadep_bvh_stats &stt = out->stats;
-    stt.n_nodes = (int32_t)(out->nodes.size() / 16);
+    stt.n_nodes = (int32_t)(out->nodes.size() / kNodeFloats);
     stt.n_leaves = all_ts.leaves + reg_ts.leaves;
     stt.max_depth = std::max(all_ts.depth, reg_ts.depth);
     stt.max_leaf_tris = std::max(all_ts.max_leaf, reg_ts.max_leaf);
     stt.n_tri = nt;
     stt.n_region = g.n_solid() + 1;
     stt.sah_cost = all_ts.sah;
-    stt.node_bytes = (int64_t)stt.n_nodes * 64;
+    stt.node_bytes = (int64_t)stt.n_nodes * kNodeFloats * 4;
     stt.tri_bytes = (int64_t)(out->tris.size() / 12) * 48;
     stt.n_refs = all_ts.refs + reg_ts.refs;
     stt.opts = o;
@@ -547,6 +695,8 @@ extern "C" void gadep_bvh_opts_default(gadep_bvh_opts *o)
     o->c_tri = 1.0f;
     o->split_alpha = 0.0f;
     o->max_dup = 2.0f;
+    o->clip_ratio = 0.0f;
+    o->clip_pieces = 16;
 }
 
 extern "C" gadep_status gadep_bvh_get_stats(const gadep_bvh *b, gadep_bvh_stats *out)
@@ -577,13 +727,19 @@ gadep_status walk_tree(const gadep_bvh *b, int32_t root, std::vector<LeafBox> &o
         stack.pop_back();
         if (it.node < 0 || it.node >= nn || ++visited > nn)
             return gadep::fail(GADEP_E_MESH, "bvh: bad node index %d", it.node);
-        const float *f = &b->nodes[(size_t)it.node * 16];
-        int32_t w[4];
-        std::memcpy(w, &f[12], 16);
-        for (int c = 0; c < 2; ++c) {
-            const float lo[3] = { f[4 * c + 0], f[4 * c + 2], f[8 + 2 * c] };
-            const float hi[3] = { f[4 * c + 1], f[4 * c + 3], f[9 + 2 * c] };
-            if (w[c] < 0 && ((~w[c]) & 7) == 0) continue;  // empty leaf slot
+        const float *f = &b->nodes[(size_t)it.node * kNodeFloats];
+        int32_t w[8];
+        std::memcpy(w, &f[24], 32);
+        if (w[4] < 1 || w[4] > 4) return gadep::fail(GADEP_E_MESH, "bvh: node %d has %d children", it.node, w[4]);
+        for (int c = 0; c < 4; ++c) {
+            const float lo[3] = { f[c], f[8 + c], f[16 + c] };
+            const float hi[3] = { f[4 + c], f[12 + c], f[20 + c] };
+            if (c >= w[4]) {
+                if (w[c] >= 0 || ((~w[c]) & 7) != 0 || lo[0] != INFINITY || hi[0] != INFINITY || lo[1] != INFINITY ||
+                    hi[1] != INFINITY || lo[2] != INFINITY || hi[2] != INFINITY)
+                    return gadep::fail(GADEP_E_MESH, "bvh: empty slot of node %d is not empty", it.node);
+                continue;
+            }
             for (int k = 0; k < 3; ++k)
                 if (lo[k] < it.lo[k] || hi[k] > it.hi[k] || lo[k] > hi[k])
                     return gadep::fail(GADEP_E_MESH, "bvh: child box of node %d not inside its parent", it.node);

@@ -9,7 +9,9 @@
 //                   decide the hit; products are never contracted into FMAs so a
 //                   shared edge gives exactly opposite values in its two
 //                   triangles, and exact zeros are re-evaluated in FP64.
-//   traverse        nearest hit in the two-child BVH with a per-thread stack
+//   node4_keys      the four box tests of a 4-wide BVH node, children hit sorted
+//                   nearest first
+//   traverse        nearest hit in the 4-wide BVH with a per-thread stack
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -219,7 +221,66 @@ __device__ __forceinline__ void leaf_test_k(const float4 *__restrict__ tris, int
     }
 }
 
-struct TravStats { uint32_t nodes, tris, relocated; };
+struct TravStats { uint32_t nodes, boxes, tris, relocated; };
+
+// Sort key of a child box met by the ray: its entry distance (non-negative, so
+// its bits order as unsigned integers) with the two low mantissa bits replaced
+// by the child's slot; kMiss for a box the ray does not meet.  Two distances
+// within 4 ulp may swap places, which only changes the visiting order.
+constexpr uint32_t kMiss = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t box_key(float lx, float hx, float ly, float hy, float lz, float hz, float ix,
+                                            float iy, float iz, float oix, float oiy, float oiz, float t_min,
+                                            float t_best, uint32_t slot)
+{
+    const float x0 = fmaf(lx, ix, -oix), x1 = fmaf(hx, ix, -oix);
+    const float y0 = fmaf(ly, iy, -oiy), y1 = fmaf(hy, iy, -oiy);
+    const float z0 = fmaf(lz, iz, -oiz), z1 = fmaf(hz, iz, -oiz);
+    const float tn = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), t_min));
+    const float tf = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), t_best));
+    return tn <= tf ? ((__float_as_uint(tn) & 0x7ffffffcu) | slot) : kMiss;
+}
+
+__device__ __forceinline__ void cswap(uint32_t &a, uint32_t &b)
+{
+    const uint32_t lo = min(a, b);
+    b = max(a, b);
+    a = lo;
+}
+
+// The four child boxes of wide node `node` against the ray (o, 1/d) restricted
+// to [t_min, t_best]: keys k[0..3] of the children hit, nearest first (kMiss
+// after the last), the node's child words and its number of children.
+__device__ __forceinline__ void node4_keys(const float4 *__restrict__ nodes, int node, float ix, float iy,
+                                           float iz, float oix, float oiy, float oiz, float t_min, float t_best,
+                                           uint32_t &k0, uint32_t &k1, uint32_t &k2, uint32_t &k3, int4 &child,
+                                           int &n_child)
+{
+    float4 lx, hx, ly, hy, lz, hz, cw, meta;
+    ldg256(nodes + 8 * node, lx, hx);
+    ldg256(nodes + 8 * node + 2, ly, hy);
+    ldg256(nodes + 8 * node + 4, lz, hz);
+    ldg256(nodes + 8 * node + 6, cw, meta);
+    child = make_int4(__float_as_int(cw.x), __float_as_int(cw.y), __float_as_int(cw.z), __float_as_int(cw.w));
+    n_child = __float_as_int(meta.x);
+    k0 = box_key(lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, ix, iy, iz, oix, oiy, oiz, t_min, t_best, 0u);
+    k1 = box_key(lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, ix, iy, iz, oix, oiy, oiz, t_min, t_best, 1u);
+    k2 = box_key(lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, ix, iy, iz, oix, oiy, oiz, t_min, t_best, 2u);
+    k3 = box_key(lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, ix, iy, iz, oix, oiy, oiz, t_min, t_best, 3u);
+    cswap(k0, k1);
+    cswap(k2, k3);
+    cswap(k0, k2);
+    cswap(k1, k3);
+    cswap(k1, k2);
+}
+
+// Child word of slot s (the low two bits of a key).
+__device__ __forceinline__ int child_of(const int4 &c, uint32_t key)
+{
+    const int a = (key & 1u) ? c.y : c.x;
+    const int b = (key & 1u) ? c.w : c.z;
+    return (key & 2u) ? b : a;
+}
 
 // Distance of the hit on mesh triangle m, taken from the triangle's plane (unit
 // normal and offset computed in FP64 from the stored vertices) once the
@@ -278,53 +339,51 @@ __device__ __forceinline__ int traverse(const float4 *__restrict__ nodes,
     float t_best = t_max;
     int best = -1;
     bool ent = false;
-    int stack[kStack];
-    stack[0] = kSentinel;
+    // stack entries: (child word, key of its box); an entry whose box is entered
+    // beyond the nearest hit found since it was pushed is dropped when popped
+    uint2 stack[kStack];
+    stack[0] = make_uint2((uint32_t)kSentinel, 0u);
     int sp = 0;
     int node = root;
     int leaf = 0;
-    uint32_t nn = 0, nt = 0;
+    uint32_t nn = 0, nb = 0, nt = 0;
+    auto pop = [&]() -> int {
+        uint2 e = stack[sp--];
+        while (__uint_as_float(e.y) > t_best) e = stack[sp--];
+        return (int)e.x;
+    };
     while (node != kSentinel) {
         while ((unsigned)node < (unsigned)kSentinel) {
-            float4 n0, n1, n2, n3f;
-            ldg256(nodes + 4 * node, n0, n1);
-            ldg256(nodes + 4 * node + 2, n2, n3f);
-            const int4 n3 = make_int4(__float_as_int(n3f.x), __float_as_int(n3f.y), 0, 0);
+            uint32_t k0, k1, k2, k3;
+            int4 cw;
+            int nch;
+            node4_keys(nodes, node, ix, iy, iz, oix, oiy, oiz, t_min, t_best, k0, k1, k2, k3, cw, nch);
             ++nn;
-            const float a0 = fmaf(n0.x, ix, -oix), a1 = fmaf(n0.y, ix, -oix);
-            const float a2 = fmaf(n0.z, iy, -oiy), a3 = fmaf(n0.w, iy, -oiy);
-            const float a4 = fmaf(n2.x, iz, -oiz), a5 = fmaf(n2.y, iz, -oiz);
-            const float b0 = fmaf(n1.x, ix, -oix), b1 = fmaf(n1.y, ix, -oix);
-            const float b2 = fmaf(n1.z, iy, -oiy), b3 = fmaf(n1.w, iy, -oiy);
-            const float b4 = fmaf(n2.z, iz, -oiz), b5 = fmaf(n2.w, iz, -oiz);
-            const float tmin0 = fmaxf(fmaxf(fminf(a0, a1), fminf(a2, a3)), fmaxf(fminf(a4, a5), t_min));
-            const float tmax0 = fminf(fminf(fmaxf(a0, a1), fmaxf(a2, a3)), fminf(fmaxf(a4, a5), t_best));
-            const float tmin1 = fmaxf(fmaxf(fminf(b0, b1), fminf(b2, b3)), fmaxf(fminf(b4, b5), t_min));
-            const float tmax1 = fminf(fminf(fmaxf(b0, b1), fmaxf(b2, b3)), fminf(fmaxf(b4, b5), t_best));
-            const bool h0 = tmin0 <= tmax0, h1 = tmin1 <= tmax1;
-            if (!h0 && !h1) {
-                node = stack[sp--];
+            nb += nch;
+            if (k0 == kMiss) {
+                node = pop();
             } else {
-                const bool first0 = h0 && (!h1 || tmin0 <= tmin1);
-                node = first0 ? n3.x : n3.y;
-                if (h0 && h1) {
-                    if (sp + 1 >= kStack) { err |= ERR_STACK; return -1; }
-                    stack[++sp] = first0 ? n3.y : n3.x;
+                node = child_of(cw, k0);
+                if (k1 != kMiss) {      // push the others, farthest first
+                    if (sp + 3 >= kStack) { err |= ERR_STACK; return -1; }
+                    if (k3 != kMiss) stack[++sp] = make_uint2((uint32_t)child_of(cw, k3), k3);
+                    if (k2 != kMiss) stack[++sp] = make_uint2((uint32_t)child_of(cw, k2), k2);
+                    stack[++sp] = make_uint2((uint32_t)child_of(cw, k1), k1);
                 }
             }
             if (node < 0 && leaf >= 0) {     // postpone this leaf, keep descending
                 leaf = node;
-                node = stack[sp--];
+                node = pop();
             }
             if (!__any_sync(__activemask(), leaf >= 0)) break;
         }
         while (leaf < 0) {
             leaf_test(tris, leaf, exclude, ox, oy, oz, sh, t_min, t_best, best, ent, nt);
             leaf = node;
-            if (node < 0) node = stack[sp--];
+            if (node < 0) node = pop();
         }
     }
-    if (COUNT) { st.nodes += nn; st.tris += nt; }
+    if (COUNT) { st.nodes += nn; st.boxes += nb; st.tris += nt; }
     if (best >= 0) {
         // direction back from its reciprocals, as the wavefront trace kernel does,
         // so that both forms take the same distance

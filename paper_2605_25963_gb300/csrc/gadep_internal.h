@@ -46,21 +46,26 @@ struct detmesh_mesh {
     std::vector<float> xyz_f;  // FP32 copy handed to the BVH and to callers
 };
 
-// Device-side compacted BVH.  Node = 4 x 16 bytes:
-//   f4[0] = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
-//   f4[1] = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
-//   f4[2] = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
-//   i4[3] = (child0, child1, 0, 0)
+// Device-side compacted BVH of 4-wide nodes.  Node = 8 x 16 bytes (128 B, one
+// L1 line), the boxes of the four children stored in the parent, one axis
+// bound per float4 so that the four box tests run side by side:
+//   f4[0] = lo.x of children 0..3      f4[1] = hi.x of children 0..3
+//   f4[2] = lo.y                       f4[3] = hi.y
+//   f4[4] = lo.z                       f4[5] = hi.z
+//   i4[6] = (child0, child1, child2, child3)
+//   i4[7] = (number of children 1..4, 0, 0, 0)
 // child >= 0: inner node index; child < 0: leaf ~(first << 3 | count) holding
-// triangles [first, first + count) (count 0 = empty slot, its box is inverted).
+// triangles [first, first + count).  Slots past the number of children are empty:
+// count 0 and a box at +infinity on every axis, which no ray's slab test meets.
 // Triangle = 3 x float4: (v0, region id bits), (v1, mesh triangle id bits), (v2, 0)
 // with region id = solid + 1 (0 = world).
 // Trees: one per region (the triangles of the region's own solid and of its child
 // solids) plus one over every triangle; all share the node and triangle arrays.
+constexpr int kNodeFloats = 32;
 struct gadep_bvh {
     int device = 0;
     gadep::MeshData geo;                 // for host-side localisation of sources
-    std::vector<float> nodes;            // 16 floats per node
+    std::vector<float> nodes;            // kNodeFloats floats per node
     std::vector<float> tris;             // 12 floats per triangle slot (leaf order, per tree)
     std::vector<int32_t> tri_orig;       // triangle slot -> mesh triangle index
     std::vector<float> planes;           // per mesh triangle: unit normal, offset n . centroid

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsig
     for (int g = 0; g < (GRAD ? 4 : 1); ++g) score[g] = 0.0f;
     Acc<GRAD> acc;
     acc.reset(-1);
-    TravStats ts{ 0u, 0u };
+    TravStats ts{};
 
     while (true) {
         // ---------------- refill idle lanes from the work counter ----------------
@@ -347,6 +347,7 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P, unsig
     if (COUNT) {
         atomicAdd(&counters[0], (unsigned long long)ts.nodes);
         atomicAdd(&counters[1], (unsigned long long)ts.tris);
+        atomicAdd(&counters[3], (unsigned long long)ts.boxes);
         if (ts.relocated) atomicAdd(&counters[2], (unsigned long long)ts.relocated);
     }
 }
@@ -372,7 +373,7 @@ __global__ void nearest_hit_kernel(const float4 *nodes, const float4 *tris, cons
     float t = INFINITY;
     bool ent = false;
     uint32_t err = 0;
-    TravStats st{ 0, 0 };
+    TravStats st{};
     const int hit = traverse<false>(nodes, tris, planes, root, r[0], r[1], r[2], r[4], r[5], r[6], r[3], ex, t, ent,
                                     err, st);
     t_out[i] = hit >= 0 ? t : INFINITY;
@@ -693,17 +694,14 @@ void scene_box(const gadep_bvh *b, float lo[3], float hi[3])
 {
     for (int k = 0; k < 3; ++k) { lo[k] = 0.0f; hi[k] = -1.0f; }
     if (b->regions[3] < 0) return;
-    const float *f = b->nodes.data() + (size_t)b->regions[3] * 16;
-    int32_t w[4];
-    std::memcpy(w, &f[12], 16);
+    const float *f = b->nodes.data() + (size_t)b->regions[3] * kNodeFloats;
+    int32_t w[8];
+    std::memcpy(w, &f[24], 32);
     for (int k = 0; k < 3; ++k) { lo[k] = INFINITY; hi[k] = -INFINITY; }
-    for (int c = 0; c < 2; ++c) {
-        if (w[c] < 0 && ((~w[c]) & 7) == 0) continue;  // empty leaf slot
-        const float clo[3] = { f[4 * c + 0], f[4 * c + 2], f[8 + 2 * c] };
-        const float chi[3] = { f[4 * c + 1], f[4 * c + 3], f[9 + 2 * c] };
+    for (int c = 0; c < w[4] && c < 4; ++c) {
         for (int k = 0; k < 3; ++k) {
-            lo[k] = std::min(lo[k], clo[k]);
-            hi[k] = std::max(hi[k], chi[k]);
+            lo[k] = std::min(lo[k], f[8 * k + c]);
+            hi[k] = std::max(hi[k], f[8 * k + 4 + c]);
         }
     }
 }
@@ -1325,13 +1323,14 @@ extern "C" gadep_status gadep_grad(const gadep_bvh *b, const gadep_materials *ma
                      (cudaStream_t)stream);
 }
 
-// Work counters of the traversal (nodes visited, triangles tested) for one batch:
-// the COUNT instantiation of the same kernel, used to derive algorithmic bytes
-// and FLOPs per segment query.
+// Work counters of the traversal (nodes visited, boxes and triangles tested) for
+// one batch: the COUNT instantiation of the same kernels, used to derive
+// algorithmic bytes and FLOPs per segment query.
 extern "C" gadep_status gadep_count_work(const gadep_bvh *b, const gadep_materials *mat, int32_t n_inst,
                                          const gadep_instance *inst, const gadep_opts *opts,
                                          gadep_result *results, uint64_t *nodes_visited,
-                                         uint64_t *tris_tested, uint64_t *relocated, void *stream)
+                                         uint64_t *tris_tested, uint64_t *relocated, uint64_t *boxes_tested,
+                                         void *stream)
 {
     gadep::clear_error();
     if (!results || !nodes_visited || !tris_tested) return fail(GADEP_E_INVAL, "gadep_count_work: NULL output");
@@ -1341,6 +1340,7 @@ extern "C" gadep_status gadep_count_work(const gadep_bvh *b, const gadep_materia
     *nodes_visited = c[0];
     *tris_tested = c[1];
     if (relocated) *relocated = c[2];
+    if (boxes_tested) *boxes_tested = c[3];
     return st;
 }
 

@@ -59,9 +59,12 @@ struct __align__(16) Hit {      // by queue position, written by trace
     int tri;                    // mesh triangle id, -1 = nothing ahead
     int region;                 // region of the triangle's solid
     int entering;               // 1 entering, 0 leaving, -2 traversal stack overflow,
-                                // kBeyond: no surface before the sampled interaction point
+                                // kBeyond: no surface before the sampled interaction point;
+                                // + kRelocated when the hit (or tri -1: none) came from the
+                                // tree of every triangle (relocation, see trace_kernel)
 };
 constexpr int kBeyond = -3;
+constexpr int kRelocated = 4;
 static_assert(sizeof(Slot) == 64, "slot record is one 64-byte DRAM fetch");
 // A charged-particle track (e_model 1) whose history goes on after the physics
 // visit that set it going: traced by etrack_kernel before the slot's next visit.
@@ -672,7 +675,7 @@ constexpr int kFetchThreshold = 20;   // refill lanes when fewer are still trave
 // interaction is still found, so physics decides exactly as with an unbounded
 // query; when none is, the hit is marked kBeyond (an interaction follows).
 template <bool COUNT>
-__global__ void __launch_bounds__(256, 5) trace_kernel(const Params P, State S, int cur, unsigned long long *counters)
+__global__ void __launch_bounds__(256, 4) trace_kernel(const Params P, State S, int cur, unsigned long long *counters)
 {
     const uint32_t FULL = 0xffffffffu;
     const float4 *__restrict__ nodes = P.nodes;
@@ -688,10 +691,17 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const Params P, State S, 
     unsigned int qidx = 0;
     float ox = 0, oy = 0, oz = 0, t_min = 0, ix = 0, iy = 0, iz = 0, oix = 0, oiy = 0, oiz = 0, t_best = 0;
     int exclude = -1, node = kSentinel, leaf = 0, sp = 0, best = -1;
-    bool ent = false, bounded = false;
+    bool ent = false, bounded = false, in_solid = false, reloc = false;
     ShearK sh{ 2, false, 0.0f, 0.0f, 1.0f };
-    int stack[kStack];
-    uint32_t nn = 0, nt = 0, err = 0;
+    // stack entries: (child word, key of its box); an entry whose box is entered
+    // beyond the nearest hit found since it was pushed is dropped when popped
+    uint2 stack[kStack];
+    uint32_t nn = 0, nb = 0, nt = 0, err = 0;
+    auto pop = [&]() -> int {
+        uint2 e = stack[sp--];
+        while (__uint_as_float(e.y) > t_best) e = stack[sp--];
+        return (int)e.x;
+    };
     // warp-uniform private range [wb, we) of the queue, refilled a chunk at a time
     unsigned int wb = 0, we = 0;
     bool global_done = false, drained = false;
@@ -741,9 +751,11 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const Params P, State S, 
                     if (mu > 0.0f) t_best = fmaf(lam / mu, 1.0f + 1.0f / 1024.0f, t_min) + 1e-3f;
                 }
                 bounded = t_best < INFINITY;
+                in_solid = (tag & 255u) != 0u;
+                reloc = false;
                 best = -1;
                 ent = false;
-                stack[0] = kSentinel;
+                stack[0] = make_uint2((uint32_t)kSentinel, 0u);
                 sp = 0;
                 const int root = R.w;
                 node = root < 0 ? kSentinel : root;
@@ -755,35 +767,26 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const Params P, State S, 
         // ---- traversal (while-while), left early when too few lanes remain ----
         while (has) {
             while ((unsigned)node < (unsigned)kSentinel) {
-                float4 n0, n1, n2, n3f;
-                ldg256(nodes + 4 * node, n0, n1);
-                ldg256(nodes + 4 * node + 2, n2, n3f);
-                const int4 n3 = make_int4(__float_as_int(n3f.x), __float_as_int(n3f.y), 0, 0);
+                uint32_t k0, k1, k2, k3;
+                int4 cw;
+                int nch;
+                node4_keys(nodes, node, ix, iy, iz, oix, oiy, oiz, t_min, t_best, k0, k1, k2, k3, cw, nch);
                 ++nn;
-                const float a0 = fmaf(n0.x, ix, -oix), a1 = fmaf(n0.y, ix, -oix);
-                const float a2 = fmaf(n0.z, iy, -oiy), a3 = fmaf(n0.w, iy, -oiy);
-                const float a4 = fmaf(n2.x, iz, -oiz), a5 = fmaf(n2.y, iz, -oiz);
-                const float b0 = fmaf(n1.x, ix, -oix), b1 = fmaf(n1.y, ix, -oix);
-                const float b2 = fmaf(n1.z, iy, -oiy), b3 = fmaf(n1.w, iy, -oiy);
-                const float b4 = fmaf(n2.z, iz, -oiz), b5 = fmaf(n2.w, iz, -oiz);
-                const float tmin0 = fmaxf(fmaxf(fminf(a0, a1), fminf(a2, a3)), fmaxf(fminf(a4, a5), t_min));
-                const float tmax0 = fminf(fminf(fmaxf(a0, a1), fmaxf(a2, a3)), fminf(fmaxf(a4, a5), t_best));
-                const float tmin1 = fmaxf(fmaxf(fminf(b0, b1), fminf(b2, b3)), fmaxf(fminf(b4, b5), t_min));
-                const float tmax1 = fminf(fminf(fmaxf(b0, b1), fmaxf(b2, b3)), fminf(fmaxf(b4, b5), t_best));
-                const bool h0 = tmin0 <= tmax0, h1 = tmin1 <= tmax1;
-                if (!h0 && !h1) {
-                    node = stack[sp--];
+                if (COUNT) nb += nch;
+                if (k0 == kMiss) {
+                    node = pop();
                 } else {
-                    const bool first0 = h0 && (!h1 || tmin0 <= tmin1);
-                    node = first0 ? n3.x : n3.y;
-                    if (h0 && h1) {
-                        if (sp + 1 >= kStack) { err |= ERR_STACK; node = kSentinel; leaf = 0; best = -1; break; }
-                        stack[++sp] = first0 ? n3.y : n3.x;
+                    node = child_of(cw, k0);
+                    if (k1 != kMiss) {      // push the others, farthest first
+                        if (sp + 3 >= kStack) { err |= ERR_STACK; node = kSentinel; leaf = 0; best = -1; break; }
+                        if (k3 != kMiss) stack[++sp] = make_uint2((uint32_t)child_of(cw, k3), k3);
+                        if (k2 != kMiss) stack[++sp] = make_uint2((uint32_t)child_of(cw, k2), k2);
+                        stack[++sp] = make_uint2((uint32_t)child_of(cw, k1), k1);
                     }
                 }
                 if (node < 0 && leaf >= 0) {
                     leaf = node;
-                    node = stack[sp--];
+                    node = pop();
                 }
                 if (!__any_sync(__activemask(), leaf >= 0)) break;
             }
@@ -793,7 +796,19 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const Params P, State S, 
                 else if (sh.kz == 1) leaf_test_k<1>(tris, leaf, exclude, ox, oy, oz, sh, t_min, t_best, best, ent, nt);
                 else leaf_test_k<2>(tris, leaf, exclude, ox, oy, oz, sh, t_min, t_best, best, ent, nt);
                 leaf = node;
-                if (node < 0) node = stack[sp--];
+                if (node < 0) node = pop();
+            }
+            if (node == kSentinel && best < 0 && !bounded && in_solid && !reloc && !(err & ERR_STACK)) {
+                // Inside a solid every ray meets the solid's boundary, so a photon whose
+                // region tree has no surface ahead sits a rounding error past it (an
+                // interaction point computed in FP32 right at a surface): search the
+                // tree of every triangle instead; physics then takes the photon to the
+                // region of the surface found, or to the world when there is none.
+                reloc = true;
+                stack[0] = make_uint2((uint32_t)kSentinel, 0u);
+                sp = 0;
+                leaf = 0;
+                node = P.root_all < 0 ? kSentinel : P.root_all;
             }
             if (node == kSentinel) {
                 Hit h;
@@ -804,7 +819,9 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const Params P, State S, 
                                           t_min)
                                 : INFINITY;
                 h.region = best >= 0 ? __float_as_int(__ldg(&tris[3 * best].w)) : 0;
-                h.entering = best >= 0 ? (ent ? 1 : 0) : ((err & ERR_STACK) ? -2 : (bounded ? kBeyond : 0));
+                h.entering = (err & ERR_STACK) ? -2
+                           : (best >= 0 ? (ent ? 1 : 0) + (reloc ? kRelocated : 0)
+                                        : (reloc ? kRelocated : (bounded ? kBeyond : 0)));
                 S.hit[qidx] = h;
                 err = 0;
                 has = false;
@@ -815,6 +832,7 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const Params P, State S, 
     if (COUNT) {
         atomicAdd(&counters[0], (unsigned long long)nn);
         atomicAdd(&counters[1], (unsigned long long)nt);
+        atomicAdd(&counters[3], (unsigned long long)nb);
     }
 }
 
@@ -841,7 +859,7 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
     const unsigned int n = S.ctrl->q_count[cur];
     const int lane = threadIdx.x & 31;
     const uint32_t k0 = P.key0, k1 = P.key1;
-    TravStats ts{ 0u, 0u, 0u };
+    TravStats ts{};
     uint32_t inter_acc = 0;             // interactions of instance inter_inst not yet tallied
     int inter_inst = 0;
     const unsigned int stride = gridDim.x * blockDim.x;
@@ -887,22 +905,15 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
             if (herr) {
                 finished = true;
             } else {
-                float t_hit = ht.t;
-                int hit_tri = ht.tri, hit_region = ht.region;
-                bool entering = ht.entering == 1;
-                if (hit_tri < 0 && region != 0 && ht.entering != kBeyond) {
-                    // Inside a solid every ray meets its boundary, so the photon sits a
-                    // rounding error past it: relocate by the nearest surface of the
-                    // whole mesh; with none ahead it is outside every solid.
-                    const int k = traverse<COUNT>(P.nodes, P.tris, P.planes, P.root_all, ry.o.x, ry.o.y, ry.o.z, ry.d.x,
-                                                  ry.d.y, ry.d.z, ry.o.w, last_tri, t_hit, entering, herr, ts);
+                const float t_hit = ht.t;
+                const int hit_tri = ht.tri, hit_region = ht.region;
+                const bool entering = ht.entering == 1 || ht.entering == 1 + kRelocated;
+                if (ht.entering >= kRelocated) {
+                    // the trace kernel relocated the photon (a rounding error past a
+                    // boundary) by the nearest surface of the whole mesh; with none
+                    // ahead it is outside every solid
                     if (COUNT) ts.relocated++;
-                    if (k < 0) {
-                        region = 0;
-                    } else {
-                        hit_tri = __float_as_int(__ldg(&P.tris[3 * k + 1].w));
-                        hit_region = __float_as_int(__ldg(&P.tris[3 * k].w));
-                    }
+                    if (hit_tri < 0) region = 0;
                 }
                 // region record: material slot, active | (group + 1) << 1, parent, tree root
                 const int4 R = s_reg[region];
@@ -1118,6 +1129,7 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
         if (s_hist[k]) atomicAdd(&S.hist[nxt][k], s_hist[k]);
     if (COUNT) {
         if (ts.nodes) atomicAdd(&counters[0], (unsigned long long)ts.nodes);
+        if (ts.boxes) atomicAdd(&counters[3], (unsigned long long)ts.boxes);
         if (ts.tris) atomicAdd(&counters[1], (unsigned long long)ts.tris);
         if (ts.relocated) atomicAdd(&counters[2], (unsigned long long)ts.relocated);
     }
@@ -1134,7 +1146,7 @@ __global__ void __launch_bounds__(256) etrack_kernel(const Params P, State S, un
     for (int i = threadIdx.x; i < P.n_region; i += blockDim.x) s_reg[i] = P.regions[i];
     __syncthreads();
     const unsigned int n = S.ctrl->t_count;
-    TravStats ts{ 0u, 0u, 0u };
+    TravStats ts{};
     for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const Track t = S.trk[i];
         const int region = (int)(t.tag & 255u), inst = (int)(t.tag >> 8);
@@ -1156,6 +1168,7 @@ __global__ void __launch_bounds__(256) etrack_kernel(const Params P, State S, un
     }
     if (COUNT) {
         if (ts.nodes) atomicAdd(&counters[0], (unsigned long long)ts.nodes);
+        if (ts.boxes) atomicAdd(&counters[3], (unsigned long long)ts.boxes);
         if (ts.tris) atomicAdd(&counters[1], (unsigned long long)ts.tris);
         if (ts.relocated) atomicAdd(&counters[2], (unsigned long long)ts.relocated);
     }

@@ -316,11 +316,13 @@ def test_full_size_coax_against_oracle(orc, otab, mats):
         assert r["sum_dep_all"] + r["sum_esc"] == pytest.approx(n * E, rel=1e-6)
 
 
-@pytest.mark.parametrize("bvh_kw", [dict(split_alpha=1e-5, max_dup=2.0), dict(max_leaf=1), dict(max_leaf=7, c_trav=2.0)])
+@pytest.mark.parametrize("bvh_kw", [dict(split_alpha=1e-5, max_dup=2.0), dict(max_leaf=1), dict(max_leaf=7, c_trav=2.0),
+                                    dict(clip_ratio=6.0, clip_pieces=16)])
 def test_bvh_options_change_no_result(orc, mats, bvh_kw):
-    """The tree only accelerates the queries: spatial splits (triangle records
-    duplicated across leaves), one-triangle leaves or large leaves give the same
-    nearest hits and the same histories as the default tree."""
+    """The tree only accelerates the queries: spatial splits or early split
+    clipping (triangle records duplicated across leaves), one-triangle leaves or
+    large leaves give the same nearest hits and the same histories as the default
+    tree."""
     m, b_def, _ = scene(orc, "COAX_P")
     b = api.gadep_bvh_build(m, 0, **bvh_kw)
     b.validate()
