@@ -190,7 +190,8 @@ typedef struct {
     float c_tri;        /* > 0; default 1 */
     float split_alpha;  /* >= 0, 0 = no spatial splits; default 0 (1e-5 is the usual value when on) */
     float max_dup;      /* 1..16; default 2 */
-    float clip_ratio;   /* 0 = off, else >= 1: early split clipping of loose triangles (below) */
+    float clip_ratio;   /* 0 = off, >= 1: early split clipping of loose triangles (below);
+                           < 0 = AUTO (default): 8 for meshes of at least 2^17 triangles, else off */
     int32_t clip_pieces;/* 1..256 references per triangle at most; default 16 */
 } gadep_bvh_opts;
 void gadep_bvh_opts_default(gadep_bvh_opts *o);

@@ -26,6 +26,8 @@ namespace {
 constexpr int kBins = 32;          // centroid bins of the object split
 constexpr int kSpatialBins = 32;   // slabs of the spatial split
 constexpr int kMaxDepth = 60;
+constexpr int32_t kClipAutoTris = 1 << 17;   // AUTO early split clipping: meshes at least this large
+constexpr float kClipAutoRatio = 8.0f;
 
 struct AABB {
     float lo[3] = { INFINITY, INFINITY, INFINITY };
@@ -619,10 +621,18 @@ gadep_status build_bvh_host(const detmesh_mesh *m, const gadep_bvh_opts &o, gade
     const int32_t nt = g.n_tri();
     if (nt >= (1 << 26)) return fail(GADEP_E_INVAL, "bvh: at most 2^26 triangles");
     if (o.max_leaf < 1 || o.max_leaf > 7 || !(o.c_trav >= 0.0f) || !(o.c_tri > 0.0f) || !(o.split_alpha >= 0.0f) ||
-        !(o.max_dup >= 1.0f) || !(o.max_dup <= 16.0f) || !(o.clip_ratio == 0.0f || o.clip_ratio >= 1.0f) ||
+        !(o.max_dup >= 1.0f) || !(o.max_dup <= 16.0f) || !(o.clip_ratio <= 0.0f || o.clip_ratio >= 1.0f) ||
         o.clip_pieces < 1 || o.clip_pieces > 256)
         return fail(GADEP_E_INVAL, "bvh: bad options (max_leaf 1..7, c_tri > 0, c_trav >= 0, split_alpha >= 0, "
-                                   "max_dup in [1, 16], clip_ratio 0 or >= 1, clip_pieces 1..256)");
+                                   "max_dup in [1, 16], clip_ratio <= 0 or >= 1, clip_pieces 1..256)");
+    // AUTO clipping (clip_ratio < 0): on for meshes of at least kClipAutoTris
+    // triangles.  Measured: the 1,012,288-triangle stress mesh traces 1.7x faster
+    // with clip_ratio 8 (its 1024-segment centre fans made 53 triangle tests per
+    // query, 19 after clipping); on the 13,824-triangle coax the tree fits in L1
+    // and the extra nodes cost as much as the triangle tests they save (1-2 %
+    // slower), so small meshes keep one reference per triangle.
+    gadep_bvh_opts oo = o;
+    if (oo.clip_ratio < 0.0f) oo.clip_ratio = nt >= kClipAutoTris ? kClipAutoRatio : 0.0f;
     out->nodes.clear();
     out->tris.clear();
     out->tri_orig.clear();
@@ -630,12 +640,12 @@ gadep_status build_bvh_host(const detmesh_mesh *m, const gadep_bvh_opts &o, gade
     TreeStats all_ts, reg_ts;
     std::vector<int32_t> all(nt);
     for (int32_t t = 0; t < nt; ++t) all[t] = t;
-    out->root_all = append_tree(m, all, o, out, all_ts, st);
+    out->root_all = append_tree(m, all, oo, out, all_ts, st);
     if (st != GADEP_OK) return st;
     const auto sets = region_triangle_sets(g);
     std::vector<int32_t> roots(sets.size(), -1);
     for (size_t r = 0; r < sets.size(); ++r) {
-        roots[r] = append_tree(m, sets[r], o, out, reg_ts, st);
+        roots[r] = append_tree(m, sets[r], oo, out, reg_ts, st);
         if (st != GADEP_OK) return st;
     }
     // regions: 0 = world, s + 1 = solid s; (material, active | (group + 1) << 1, parent, root)
@@ -681,7 +691,7 @@ gadep_status build_bvh_host(const detmesh_mesh *m, const gadep_bvh_opts &o, gade
     stt.node_bytes = (int64_t)stt.n_nodes * kNodeFloats * 4;
     stt.tri_bytes = (int64_t)(out->tris.size() / 12) * 48;
     stt.n_refs = all_ts.refs + reg_ts.refs;
-    stt.opts = o;
+    stt.opts = oo;
     return GADEP_OK;
 }
 
@@ -695,7 +705,7 @@ extern "C" void gadep_bvh_opts_default(gadep_bvh_opts *o)
     o->c_tri = 1.0f;
     o->split_alpha = 0.0f;
     o->max_dup = 2.0f;
-    o->clip_ratio = 0.0f;
+    o->clip_ratio = -1.0f;
     o->clip_pieces = 16;
 }
 

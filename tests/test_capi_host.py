@@ -192,8 +192,12 @@ def test_bvh_options():
     st = b.stats()
     assert st["max_leaf_tris"] <= 2 and st["opts"]["max_leaf"] == 2 and st["opts"]["c_trav"] == 0.5
     d = api.gadep_bvh_build(m, device=-1).stats()["opts"]
+    # the options a tree reports are the ones it was built with: AUTO clipping
+    # resolved to off for this small mesh
     assert d == {"max_leaf": 4, "c_trav": 1.5, "c_tri": 1.0, "split_alpha": 0.0, "max_dup": 2.0, "clip_ratio": 0.0,
                  "clip_pieces": 16}
+    o = api.bvh_opts()
+    assert o.clip_ratio < 0 and o.clip_pieces == 16
     for kw in (dict(clip_ratio=0.5), dict(clip_ratio=4.0, clip_pieces=0), dict(clip_ratio=4.0, clip_pieces=257)):
         with pytest.raises(capi.GadepError):
             api.gadep_bvh_build(m, device=-1, **kw)
