@@ -82,9 +82,11 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload, kind):
-    """DRAM bytes per launch of kernel `kind` from the committed ncu launch list,
-    or None when the kernels changed since it was taken."""
+def recorded_traffic(workload, kind, queries_per_launch):
+    """DRAM bytes per launch of kernel `kind`: the committed per-query figure
+    (ncu on a small case of the workload, a few launches of that kernel alone,
+    divided by the queries those launches served) times the queries of an average
+    launch here; None when the kernels changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
@@ -93,7 +95,8 @@ def recorded_traffic(workload, kind):
     e = d.get(workload)
     if not e or e.get("kernel_hash") != kernel_hash():
         return None
-    return e.get("dram_bytes_per_launch", {}).get(kind)
+    per_query = e.get("dram_bytes_per_query", {}).get(kind)
+    return None if per_query is None else per_query * queries_per_launch
 
 
 def measured_peaks():
@@ -282,13 +285,98 @@ def measure_forms(dev, scale=1.0):
 
     t_b5, (rb5, _, _, _) = one_plan(False)
     t_g5, (rg5, _, dg5, _) = one_plan(True)
+    roof5 = stress_roofline(b5, mats, items5, dev)
     out["stress"] = {"triangles": int(b5.stats()["n_tri"]), "mesh_build_s": round(t_mesh5, 3),
                      "bvh_build_s": round(t_bvh5, 3), "instances": len(items5), "histories": total5,
                      "plain_hist_per_s": total5 / t_p5, "batched_hist_per_s": total5 / t_b5,
                      "batched_grad_hist_per_s": total5 / t_g5, "batched_vs_plain": t_p5 / t_b5,
                      "batched_grad_vs_plain": t_p5 / t_g5,
                      "fepe": [r["fepe"] for r in rg5], "dfepe_first": [float(x) for x in dg5[0]],
-                     "n_err": sum(r["n_err"] for r in rb5) + sum(r["n_err"] for r in rg5)}
+                     "n_err": sum(r["n_err"] for r in rb5) + sum(r["n_err"] for r in rg5),
+                     "bvh": b5.stats()["opts"], "bvh_mb": round((b5.stats()["node_bytes"] + b5.stats()["tri_bytes"]) / 1e6, 1),
+                     "roofline": roof5}
+    del b5, m5
+    # ---- Table 4 shape (detector #2, 13 energies, source 250 mm) and the mesh-density sweep ----
+    out["table4"] = table4_form(dev, scale)
+    cfg_c = workload_config("coax", 0)
+    out["mesh_sweep"] = {"coax": mesh_sweep(cfg_c, dev, max(1, int(10_000_000 * scale)), api.make_opts()),
+                         "table4": mesh_sweep(workload_config("table4", 0), dev, max(1, int(10_000_000 * scale)),
+                                              api.make_opts()),
+                         "histories_per_energy": max(1, int(10_000_000 * scale))}
+    return out
+
+
+def stress_roofline(bvh, mats, items, dev):
+    """Roofline of the trace kernel on the stress workload: the one batched plan
+    timed again with a CUDA event pair around every kernel (host-issued
+    iterations), the traversal work counted by the instrumented kernels on the
+    same histories, and the algorithmic FLOPs and node/triangle bytes per second
+    against the derived FP32 peak and the measured L2 and HBM peaks."""
+    from paper_2605_25963_gb300 import api
+    p = api.Plan(bvh, mats, api.make_instances(items), api.make_opts())
+    p.launch()
+    p.set_timing(True)
+    p.kernel_stats(reset=True)
+    p.launch()
+    st = p.kernel_stats(reset=True)
+    res, _, _, _ = p.results(want_spectra=False)
+    del p
+    _, nodes, tris, _, boxes = api.gadep_count_work(bvh, mats, api.make_instances(items), api.make_opts())
+    segs = sum(r["n_segments"] for r in res)
+    queries = segs - sum(r["n_culled"] for r in res)
+    nl, ms = st.get("trace", (0, 0.0))
+    if not nl:
+        return None
+    flops = FLOP_PER_BOX * boxes + FLOP_PER_TRI * tris
+    bytes_ = NODE_BYTES * nodes + TRI_BYTES * tris
+    sm_max = measured_peaks().get("sm_max_mhz") or 2070.0
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (ms / 1e3) / 1e12
+    hbm = measured_peaks().get("hbm_gbs")
+    return {"bound": "alu", "kernel": "trace", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": recorded_traffic("stress", "trace", queries / nl),
+            "launches": nl, "avg_launch_ms": ms / nl, "flop_per_launch": flops / nl,
+            "node_tri_bytes_gbs": bytes_ / (ms / 1e3) / 1e9, "hbm_peak_gbs": hbm,
+            "per_query": {"nodes": nodes / max(queries, 1), "boxes": boxes / max(queries, 1),
+                          "tris": tris / max(queries, 1)},
+            "kernels_ms": {k: round(v, 2) for k, (n, v) in st.items() if n},
+            "queries": queries,
+            "note": "stress BVH (clipped references) exceeds L2: node and triangle bytes per second of the trace "
+                    "kernel are served partly from HBM"}
+
+
+def table4_form(dev, scale=1.0):
+    """The Table 4 shape workload: detector #2 of Table 1, point source 250 mm on
+    the axis, the 13 Table 3 energies, at 1e7 and 1e8 histories per energy (one
+    step each, device time after a warm-up step), beside the paper's RTX 4090
+    times for coupled photon-electron transport (context only)."""
+    import torch
+    from paper_2605_25963_gb300 import api
+    cfg = workload_config("table4", 0)
+    mats = api.Materials.default()
+    m = api.detmesh_build(cfg["det"])
+    b = api.gadep_bvh_build(m, dev)
+    out = {"triangles": int(b.stats()["n_tri"]), "energies": len(cfg["energies"])}
+    for n in (10_000_000, 100_000_000):
+        nn = max(1, int(n * scale))
+        plans = [api.Plan(b, mats, api.make_instances([(E, cfg["src"], nn, i, [])]), api.make_opts())
+                 for i, E in enumerate(cfg["energies"])]
+        for p in plans:
+            p.launch()
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for p in plans:
+            p.launch()
+        e.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e)
+        fe = [p.results(want_spectra=False)[0][0]["fepe"] for p in plans]
+        out["%.0e" % n] = {"histories_per_energy": nn, "ms_all_energies": round(ms, 2),
+                           "hist_per_s": nn * len(plans) / (ms / 1e3),
+                           "paper_rtx4090_s": cfg["paper_s"]["1e7" if n == 10_000_000 else "1e8"],
+                           "fepe": fe, "form": "AUTO (per energy)"}
+        del plans
     return out
 
 
@@ -364,6 +452,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run through gadep_run with host buffers")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / gradient comparison")
     ap.add_argument("--forms-scale", type=float, default=1.0, help="history-count scale of the form runs")
+    ap.add_argument("--queue-log", action="store_true",
+                    help="add the trace queue size of every wavefront iteration of the instrumented pass "
+                         "(per plan) to the line, to turn ncu counters of single launches into per-query figures")
     ap.add_argument("--mesh-sweep", action="store_true",
                     help="also time the workload's detector at N_theta x N_phi from 32 x 10 to 1024 x 40")
     args = ap.parse_args()
@@ -470,6 +561,7 @@ def main():
     for f, E in zip(fepe, cfg["energies"]):
         f["E_keV"] = E
 
+    qlog = [p.queue_sizes() for p in plans] if args.queue_log else None
     # algorithmic work of one step (instrumented copy of the kernel, untimed)
     nodes = tris = relocated = boxes = 0
     for i, E in enumerate(cfg["energies"]):
@@ -566,7 +658,8 @@ def main():
                        "bvh": bvh.stats()["opts"]},
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved_tflops, "peak": peak_tflops,
                          "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
-                         "traffic": recorded_traffic(args.workload, dom),
+                         "traffic": recorded_traffic(args.workload, dom,
+                                                     queries * args.steps / max(dom_launches, 1)),
                          "launches": dom_launches, "avg_launch_ms": dom_ms / max(dom_launches, 1),
                          "flop_per_launch": flops_per_step * args.steps / max(dom_launches, 1),
                          "peak_note": "FP32 non-tensor: %d SMs x %d lanes x 2 x %.0f MHz (derived)" % (
@@ -593,6 +686,8 @@ def main():
         }
         if sweep is not None:
             line["mesh_sweep"] = sweep
+        if qlog is not None:
+            line["queue_sizes"] = qlog
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

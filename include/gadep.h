@@ -41,7 +41,7 @@ typedef enum {
 
 /* Thread-local description of the last error of this thread (never NULL). */
 const char *gadep_last_error(void);
-/* ABI version of this header: 1. */
+/* ABI version of this header: 2. */
 int32_t gadep_abi_version(void);
 
 /* ------------------------------------------------------------------------- */
@@ -458,6 +458,13 @@ gadep_status gadep_plan_set_timing(gadep_plan *p, int32_t on);
 /* Waits for the timed launches (host synchronisation on their events), writes
  * the statistics to *out (host) and, when reset != 0, clears them. */
 gadep_status gadep_plan_kernel_stats(gadep_plan *p, gadep_kernel_stats *out, int32_t reset);
+
+/* Trace queue size of each wavefront iteration of the plan's last launch, in
+ * order (the queries its trace kernel launches served), for measurements that
+ * need the work of individual launches (no counterpart in the paper).  out: host
+ * [max]; *n: entries written (0 for a megakernel plan; the log holds the first
+ * 8192 iterations).  Synchronises `stream`. */
+gadep_status gadep_plan_queue_sizes(gadep_plan *p, uint32_t *out, int32_t max, int32_t *n, void *stream);
 
 /* Work counters of the traversal for one batch (same histories as gadep_run_batch):
  * 4-wide BVH nodes visited, child boxes tested in them (a node's empty slots not

@@ -399,6 +399,14 @@ class Plan(_Handle):
         check(capi.load().gadep_plan_kernel_stats(self._h, C.byref(ks), 1 if reset else 0))
         return {k: (int(ks.launches[i]), float(ks.ms[i])) for i, k in enumerate(capi.KERNEL_KINDS)}
 
+    def queue_sizes(self, max_entries=8192, stream=None):
+        """Trace queue size of each wavefront iteration of the last launch (empty
+        for a megakernel plan)."""
+        buf = (C.c_uint32 * max_entries)()
+        n = C.c_int32()
+        check(capi.load().gadep_plan_queue_sizes(self._h, buf, max_entries, C.byref(n), _stream(stream)))
+        return [int(buf[i]) for i in range(n.value)]
+
     def results(self, want_spectra=True, stream=None, raise_device_errors=True):
         """Tallies of the last launch.  With raise_device_errors=False a set device
         error word is reported through each result's n_err / dev_err instead."""

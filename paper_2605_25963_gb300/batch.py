@@ -56,9 +56,15 @@ def _scaled(items, total):
 
 
 def default_candidates():
+    """Megakernel launch shapes, and the wavefront form with the slot count sized
+    from the run (0) or fixed.  The slot count trades the trace kernel, which
+    prefers every photon in flight at once (fuller, better sorted queues), against
+    the physics kernel, whose random 64-byte slot records stay in L2 when there
+    are fewer of them (batched workload: physics 299 ms at 2^25 slots, 204 ms at
+    2^22; the whole plan fastest at 2^22)."""
     cands = [dict(variant=MEGA, block=b, chunk=c, blocks_per_sm=0)
              for b, c in itertools.product((128, 256), (64, 256, 1024))]
-    cands.append(dict(variant=WAVEFRONT))
+    cands += [dict(variant=WAVEFRONT, wf_slots=s) for s in (0, 1 << 21, 1 << 22, 1 << 23)]
     return cands
 
 
@@ -77,7 +83,7 @@ def _time_plan(plan, repeats):
     return best
 
 
-def autotune(bvh, mats, items, grad=False, sample_histories=20_000_000, candidates=None, repeats=2,
+def autotune(bvh, mats, items, grad=False, sample_histories=100_000_000, candidates=None, repeats=2,
              opts_kw=None):
     """Time each launch form / shape on a scaled copy of the batch; return (best opts, table).
 

@@ -23,7 +23,7 @@ EXPORTS = (
     "gadep_bvh_build_opts", "gadep_bvh_opts_default", "gadep_bvh_get_stats", "gadep_bvh_validate", "gadep_bvh_destroy", "gadep_nearest_hit",
     "gadep_opts_default", "gadep_run", "gadep_run_batch", "gadep_grad", "gadep_plan_create",
     "gadep_plan_launch", "gadep_plan_results", "gadep_plan_shape", "gadep_plan_destroy",
-    "gadep_count_work", "gadep_philox_words", "gadep_run_noalloc", "gadep_plan_set_timing",
+    "gadep_count_work", "gadep_philox_words", "gadep_run_noalloc", "gadep_plan_set_timing", "gadep_plan_queue_sizes",
     "gadep_plan_kernel_stats", "gadep_measure_peaks",
 )
 # kernel kinds of gadep_kernel_stats
@@ -158,6 +158,7 @@ def load(build_if_missing: bool = True):
         "gadep_plan_shape": (st, [vp, P(C.c_int32), P(C.c_int32), P(C.c_int32)]),
         "gadep_plan_destroy": (None, [vp]),
         "gadep_plan_set_timing": (st, [vp, C.c_int32]),
+        "gadep_plan_queue_sizes": (st, [vp, P(C.c_uint32), C.c_int32, P(C.c_int32), vp]),
         "gadep_measure_peaks": (st, [C.c_int32, P(C.c_double), P(C.c_double)]),
         "gadep_plan_kernel_stats": (st, [vp, P(gadep_kernel_stats), C.c_int32]),
         "gadep_count_work": (st, [vp, P(gadep_materials), C.c_int32, P(gadep_instance), P(gadep_opts),

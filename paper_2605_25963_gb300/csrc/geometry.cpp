@@ -295,4 +295,4 @@ gadep_status validate_and_nest(MeshData &m)
 }  // namespace gadep
 
 extern "C" const char *gadep_last_error(void) { return gadep::last_error(); }
-extern "C" int32_t gadep_abi_version(void) { return 1; }
+extern "C" int32_t gadep_abi_version(void) { return 2; }

@@ -543,6 +543,7 @@ struct gadep_plan {
     uint32_t *last_spectra = nullptr;
     gadep::WavefrontBuffers *wf = nullptr;   // set when the plan runs the wavefront form
     bool wf_cached = false;                  // wf borrowed from the BVH's cache
+    int wf_slots = 0;                        // photon slots the plan keeps in flight
     gadep::KernelTimer timer;                // launch counts and optional event timing
 };
 
@@ -923,11 +924,12 @@ gadep_status plan_create(const gadep_bvh *b, const gadep_materials *mat, int32_t
             slots = 1 << 20;
             while (slots < (1 << 25) && (double)slots < reaching) slots <<= 1;
         }
+        p->wf_slots = slots;
         gadep_bvh *bm = const_cast<gadep_bvh *>(b);
         {
             std::lock_guard<std::mutex> lock(bm->wf_mutex);
             if (!bm->wf_cache_busy) {
-                // keep the largest buffers seen: a run may use more slots than it asked for
+                // keep the largest buffers seen; a run uses the slots it asked for
                 if (bm->wf_cache && bm->wf_cache_slots < slots) {
                     wavefront_destroy(bm->wf_cache);
                     bm->wf_cache = nullptr;
@@ -1072,7 +1074,7 @@ gadep_status plan_launch(gadep_plan *p, uint32_t *spectra_dev, float *edep_trace
         (e = cudaMemsetAsync(p->d_counters, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
         return cuda_fail(e, "plan launch: memset");
     if (P.total == 0) return GADEP_OK;
-    if (p->wf) return wavefront_run(p->wf, P, p->grad, p->count, p->d_counters, &p->timer, s);
+    if (p->wf) return wavefront_run(p->wf, P, p->grad, p->count, p->d_counters, &p->timer, s, p->wf_slots);
     p->timer.before(s);
     if (p->grad) {
         if (p->count) dev::transport_kernel<true, true, false><<<p->grid, p->block, p->smem, s>>>(P, p->d_counters);
@@ -1249,6 +1251,19 @@ extern "C" gadep_status gadep_plan_kernel_stats(gadep_plan *p, gadep_kernel_stat
     }
     if (reset) p->timer.reset();
     return e == cudaSuccess ? GADEP_OK : gadep::cuda_fail(e, "gadep_plan_kernel_stats: event");
+}
+
+extern "C" gadep_status gadep_plan_queue_sizes(gadep_plan *p, uint32_t *out, int32_t max, int32_t *n, void *stream)
+{
+    gadep::clear_error();
+    if (!p || !n || (max > 0 && !out)) return fail(GADEP_E_INVAL, "gadep_plan_queue_sizes: NULL argument");
+    *n = 0;
+    if (!p->wf) return GADEP_OK;
+    DeviceGuard g(p->device);
+    int k = 0;
+    const gadep_status st = gadep::wavefront_queue_log(p->wf, out, max, &k, (cudaStream_t)stream);
+    *n = k;
+    return st;
 }
 
 extern "C" gadep_status gadep_plan_shape(const gadep_plan *p, int32_t *grid, int32_t *block, int32_t *smem_bytes)

@@ -378,10 +378,13 @@ struct WavefrontBuffers;
 constexpr int kWavefrontMaxInstances = 1024;   // block tallies live in shared memory
 gadep_status wavefront_create(int device, int slots, bool grad, WavefrontBuffers **out);
 void wavefront_destroy(WavefrontBuffers *w);
+// slots: photon slots the run keeps in flight (at most the buffers' capacity; 0 =
+// the capacity).
 gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P, bool grad, bool count,
-                           unsigned long long *counters, KernelTimer *timer, cudaStream_t s);
+                           unsigned long long *counters, KernelTimer *timer, cudaStream_t s, int slots);
 int wavefront_trace_grid(const WavefrontBuffers *w);
 gadep_status wavefront_check(WavefrontBuffers *w, cudaStream_t s);
+gadep_status wavefront_queue_log(WavefrontBuffers *w, uint32_t *out, int max, int *n, cudaStream_t s);
 // Whether the wavefront records can address the mesh (region and triangle ids
 // share one 32-bit word).
 bool wavefront_supports(int n_region, long long n_mesh_tri);

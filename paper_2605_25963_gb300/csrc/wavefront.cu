@@ -321,8 +321,10 @@ struct State {
     unsigned long long pend_mask;  // ring size - 1 (a power of two)
     unsigned long long gen_target; // ring fill at which gen stops claiming ids
     Ctrl *ctrl;
+    unsigned int *qlog;            // trace queue size of each iteration (the first kQueueLog)
     int slots;
 };
+constexpr int kQueueLog = 8192;
 
 constexpr int kGenChunk = 2048;    // history ids per gen claim (8 per thread)
 constexpr int kTraceChunk = 64;    // queue entries per trace claim
@@ -440,7 +442,11 @@ __global__ void ctrl_kernel(State S, int cur, unsigned long long total, cudaGrap
     }
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     Ctrl &c = *S.ctrl;
-    if (!c.done) ctrl_step(c, cur, total);
+    if (!c.done) {
+        ctrl_step(c, cur, total);
+        // queue of the iteration just planned (for measurements per query)
+        if (!c.done && c.iter <= (unsigned int)kQueueLog) S.qlog[c.iter - 1] = c.q_count[cur ^ 1];
+    }
     if (in_graph) cudaGraphSetConditional(loop, c.done ? 0u : 1u);
 }
 
@@ -1234,6 +1240,7 @@ gadep_status wavefront_create(int device, int slots, bool grad, WavefrontBuffers
     size_t o_d0 = off; off = align_up(off + n * 4);
     size_t o_pend = off; off = align_up(off + ring * sizeof(unsigned long long));
     size_t o_ctrl = off; off = align_up(off + sizeof(wf::Ctrl));
+    size_t o_qlog = off; off = align_up(off + sizeof(unsigned int) * wf::kQueueLog);
     cudaError_t e = cudaMalloc(&w->block, off);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1266,6 +1273,7 @@ gadep_status wavefront_create(int device, int slots, bool grad, WavefrontBuffers
     w->S.pend_mask = ring - 1;
     w->S.gen_target = target;
     w->S.ctrl = (wf::Ctrl *)(b + o_ctrl);
+    w->S.qlog = (unsigned int *)(b + o_qlog);
     w->S.slots = slots;
     *out = w;
     return GADEP_OK;
@@ -1284,7 +1292,7 @@ void wavefront_destroy(WavefrontBuffers *w)
 
 // Run every history of the plan's Params through the wavefront kernels on `s`.
 gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P0, bool grad, bool count,
-                           unsigned long long *counters, KernelTimer *timer, cudaStream_t s)
+                           unsigned long long *counters, KernelTimer *timer, cudaStream_t s, int slots)
 {
     if (P0.e_model && !w->trk) {
         void *t = nullptr;
@@ -1296,6 +1304,12 @@ gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P0, bool grad
         w->S.trk = (wf::Track *)t;
     }
     wf::State S = w->S;
+    // a run may keep fewer photons in flight than the (cached, largest-seen)
+    // buffers hold: its free-slot stack and birth target cover only those slots
+    if (slots > 0 && slots < S.slots) {
+        S.slots = slots;
+        S.gen_target = (unsigned long long)slots;
+    }
     dev::Params P = P0;
     P.face_bins = wf::face_bins_for(P.n_region);
     P.n_keys = P.n_region * 6 * P.face_bins * P.face_bins;
@@ -1492,6 +1506,24 @@ gadep_status wavefront_run(WavefrontBuffers *w, const dev::Params &P0, bool grad
                 return fail(GADEP_E_TIMEOUT, "wavefront: iteration bound reached with photons still alive");
         }
     }
+}
+
+// After a run has completed on `s`: the trace queue size of each of its
+// iterations (at most `max`, and at most the first kQueueLog); returns the count.
+gadep_status wavefront_queue_log(WavefrontBuffers *w, uint32_t *out, int max, int *n, cudaStream_t s)
+{
+    cudaError_t e = cudaMemcpyAsync(w->host_ctrl, w->S.ctrl, sizeof(wf::Ctrl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(GADEP_E_CUDA, "wavefront: queue log: %s", cudaGetErrorString(e));
+    const int iters = (int)std::min<unsigned int>(w->host_ctrl->iter, (unsigned int)wf::kQueueLog);
+    const int k = std::max(0, std::min(iters, max));
+    if (k > 0) {
+        e = cudaMemcpyAsync(out, w->S.qlog, sizeof(uint32_t) * (size_t)k, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return fail(GADEP_E_CUDA, "wavefront: queue log: %s", cudaGetErrorString(e));
+    }
+    *n = k;
+    return GADEP_OK;
 }
 
 // After a run has completed on `s` (the caller synchronised it): the iteration

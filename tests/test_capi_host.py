@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol():
     for n in names:
         assert hasattr(L, n), n
     assert set(names) == set(capi.EXPORTS)
-    assert L.gadep_abi_version() == 1
+    assert L.gadep_abi_version() == 2
 
 
 def det_pair(orc, d):

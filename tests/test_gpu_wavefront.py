@@ -78,6 +78,34 @@ def test_graph_loop_equals_host_loop():
             assert a[k] == c[k] == d[k], k
     assert np.array_equal(sg, sh) and np.array_equal(sg, sg2)
     assert stats["trace"][0] > 0 and stats["trace"][1] > 0.0
+    # the queue log: one entry per iteration of the last launch, which served every
+    # segment that needed a query (histories ended at birth need none)
+    q = p.queue_sizes()
+    assert len(q) == stats["trace"][0] or len(q) == stats["trace"][0] - 1
+    assert sum(q) == sum(r["n_segments"] - r["n_culled"] for r in rg2)
+    assert max(q) <= 65536
+
+
+def test_smaller_slot_count_on_cached_buffers():
+    """A run asking for fewer photon slots than the BVH's cached buffers hold keeps
+    only those in flight (more iterations) and gives the same histories."""
+    m = api.detmesh_build(W.COAX_P)
+    b = api.gadep_bvh_build(m, 0)
+    mats = api.Materials.default()
+    inst = api.make_instances([(662.0, W.COAX_POINT_25, 800_000, 0, [])])
+    big = api.Plan(b, mats, inst, api.make_opts(variant=WAVEFRONT, wf_slots=1 << 20))
+    big.launch()
+    rb, sb, _, _ = big.results()
+    qb = big.queue_sizes()
+    del big
+    small = api.Plan(b, mats, inst, api.make_opts(variant=WAVEFRONT, wf_slots=1 << 14))
+    small.launch()
+    rs, ss, _, _ = small.results()
+    qs = small.queue_sizes()
+    assert max(qs) <= 1 << 14 < max(qb) and len(qs) > len(qb)
+    for k in ("n_hist", "n_fep", "n_zero", "n_over", "n_segments", "n_culled"):
+        assert rb[0][k] == rs[0][k], k
+    assert np.array_equal(sb, ss)
 
 
 def test_graph_batch_captures_wavefront_plan():
