@@ -552,12 +552,17 @@ def main():
     hist_per_step = n * len(plans) * world
     value = hist_per_step * args.steps / (total_ms / 1e3)
 
-    # results of the last step (FEPE per energy)
+    # results of the last step (FEPE per energy); with several ranks the tallies and
+    # spectra of every rank's history range are summed (after the timed region)
     fepe = []
     for p in plans:
-        res, _, _, _ = p.results(want_spectra=False, raise_device_errors=False)
-        fepe.append({"E_keV": None, "fepe": res[0]["fepe"], "sigma": res[0]["sigma"], "n_err": res[0]["n_err"],
-                     "dev_err": res[0]["dev_err"], "segments": res[0]["n_segments"], "culled": res[0]["n_culled"]})
+        res, spec, _, _ = p.results(want_spectra=dist is not None, raise_device_errors=False)
+        f = {"E_keV": None, "fepe": res[0]["fepe"], "sigma": res[0]["sigma"], "n_err": res[0]["n_err"],
+             "dev_err": res[0]["dev_err"], "segments": res[0]["n_segments"], "culled": res[0]["n_culled"]}
+        if dist is not None:
+            tot, _, f_all, s_all = shard.reduce_tallies(res[0], spec[0])
+            f["all_ranks"] = {"n_hist": tot["n_hist"], "n_fep": tot["n_fep"], "fepe": f_all, "sigma": s_all}
+        fepe.append(f)
     for f, E in zip(fepe, cfg["energies"]):
         f["E_keV"] = E
 
