@@ -39,21 +39,34 @@ namespace wf {
 
 using namespace gadep::dev;
 
-// Per-slot photon record: 64 bytes, the DRAM fetch unit, so the physics visit
-// that needs all of it costs one fetch and the trace query (first half) no more.
-struct Ray {
-    float4 o;                   // origin, w = t_cur (distance already travelled from o)
-    float4 d;                   // direction, w = tag bits (last mesh triangle + 1) << 8 | region
+// Per-slot photon record: 64 bytes, the DRAM fetch unit, in two 32-byte halves
+// (DRAM sectors).  The first holds everything a boundary crossing -- three
+// visits in four -- reads and changes, so such a physics visit moves one sector
+// each way; the second (flight origin, direction, random-number state) is read
+// only at interactions and when a waiting annihilation photon starts, and
+// written then.  The trace query reads both.
+struct __align__(32) SlotA {
+    float4 f;                   // t_cur (distance travelled from the flight origin), tag bits
+                                // (last mesh triangle + 1) << 8 | region, E, lam (mean free paths left)
+    uint4 u;                    // info (instance, error bits, flags, direction cell), segments so far,
+                                // edep (active) bits, dep_all bits
 };
-struct Phot {
-    float4 f;                   // E, lam (mean free paths left), edep (active), dep_all
-    uint4 u;                    // Philox words used, history index within the instance,
-                                // instance | error bits << 16 | flags << 24, segments so far
+struct __align__(32) SlotB {
+    float4 o;                   // flight origin, w = Philox words used (bits)
+    float4 d;                   // direction, w = history index within the instance (bits)
 };
 struct __align__(64) Slot {
-    Ray r;                      // read by trace and physics, written by spawn and physics
-    Phot p;                     // read and written by physics, written by spawn
+    SlotA a;                    // read and written by every physics visit, read by trace
+    SlotB b;                    // read by trace; read and written by physics at interactions
 };
+// info word: instance (10 bits; a run has at most 1024), error bits (6), flags (2),
+// direction cell of the sort key (14: face and cell of the cube map)
+constexpr uint32_t kInstMask = 0x3ffu, kErrShift = 10, kErrMask = 0x3fu, kFlagShift = 16, kFlagMask = 3u,
+                   kCellShift = 18;
+__device__ __forceinline__ uint32_t info_pack(uint32_t inst, uint32_t err, uint32_t flags, uint32_t cell)
+{
+    return inst | ((err & kErrMask) << kErrShift) | ((flags & kFlagMask) << kFlagShift) | (cell << kCellShift);
+}
 struct __align__(16) Hit {      // by queue position, written by trace
     float t;
     int tri;                    // mesh triangle id, -1 = nothing ahead
@@ -65,7 +78,7 @@ struct __align__(16) Hit {      // by queue position, written by trace
 };
 constexpr int kBeyond = -3;
 constexpr int kRelocated = 4;
-static_assert(sizeof(Slot) == 64, "slot record is one 64-byte DRAM fetch");
+static_assert(sizeof(Slot) == 64 && sizeof(SlotA) == 32, "slot record: two 32-byte DRAM sectors");
 // A charged-particle track (e_model 1) whose history goes on after the physics
 // visit that set it going: traced by etrack_kernel before the slot's next visit.
 struct __align__(16) Track {
@@ -105,7 +118,7 @@ __device__ __forceinline__ uint32_t ray_tag(int last_tri, int region)
 // other two components divided by the dominant one.  Lanes of a warp then share
 // the region's tree and the shear permutation of the triangle test, and descend
 // the tree along similar paths.
-__device__ __forceinline__ uint32_t sort_key(int region, int fb, float dx, float dy, float dz)
+__device__ __forceinline__ uint32_t dir_cell(int fb, float dx, float dy, float dz)
 {
     const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
     const uint32_t kz = (ax > ay) ? ((ax > az) ? 0u : 2u) : ((ay > az) ? 1u : 2u);
@@ -114,7 +127,14 @@ __device__ __forceinline__ uint32_t sort_key(int region, int fb, float dx, float
     const float h = 0.5f * (float)fb / fabsf(m);
     const uint32_t bu = min((uint32_t)fmaxf(fmaf(u, h, 0.5f * (float)fb), 0.0f), (uint32_t)fb - 1u);
     const uint32_t bw = min((uint32_t)fmaxf(fmaf(w, h, 0.5f * (float)fb), 0.0f), (uint32_t)fb - 1u);
-    return ((uint32_t)region * 6u + kz * 2u + (m < 0.0f ? 1u : 0u)) * (uint32_t)(fb * fb) + bu * (uint32_t)fb + bw;
+    return (kz * 2u + (m < 0.0f ? 1u : 0u)) * (uint32_t)(fb * fb) + bu * (uint32_t)fb + bw;
+}
+
+// Sort key from the region and the direction cell (dir_cell, kept in the slot so
+// that a crossing, which keeps the direction, needs no direction to key the ray).
+__device__ __forceinline__ uint32_t sort_key(int region, int fb, uint32_t cell)
+{
+    return (uint32_t)region * 6u * (uint32_t)(fb * fb) + cell;
 }
 
 // Adds key k to a shared-memory histogram, one atomic per distinct key of the warp.
@@ -301,6 +321,7 @@ struct Ctrl {
     unsigned long long gen_live;   // ring entries left once the next spawn has run
     unsigned long long max_iter;
     unsigned int t_count;          // deferred charged-particle tracks of this iteration
+    unsigned int qlog_n;           // iterations whose queue size is in the log
 };
 
 struct State {
@@ -398,6 +419,7 @@ __global__ void init_kernel(State S, unsigned long long max_iter)
         c.gen_live = 0;
         c.max_iter = max_iter;
         c.t_count = 0;
+        c.qlog_n = 0;
     }
 }
 
@@ -445,7 +467,10 @@ __global__ void ctrl_kernel(State S, int cur, unsigned long long total, cudaGrap
     if (!c.done) {
         ctrl_step(c, cur, total);
         // queue of the iteration just planned (for measurements per query)
-        if (!c.done && c.iter <= (unsigned int)kQueueLog) S.qlog[c.iter - 1] = c.q_count[cur ^ 1];
+        if (!c.done && c.iter <= (unsigned int)kQueueLog) {
+            S.qlog[c.iter - 1] = c.q_count[cur ^ 1];
+            c.qlog_n = c.iter;
+        }
     }
     if (in_graph) cudaGraphSetConditional(loop, c.done ? 0u : 1u);
 }
@@ -548,15 +573,15 @@ __device__ __forceinline__ uint32_t spawn_one(const Params &P, const State &S, i
     float ox, oy, oz, dx, dy, dz;
     sample_birth(I, r, k0, k1, ox, oy, oz, dx, dy, dz);
     const float lam = -logf(r.u01(k0, k1));
-    Ray ry;
-    ry.o = make_float4(ox, oy, oz, 0.0f);
-    ry.d = make_float4(dx, dy, dz, __uint_as_float(ray_tag(-1, I.birth_region)));
-    Phot ph;
-    ph.f = make_float4(I.E0, lam, 0.0f, 0.0f);
-    ph.u = make_uint4(r.w, (uint32_t)local, (uint32_t)inst, 0u);
-    S.slot[slot] = Slot{ ry, ph };
+    const uint32_t cell = dir_cell(P.face_bins, dx, dy, dz);
+    Slot sl;
+    sl.a.f = make_float4(0.0f, __uint_as_float(ray_tag(-1, I.birth_region)), I.E0, lam);
+    sl.a.u = make_uint4(info_pack((uint32_t)inst, 0u, 0u, cell), 0u, __float_as_uint(0.0f), __float_as_uint(0.0f));
+    sl.b.o = make_float4(ox, oy, oz, __uint_as_float(r.w));
+    sl.b.d = make_float4(dx, dy, dz, __uint_as_float((uint32_t)local));
+    S.slot[slot] = sl;
     if (GRAD) S.score[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    const uint32_t key = sort_key(I.birth_region, P.face_bins, dx, dy, dz);
+    const uint32_t key = sort_key(I.birth_region, P.face_bins, cell);
     S.queue[cur][qpos] = slot;
     S.qkey[cur][qpos] = key;
     return key;
@@ -735,16 +760,20 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const Params P, State S, 
             if (!has && idx != 0xffffffffu) {
                 qidx = idx;
                 const Slot &sr = S.slot[queue[idx]];
-                const Ray r = sr.r;
-                const float E = sr.p.f.x, lam = sr.p.f.y;
-                const uint32_t pinst = sr.p.u.z & 0xffffu;
-                const uint32_t tag = __float_as_uint(r.d.w);
-                ox = r.o.x; oy = r.o.y; oz = r.o.z; t_min = r.o.w;
+                const float4 af = sr.a.f;
+                const uint32_t pinst = sr.a.u.x & kInstMask;
+                const float4 bo = sr.b.o, bd = sr.b.d;
+                const float E = af.z, lam = af.w;
+                const uint32_t tag = __float_as_uint(af.y);
+                t_min = af.x;
+                // the ray runs from the flight origin; surfaces count beyond the
+                // distance already travelled along it (t_min)
+                ox = bo.x; oy = bo.y; oz = bo.z;
                 exclude = (int)(tag >> kTagShift) - 1;
-                sh = make_shear_k(r.d.x, r.d.y, r.d.z);
-                ix = 1.0f / (fabsf(r.d.x) > 1e-30f ? r.d.x : copysignf(1e-30f, r.d.x));
-                iy = 1.0f / (fabsf(r.d.y) > 1e-30f ? r.d.y : copysignf(1e-30f, r.d.y));
-                iz = 1.0f / (fabsf(r.d.z) > 1e-30f ? r.d.z : copysignf(1e-30f, r.d.z));
+                sh = make_shear_k(bd.x, bd.y, bd.z);
+                ix = 1.0f / (fabsf(bd.x) > 1e-30f ? bd.x : copysignf(1e-30f, bd.x));
+                iy = 1.0f / (fabsf(bd.y) > 1e-30f ? bd.y : copysignf(1e-30f, bd.y));
+                iz = 1.0f / (fabsf(bd.z) > 1e-30f ? bd.z : copysignf(1e-30f, bd.z));
                 oix = ox * ix; oiy = oy * iy; oiz = oz * iz;
                 const int4 R = s_reg[tag & 255u];
                 t_best = INFINITY;
@@ -885,21 +914,35 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
         Track tr;
         if (mine) {
             const Hit ht = S.hit[j];
-            const Slot sl = S.slot[slot];
-            Ray ry = sl.r;
-            Phot ph = sl.p;
-            float E = ph.f.x, lam = ph.f.y, edep = ph.f.z, dep_all = ph.f.w;
-            const uint32_t local = ph.u.y;
-            inst = (int)(ph.u.z & 0xffffu);
-            uint32_t herr = (ph.u.z >> 16) & 0xffu, flags = ph.u.z >> 24, steps = ph.u.w;
-            const uint32_t tag = __float_as_uint(ry.d.w);
+            const SlotA sa = S.slot[slot].a;
+            float t_cur = sa.f.x;
+            const uint32_t tag = __float_as_uint(sa.f.y);
+            float E = sa.f.z, lam = sa.f.w;
+            float edep = __uint_as_float(sa.u.z), dep_all = __uint_as_float(sa.u.w);
+            const uint32_t info = sa.u.x;
+            inst = (int)(info & kInstMask);
+            uint32_t herr = (info >> kErrShift) & kErrMask, flags = (info >> kFlagShift) & kFlagMask;
+            uint32_t cell = info >> kCellShift, steps = sa.u.y;
             int region = (int)(tag & 255u);
             int last_tri = (int)(tag >> kTagShift) - 1;
             const float4 sc4 = GRAD ? S.score[slot] : make_float4(0, 0, 0, 0);
             float score[4] = { sc4.x, sc4.y, sc4.z, sc4.w };
             const InstDev &I = P.inst[inst];
+            // the slot's second half (flight origin, direction, random-number state),
+            // loaded only by an interaction or a waiting annihilation photon
+            bool have_b = false;
+            float4 bo = make_float4(0.0f, 0.0f, 0.0f, 0.0f), bd = bo;
+            uint32_t local = 0;
             Words r;
-            r.init(ph.u.x, I.hist_offset + local, I.inst_id);
+            auto load_b = [&]() {
+                if (have_b) return;
+                const SlotB sb = S.slot[slot].b;
+                bo = sb.o;
+                bd = sb.d;
+                local = __float_as_uint(sb.d.w);
+                r.init(__float_as_uint(sb.o.w), I.hist_offset + local, I.inst_id);
+                have_b = true;
+            };
             float esc_now = 0.0f;       // energy escaping in this segment
             if (inst != inter_inst) {
                 if (inter_acc) atomicAdd(&bt.t[inter_inst].inter, inter_acc);
@@ -933,17 +976,17 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
                 bool photon_done = false;
                 if (herr) {
                     finished = true;
-                } else if (d_int < t_hit - ry.o.w) {
+                } else if (d_int < t_hit - t_cur) {
                     // ---- interaction ----
+                    load_b();
                     ++inter_acc;
                     if (GRAD && group >= 0 && group < 4) score[group] += 1.0f / scl - mu_unit * d_int;
-                    const float tt = ry.o.w + d_int;
-                    const float px = fmaf(tt, ry.d.x, ry.o.x), py = fmaf(tt, ry.d.y, ry.o.y),
-                                pz = fmaf(tt, ry.d.z, ry.o.z);
+                    const float tt = t_cur + d_int;
+                    const float px = fmaf(tt, bd.x, bo.x), py = fmaf(tt, bd.y, bo.y), pz = fmaf(tt, bd.z, bo.z);
                     const float u = r.u01(k0, k1) * mu_unit;
                     float dep = 0.0f;
                     // charged particles of e_model 1: kinetic energy, direction, count
-                    float eT = 0.0f, eux = ry.d.x, euy = ry.d.y, euz = ry.d.z, ew = 1.0f;
+                    float eT = 0.0f, eux = bd.x, euy = bd.y, euz = bd.z, ew = 1.0f;
                     if (u < pe) {
                         if (EM) eT = E;
                         else dep = E;
@@ -974,11 +1017,11 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
                             float sp, cp;
                             sincospif(2.0f * r.u01(k0, k1), &sp, &cp);
                             const float Ep = E / x;
-                            rotate(ry.d.x, ry.d.y, ry.d.z, c, sp, cp);
+                            rotate(bd.x, bd.y, bd.z, c, sp, cp);
                             if (EM) {
                                 eT = E - Ep;
-                                const float qx = E * eux - Ep * ry.d.x, qy = E * euy - Ep * ry.d.y,
-                                            qz = E * euz - Ep * ry.d.z;
+                                const float qx = E * eux - Ep * bd.x, qy = E * euy - Ep * bd.y,
+                                            qz = E * euz - Ep * bd.z;
                                 const float ql = sqrtf(qx * qx + qy * qy + qz * qz);
                                 if (ql > 0.0f) { eux = qx / ql; euy = qy / ql; euz = qz / ql; }
                             } else {
@@ -996,7 +1039,7 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
                         const float s = sqrtf(fmaxf(0.0f, 1.0f - c * c));
                         const float nx = s * cp, ny = s * sp, nz = c;
                         E = kMeC2;
-                        ry.d.x = nx; ry.d.y = ny; ry.d.z = nz;
+                        bd.x = nx; bd.y = ny; bd.z = nz;
                         flags |= kFlagSec;
                         Sec sc;
                         sc.p = make_float4(px, py, pz, 0.0f);
@@ -1021,7 +1064,8 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
                             esc_now += e_esc;
                         }
                     }
-                    ry.o = make_float4(px, py, pz, 0.0f);
+                    bo.x = px; bo.y = py; bo.z = pz;
+                    t_cur = 0.0f;
                     last_tri = -1;
                     if (herr) finished = true;
                     else if (!photon_done) lam = -logf(r.u01(k0, k1));
@@ -1033,10 +1077,10 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
                     if (herr) finished = true;
                 } else {
                     // ---- boundary crossing ----
-                    const float len = t_hit - ry.o.w;
+                    const float len = t_hit - t_cur;
                     lam -= mu * len;
                     if (GRAD && group >= 0 && group < 4) score[group] -= mu_unit * len;
-                    ry.o.w = t_hit;
+                    t_cur = t_hit;
                     last_tri = hit_tri;
                     region = entering ? hit_region : s_reg[hit_region].z;
                 }
@@ -1050,11 +1094,13 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
                 }
                 if (photon_done && !finished) {
                     if (flags & kFlagSec) {
+                        load_b();
                         const Sec sc = S.sec[slot];
                         flags &= ~kFlagSec;
                         region = __float_as_int(sc.d.w);
-                        ry.o = make_float4(sc.p.x, sc.p.y, sc.p.z, 0.0f);
-                        ry.d.x = sc.d.x; ry.d.y = sc.d.y; ry.d.z = sc.d.z;
+                        bo.x = sc.p.x; bo.y = sc.p.y; bo.z = sc.p.z;
+                        t_cur = 0.0f;
+                        bd.x = sc.d.x; bd.y = sc.d.y; bd.z = sc.d.z;
                         last_tri = -1;
                         E = kMeC2;
                         lam = -logf(r.u01(k0, k1));
@@ -1062,7 +1108,7 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
                         finished = true;
                     }
                 }
-                if (!finished && !(isfinite(ry.d.x) && isfinite(E) && isfinite(lam))) {
+                if (!finished && !((!have_b || isfinite(bd.x)) && isfinite(E) && isfinite(lam))) {
                     herr |= ERR_NONFINITE;
                     finished = true;
                 }
@@ -1070,12 +1116,21 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
             herr_out = herr;
             edep_out = edep;
             if (!finished) {
-                ry.d.w = __uint_as_float(ray_tag(last_tri, region));
-                ph.f = make_float4(E, lam, edep, dep_all);
-                ph.u = make_uint4(r.w, local, (uint32_t)inst | (herr << 16) | (flags << 24), steps);
-                S.slot[slot] = Slot{ ry, ph };
+                // a crossing keeps the direction (and its key cell) and the second half
+                if (have_b) cell = dir_cell(P.face_bins, bd.x, bd.y, bd.z);
+                SlotA na;
+                na.f = make_float4(t_cur, __uint_as_float(ray_tag(last_tri, region)), E, lam);
+                na.u = make_uint4(info_pack((uint32_t)inst, herr, flags, cell), steps, __float_as_uint(edep),
+                                  __float_as_uint(dep_all));
+                S.slot[slot].a = na;
+                if (have_b) {
+                    SlotB nb;
+                    nb.o = make_float4(bo.x, bo.y, bo.z, __uint_as_float(r.w));
+                    nb.d = make_float4(bd.x, bd.y, bd.z, __uint_as_float(local));
+                    S.slot[slot].b = nb;
+                }
                 if (GRAD) S.score[slot] = make_float4(score[0], score[1], score[2], score[3]);
-                key = sort_key(region, P.face_bins, ry.d.x, ry.d.y, ry.d.z);
+                key = sort_key(region, P.face_bins, cell);
                 alive_slot = true;
             } else {
                 float esc = 0.0f;
@@ -1086,8 +1141,11 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
                 } else {
                     fep_out = fep; dep_all_out = dep_all; esc_out = esc; segs_out = steps;
                 }
-                const unsigned long long g = (inst ? P.inst_end[inst - 1] : 0ull) + local;
-                if (g < P.n_trace) P.edep_trace[g] = herr ? -1.0f : edep;
+                if (P.n_trace) {
+                    const uint32_t loc = have_b ? local : __float_as_uint(S.slot[slot].b.d.w);
+                    const unsigned long long g = (inst ? P.inst_end[inst - 1] : 0ull) + loc;
+                    if (g < P.n_trace) P.edep_trace[g] = herr ? -1.0f : edep;
+                }
             }
         }
         if (!GRAD) bt.history_warp(finished, inst, segs_out, herr_out, fep_out, edep_out, dep_all_out, esc_out, P.e_max);
@@ -1160,17 +1218,17 @@ __global__ void __launch_bounds__(256) etrack_kernel(const Params P, State S, un
         uint32_t herr = 0;
         e_track<COUNT>(P, s_reg, P.inst[inst].scale, t.p.x, t.p.y, t.p.z, t.u.x, t.u.y, t.u.z, t.p.w, t.u.w, region,
                        edep, dep_all, esc, herr, ts);
-        Phot &ph = S.slot[t.slot].p;
-        ph.f.z += edep;
-        ph.f.w += dep_all;
-        uint32_t uz = ph.u.z;
+        SlotA &a = S.slot[t.slot].a;
+        uint4 u = a.u;
+        u.z = __float_as_uint(__uint_as_float(u.z) + edep);
+        u.w = __float_as_uint(__uint_as_float(u.w) + dep_all);
         if (esc != 0.0f) {
-            const bool had = ((uz >> 24) & kFlagEsc) != 0u;
+            const bool had = ((u.x >> kFlagShift) & kFlagEsc) != 0u;
             S.esc[t.slot] = (had ? S.esc[t.slot] : 0.0f) + esc;
-            uz |= (uint32_t)kFlagEsc << 24;
+            u.x |= (uint32_t)kFlagEsc << kFlagShift;
         }
-        uz |= (herr & 0xffu) << 16;
-        ph.u.z = uz;
+        u.x |= (herr & kErrMask) << kErrShift;
+        a.u = u;
     }
     if (COUNT) {
         if (ts.nodes) atomicAdd(&counters[0], (unsigned long long)ts.nodes);
@@ -1515,7 +1573,7 @@ gadep_status wavefront_queue_log(WavefrontBuffers *w, uint32_t *out, int max, in
     cudaError_t e = cudaMemcpyAsync(w->host_ctrl, w->S.ctrl, sizeof(wf::Ctrl), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(GADEP_E_CUDA, "wavefront: queue log: %s", cudaGetErrorString(e));
-    const int iters = (int)std::min<unsigned int>(w->host_ctrl->iter, (unsigned int)wf::kQueueLog);
+    const int iters = (int)std::min<unsigned int>(w->host_ctrl->qlog_n, (unsigned int)wf::kQueueLog);
     const int k = std::max(0, std::min(iters, max));
     if (k > 0) {
         e = cudaMemcpyAsync(out, w->S.qlog, sizeof(uint32_t) * (size_t)k, cudaMemcpyDeviceToHost, s);
