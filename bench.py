@@ -222,6 +222,29 @@ def measure_forms(dev, scale=1.0):
                       "batched_vs_plain": t_plain / t_batch, "autotuned": kw, "batched_form": how,
                       "autotune_ms": [[k, round(v, 3)] for k, v in table],
                       "fepe_first": res[0]["fepe"], "n_err": sum(r["n_err"] for r in res)}
+    del g
+    # the same comparison end to end through the public calls a user makes, host
+    # buffers: 120 gadep_run calls (each stages its tables and instance, runs and
+    # reads its spectrum back) against one gadep_run_batch call with the autotuned
+    # options; wall-clock seconds after one warm-up call of each
+    ob = api.make_opts(**kw)
+    api.gadep_run(b3, mats, items[0][1], items[0][0], items[0][2], instance=items[0][3],
+                  opts=api.make_opts(group_scale=items[0][4]))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for E, src, n, iid, sc in items:
+        api.gadep_run(b3, mats, src, E, n, instance=iid, opts=api.make_opts(group_scale=sc))
+    torch.cuda.synchronize()
+    e2e_plain = time.perf_counter() - t0
+    inst3 = api.make_instances(items)
+    api.gadep_run_batch(b3, mats, inst3, ob)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    api.gadep_run_batch(b3, mats, inst3, ob)
+    torch.cuda.synchronize()
+    e2e_batch = time.perf_counter() - t0
+    out["batched"]["e2e"] = {"plain_s": e2e_plain, "batched_s": e2e_batch, "batched_vs_plain": e2e_plain / e2e_batch,
+                             "note": "wall clock: 120 gadep_run calls vs one gadep_run_batch call, host buffers"}
     # ---- gradient ----
     m4 = api.detmesh_build(W.GRAD_DET)
     b4 = api.gadep_bvh_build(m4, dev)
