@@ -16,6 +16,15 @@
  * Profiles are walked with the solid's outward normal on the left of the
  * walking direction (rho to the right, z up); each profile segment becomes a
  * band of N_theta quads (two triangles) or a fan when one end is on the axis.
+ * A segment from the axis to a ring in the same plane (a flat end face; the
+ * paper does not say how such a face is cut into triangles) is cut into
+ * concentric rings instead of a fan of slivers that all meet at the centre:
+ * ring k at radius R - k w, w = 4 (2 pi R / N_theta) (four times the arc between
+ * the outer ring's vertices), with max(8, round(N_theta (R - k w) / R)) vertices
+ * at angles 2 pi i / count, for k = 1, 2, ... while the radius is at least w and
+ * the count falls; consecutive rings are joined by walking around them by angle,
+ * and the innermost ring closes with a fan at the centre.  The face is the same
+ * plane polygon, so volumes and the surface are unchanged.
  *
  * Coaxial detector layout (Table 2 parameters, Sec. 2.3.2):
  *   solid 0  endcap (Al)            cylinder R = d1, z in [-d7, 0]
@@ -78,6 +87,52 @@ static void add_tri(builder *b, int a, int c, int d, int solid)
     b->n_tri++;
 }
 
+/* Triangles joining ring A (na vertices from a0) to ring B (nb from b0), both
+   starting at angle 0, oriented like the quad band (A_i, B_i, A_i+1),
+   (A_i+1, B_i, B_i+1): around the rings by angle, stepping along A unless B's
+   next vertex comes strictly first. */
+static void join_rings(builder *b, int solid, int a0, int na, int b0, int nb)
+{
+    int i = 0, j = 0;
+    while (i < na || j < nb) {
+        int step_a;
+        if (i == na) step_a = 0;
+        else if (j == nb) step_a = 1;
+        else step_a = (double)(i + 1) * nb <= (double)(j + 1) * na;   /* next angle of A <= next of B */
+        if (step_a) {
+            add_tri(b, a0 + i % na, b0 + j % nb, a0 + (i + 1) % na, solid);
+            ++i;
+        } else {
+            add_tri(b, a0 + i % na, b0 + j % nb, b0 + (j + 1) % nb, solid);
+            ++j;
+        }
+    }
+}
+
+/* The inner rings of a flat end face whose outer ring has radius R and N
+   vertices (header comment): appends their vertices, stores each ring's first
+   vertex and count (at most 64 rings) and returns how many there are. */
+static int disk_rings(builder *b, double R, double zf, int N, int *first, int *count)
+{
+    const double w = 4.0 * (2.0 * ORC_PI * R / (double)N);
+    int k_rings = 0, prev = N;
+    for (int k = 1; k < 64; ++k) {
+        double r = R - (double)k * w;
+        long m = lround((double)N * r / R);
+        if (m < 8) m = 8;
+        if (r < w || m >= prev) break;
+        first[k_rings] = b->n_vert;
+        count[k_rings] = (int)m;
+        for (int i = 0; i < m; ++i) {
+            double th = 2.0 * ORC_PI * (double)i / (double)m;
+            add_vertex(b, r * cos(th), r * sin(th), zf);
+        }
+        prev = (int)m;
+        ++k_rings;
+    }
+    return k_rings;
+}
+
 /* Revolve a profile of np points (rho, z); rho == 0 marks an axis point. */
 static void revolve(builder *b, int solid, const double *rho, const double *z, int np, int N)
 {
@@ -95,6 +150,25 @@ static void revolve(builder *b, int solid, const double *rho, const double *z, i
     }
     for (int k = 0; k + 1 < np; ++k) {
         int ra = rho[k] != 0.0, rb = rho[k + 1] != 0.0;
+        if (ra != rb && z[k] == z[k + 1]) {
+            /* flat end face: rings from the outer one inward, then the centre fan */
+            int rf[64], rc[64];
+            const int kr = ra ? k : k + 1, kc = ra ? k + 1 : k;
+            const int nr = disk_rings(b, rho[kr], z[kr], N, rf, rc);
+            int o0 = first[kr], on = N;
+            for (int q = 0; q < nr; ++q) {
+                if (ra) join_rings(b, solid, o0, on, rf[q], rc[q]);       /* ring first, then inward */
+                else join_rings(b, solid, rf[q], rc[q], o0, on);          /* axis first: inner ring is A */
+                o0 = rf[q];
+                on = rc[q];
+            }
+            for (int i = 0; i < on; ++i) {
+                int i1 = (i + 1) % on;
+                if (ra) add_tri(b, o0 + i, first[kc], o0 + i1, solid);
+                else add_tri(b, first[kc], o0 + i, o0 + i1, solid);
+            }
+            continue;
+        }
         for (int i = 0; i < N; ++i) {
             int i1 = (i + 1) % N;
             if (ra && rb) {

@@ -58,10 +58,75 @@ Ring make_ring(Surface &s, double rho, double z, int n_theta)
     return Ring{ first, false };
 }
 
-// Band of quads between two consecutive rings (a fan if one is an axis vertex).
-// Quads are split along the (a_i, b_{i+1}) diagonal.
+// Triangles between ring P (n_p vertices from p0) and ring Q (n_q from q0), both
+// starting at angle 0: walking around by angle, each step takes the ring whose
+// next vertex comes first.  With n_p == n_q this is the quad band split along
+// (P_i, Q_{i+1}), with the same orientation.
+void merge_rings(Surface &s, int p0, int n_p, int q0, int n_q)
+{
+    int i = 0, j = 0;
+    while (i < n_p || j < n_q) {
+        const double tp = (double)(i + 1) / n_p, tq = (double)(j + 1) / n_q;
+        if (j < n_q && (i == n_p || tq <= tp)) {
+            s.tri(p0 + i % n_p, q0 + (j + 1) % n_q, q0 + j % n_q);
+            ++j;
+        } else {
+            s.tri(p0 + i % n_p, p0 + (i + 1) % n_p, q0 + j % n_q);
+            ++i;
+        }
+    }
+}
+
+// A flat disk face (axis vertex c and ring r of n vertices in one plane) as
+// concentric rings instead of a fan of n slivers meeting at the centre: rings
+// inward at a spacing of kDiskAspect times the arc between the outer ring's
+// vertices, each with vertices in proportion to its radius (at least
+// kDiskMinRing), and a small fan at the centre.  The same surface, without
+// n triangles whose boxes all contain the centre.
+constexpr double kDiskAspect = 4.0;
+constexpr int kDiskMinRing = 8;
+
+void flat_disk(Surface &s, int c, int r0, int n, bool centre_first)
+{
+    const double z = s.v[3 * (size_t)r0 + 2];
+    const double R = std::hypot(s.v[3 * (size_t)r0], s.v[3 * (size_t)r0 + 1]);
+    const double w = kDiskAspect * 2.0 * kPi * R / n;
+    int prev = r0, n_prev = n;
+    for (int k = 1;; ++k) {
+        const double rho = R - k * w;
+        const int m = std::max(kDiskMinRing, (int)std::lround(n * rho / R));
+        if (rho < w || m >= n_prev) break;
+        const int first = (int)(s.v.size() / 3);
+        for (int i = 0; i < m; ++i) {
+            const double th = 2.0 * kPi * i / m;
+            s.add(rho * std::cos(th), rho * std::sin(th), z);
+        }
+        // the outer ring plays the role it has in stitch(): Q (second) when the
+        // centre comes first in the profile, P (first) otherwise
+        if (centre_first) merge_rings(s, first, m, prev, n_prev);
+        else merge_rings(s, prev, n_prev, first, m);
+        prev = first;
+        n_prev = m;
+    }
+    for (int i = 0; i < n_prev; ++i) {
+        const int j = (i + 1) % n_prev;
+        if (centre_first) s.tri(c, prev + j, prev + i);
+        else s.tri(prev + i, prev + j, c);
+    }
+}
+
+// Band of quads between two consecutive rings (a fan if one is an axis vertex;
+// a flat disk of concentric rings when the axis vertex and the ring lie in one
+// plane).  Quads are split along the (a_i, b_{i+1}) diagonal.
 void stitch(Surface &s, const Ring &a, const Ring &b, int n_theta)
 {
+    if (a.axis != b.axis) {
+        const int c = a.axis ? a.first : b.first, r = a.axis ? b.first : a.first;
+        if (s.v[3 * (size_t)c + 2] == s.v[3 * (size_t)r + 2]) {
+            flat_disk(s, c, r, n_theta, a.axis);
+            return;
+        }
+    }
     for (int i = 0; i < n_theta; ++i) {
         int j = (i + 1) % n_theta;
         if (!a.axis && !b.axis) {

@@ -48,6 +48,40 @@ def rounded_profile(R, rch, zf, zb, n_phi):
     return pts
 
 
+def disk_rings(R, N):
+    """Inner ring (radius, vertex count) of a flat end face whose outer ring has
+    radius R and N vertices: spacing w = 4 arcs of the outer ring, vertices in
+    proportion to the radius (at least 8), while the radius is at least w and the
+    count falls."""
+    w = 4.0 * (2.0 * math.pi * R / N)
+    rings, prev, k = [], N, 1
+    while k < 64:
+        r = R - k * w
+        m = max(8, int(math.floor(N * r / R + 0.5)))
+        if r < w or m >= prev:
+            break
+        rings.append((r, m))
+        prev, k = m, k + 1
+    return rings
+
+
+def profile_tris(profile, N):
+    """Triangles of a revolved profile: 2N per band between rings, N per fan to
+    an axis point off the ring's plane, and for a flat end face the bands
+    between its rings (as many triangles as the two rings have vertices) plus
+    the centre fan of the innermost ring."""
+    n = 0
+    for (ra, za), (rb, zb) in zip(profile[:-1], profile[1:]):
+        if ra > 0 and rb > 0:
+            n += 2 * N
+        elif (ra > 0) != (rb > 0) and za == zb:
+            counts = [N] + [m for _, m in disk_rings(max(ra, rb), N)]
+            n += sum(a + b for a, b in zip(counts[:-1], counts[1:])) + counts[-1]
+        elif (ra > 0) != (rb > 0):
+            n += N
+    return n
+
+
 def test_bare_cylinder_counts_volume_topology(orc):
     m = det(orc, W.BARE_CYLINDER)
     assert (m.n_vert, m.n_tri, m.n_solid) == (98, 192, 1)
@@ -107,8 +141,29 @@ def test_coax_solids(orc):
     smooth = math.pi * R * R * L - (1 - math.pi / 4) * rch * rch * 2 * math.pi * (R - rch * (
         (10 - 3 * math.pi) / (12 - 3 * math.pi)))
     assert m.volume(3) == pytest.approx(smooth, rel=2e-3)
-    # triangle budget: 2N(Nphi+2) per rounded crystal solid, 2N(Nphi+1) per bore solid
-    assert m.n_tri == 2 * 4 * N + 8 * N + 2 * 2 * N * (nphi + 2) + 2 * 2 * N * (nphi + 1)
+    # triangle budget of the revolved profiles, flat end faces as concentric rings
+    assert m.n_tri == sum(profile_tris(prof, N) for prof in profiles.values())
+    # each flat end face is the plane N-gon: its triangles cover exactly its area,
+    # and its inner vertices sit on the rings of the stated rule
+    xyz, tri, ts, solids = m.arrays()
+    v = xyz[tri]
+    area = 0.5 * np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0])
+    for s, prof in profiles.items():
+        for (ra, za), (rb, zb) in zip(prof[:-1], prof[1:]):
+            if (ra > 0) == (rb > 0) or za != zb:
+                continue
+            Rf = max(ra, rb)
+            face = (ts == s) & np.all(np.abs(v[:, :, 2] - za) < 1e-9, axis=1)
+            assert np.abs(area[face, 2]).sum() == pytest.approx(0.5 * N * Rf * Rf * math.sin(2 * math.pi / N),
+                                                                rel=1e-10), (s, za)
+            fv = xyz[np.unique(tri[face])]
+            rad = np.hypot(fv[:, 0], fv[:, 1])
+            for r, mcount in disk_rings(Rf, N):
+                assert np.sum(np.abs(rad - r) < 1e-9) == mcount, (s, za, r)
+            # no sliver: every triangle's box is within a small multiple of its area
+            box = np.ptp(v[face][:, :, 0], axis=1) * np.ptp(v[face][:, :, 1], axis=1)
+            if disk_rings(Rf, N):
+                assert np.max(box / np.abs(area[face, 2])) < 40, (s, za)
     xyz, tri, ts, solids = m.arrays()
     assert list(solids["parent"]) == [-1, 0, 1, 1, 3, 4, 5]
     assert list(solids["material"]) == [W.MAT_AL, W.MAT_VACUUM, W.MAT_CU, W.MAT_GE, W.MAT_GE,
@@ -120,9 +175,12 @@ def test_coax_solids(orc):
         phi = 0.5 * math.pi * j / nphi
         rho = (R - rch) + rch * math.cos(phi)
         z = zf - rch * (1 - math.sin(phi))
-        sel = np.isclose(cx[:, 2], z, atol=1e-12) & (np.hypot(cx[:, 0], cx[:, 1]) > 0)
+        # the outermost ring at height z_j (the front face's inner rings share z_N_phi)
+        at = np.isclose(cx[:, 2], z, atol=1e-12)
+        rad = np.hypot(cx[at, 0], cx[at, 1])
+        sel = rad > rad.max() - 1e-9
         assert sel.sum() == N
-        assert np.allclose(np.hypot(cx[sel, 0], cx[sel, 1]), rho, atol=1e-12)
+        assert np.allclose(rad[sel], rho, atol=1e-12)
 
 
 def test_parity_rule_locates_known_points(orc):
@@ -241,14 +299,15 @@ def test_detector2_triangle_counts_in_the_paper_range(orc):
     4416 at (N_theta, N_phi) = (32, 10) and 13440 at (64, 20).  The paper does not
     list the components behind them, so they bound a sanity range, not an exact
     value: ours (endcap, holder cup, crystal, active volume, bore contact and
-    bore vacuum) are within 30 % of both and grow by a similar factor."""
+    bore vacuum, flat end faces as concentric rings at 64 segments) are within 30 %
+    of both and grow by a similar factor."""
     import dataclasses
     counts = []
     for (nt, nphi), paper in (((32, 10), 4416), ((64, 20), 13440)):
         m = det(orc, dataclasses.replace(W.DET2, n_theta=nt, n_phi=nphi))
         counts.append(m.n_tri)
         assert 0.7 * paper <= m.n_tri <= 1.3 * paper, (nt, nphi, m.n_tri, paper)
-    assert counts == [3456, 12032]
+    assert counts == [3456, 12968]
     assert 0.7 * 13440 / 4416 <= counts[1] / counts[0] <= 1.3 * 13440 / 4416
 
 

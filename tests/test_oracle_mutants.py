@@ -161,6 +161,15 @@ MUTANTS = [
      "double th = 2.0 * ORC_PI * (double)i / (double)N;\n                add_vertex(b, rho[k]",
      "double th = 2.0 * ORC_PI * ((double)i + 0.5) / (double)N;\n                add_vertex(b, rho[k]",
      ("test_oracle_mesh", "test_bare_cylinder_counts_volume_topology"), None),
+    ("disk_ring_spacing", "orc_mesh.c", "const double w = 4.0 * (2.0 * ORC_PI * R / (double)N);",
+     "const double w = 3.0 * (2.0 * ORC_PI * R / (double)N);",
+     ("test_oracle_mesh", "test_coax_solids"), None),
+    ("disk_ring_count_off_by_one", "orc_mesh.c", "long m = lround((double)N * r / R);",
+     "long m = lround((double)N * r / R) + 1;",
+     ("test_oracle_mesh", "test_coax_solids"), None),
+    ("disk_band_winding", "orc_mesh.c", "add_tri(b, a0 + i % na, b0 + j % nb, a0 + (i + 1) % na, solid);",
+     "add_tri(b, a0 + i % na, a0 + (i + 1) % na, b0 + j % nb, solid);",
+     ("test_oracle_mesh", "test_coax_solids"), None),
 ]
 
 
