@@ -47,7 +47,7 @@ FLOP_PER_BOX = 18.0
 FLOP_PER_TRI = 45.0
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-NODE_BYTES, TRI_BYTES = 128, 48       # 4-wide BVH node record; three float4 vertices of a triangle
+NODE_BYTES, TRI_BYTES = 64, 48        # 4-wide BVH node (quantised child boxes); three float4 vertices
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -622,7 +622,7 @@ def main():
     # nearest-hit queries: every segment but the one of a history that ends at birth
     # (born in the world aimed away from the scene box), which is counted without a query
     queries = segs - sum(f["culled"] for f in fepe)
-    # algorithmic node and triangle bytes of the traversal (128 B per node visit, 48 B per
+    # algorithmic node and triangle bytes of the traversal (64 B per node visit, 48 B per
     # triangle test), served by L1 and L2, per second of the dominant kernel
     l1l2_gbs = (NODE_BYTES * nodes + TRI_BYTES * tris) * args.steps / (dom_ms / 1e3) / 1e9
     # the timed plans hold the mesh's cached wavefront buffers; release them so the

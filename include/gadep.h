@@ -205,7 +205,8 @@ typedef struct {
 } gadep_bvh_stats;
 
 /* Binned-SAH BVH over all triangles of the mesh (the tree the paper's Gadep uses
- * to accelerate triangle queries, Sec. 2.4.3), compacted to 64-byte nodes and
+ * to accelerate triangle queries, Sec. 2.4.3), compacted to 64-byte 4-wide nodes
+ * (child boxes quantised to 7 bits on each node's own grid, rounded outward) and
  * 48-byte triangle records, copied to `device`: one tree over every triangle and
  * one per region (the triangles a photon in that region can reach first).  The
  * mesh may be destroyed afterwards.  device = -1 builds the host copy only

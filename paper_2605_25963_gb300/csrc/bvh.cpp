@@ -9,11 +9,13 @@
 // Optionally (split_alpha > 0) spatial splits cut triangle references too.
 // The costs, the leaf limit and the split threshold are build options
 // (gadep_bvh_opts); C_trav = 1.5 C_tri measured fastest on the coaxial meshes.
-// The binary tree is then collapsed into the 128-byte 4-wide node layout
+// The binary tree is then collapsed into the 64-byte 4-wide node layout
 // documented in gadep_internal.h (the four child boxes stored in the parent,
-// depth-first order) with the triangles reordered so that every leaf is one
-// contiguous run of 48-byte triangles.  A wide node halves the dependent node
-// steps of a query and gives each step four independent box tests.
+// quantised to 7 bits on the node's own grid, depth-first order) with the
+// triangles reordered so that every leaf is one contiguous run of 48-byte
+// triangles.  A wide node halves the dependent node steps of a query and gives
+// each step four independent box tests; quantising its boxes halves the bytes
+// each step loads.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -451,6 +453,61 @@ void pad_box(const AABB &b, float out_lo[3], float out_hi[3])
     }
 }
 
+// Word layout of a quantised node (see gadep_internal.h).
+constexpr int kWordS[3] = { 3, 14, 15 };      // S per axis
+constexpr int kWordLo[3] = { 8, 10, 12 };     // low-plane bytes per axis; high planes follow
+constexpr int kQMax = 127;
+
+// Quantise the padded boxes of a node's n children onto the node's own grid
+// and write the node's 16 words: per axis the base b (rounded down so that
+// b + S lies at or below every low plane), the grid step s (a power of two,
+// the smallest with 127 s spanning the children) and per child the low plane
+// rounded down and the high plane rounded up to the grid.  All of it is exact
+// in FP64 (floats, powers of two and small integer multiples of them).
+void quantise_node(int n, const float lo[4][3], const float hi[4][3], const int32_t child[4],
+                   float f[kNodeFloats])
+{
+    uint32_t u[kNodeFloats] = {};
+    for (int k = 0; k < 3; ++k) {
+        double p = INFINITY, top = -INFINITY;
+        for (int c = 0; c < n; ++c) {
+            p = std::min(p, (double)lo[c][k]);
+            top = std::max(top, (double)hi[c][k]);
+        }
+        int e = 0;
+        std::frexp((top - p) / kQMax, &e);    // 2^e >= (top - p) / 127
+        double s, S, base;
+        float b;
+        for (;;) {
+            s = std::ldexp(1.0, e);
+            S = 128.0 * s;
+            b = round_down(p - S);
+            base = (double)b + S;     // the plane of q = 0
+            if (base <= p && top - base <= kQMax * s) break;
+            ++e;
+        }
+        const float Sf = (float)S;
+        std::memcpy(&u[k], &b, 4);
+        std::memcpy(&u[kWordS[k]], &Sf, 4);
+        uint32_t wl = 0, wh = 0;
+        for (int c = 0; c < 4; ++c) {
+            int ql = kQMax, qh = 0;            // empty slot: inverted box
+            if (c < n) {
+                ql = (int)std::floor(((double)lo[c][k] - base) / s);
+                qh = (int)std::ceil(((double)hi[c][k] - base) / s);
+                ql = std::max(0, std::min(ql, kQMax));
+                qh = std::max(0, std::min(qh, kQMax));
+            }
+            wl |= (uint32_t)(128 + ql) << (8 * c);
+            wh |= (uint32_t)(128 + qh) << (8 * c);
+        }
+        u[kWordLo[k]] = wl;
+        u[kWordLo[k] + 1] = wh;
+    }
+    std::memcpy(&u[4], child, 16);
+    std::memcpy(f, u, sizeof(u));
+}
+
 }  // namespace
 
 namespace gadep {
@@ -563,25 +620,12 @@ int32_t append_tree(const detmesh_mesh *m, const std::vector<int32_t> &ids, cons
     for (const int32_t bn : order) {
         int32_t kids[4];
         const int n = collapse(bn, kids);
-        float f[kNodeFloats];
-        int32_t w[8] = { 0, 0, 0, 0, n, 0, 0, 0 };
+        int32_t w[4] = { kEmptyChild, kEmptyChild, kEmptyChild, kEmptyChild };
+        float lo[4][3], hi[4][3];
         ts.sah += B.nodes[bn].leaf() ? 0.0 : B.nodes[bn].box.area() / root_area * o.c_trav;
-        for (int c = 0; c < 4; ++c) {
-            if (c >= n) {
-                // empty slot: a box at +infinity on every axis, which the slab test of
-                // any ray misses (both planes of an axis give the same infinite
-                // distance), holding a leaf of no triangles
-                for (int k = 0; k < 6; ++k) f[4 * k + c] = INFINITY;
-                w[c] = leaf_ref(0, 0);
-                continue;
-            }
+        for (int c = 0; c < n; ++c) {
             const BNode &ch = B.nodes[kids[c]];
-            float lo[3], hi[3];
-            pad_box(ch.box, lo, hi);
-            for (int k = 0; k < 3; ++k) {
-                f[8 * k + c] = lo[k];
-                f[8 * k + 4 + c] = hi[k];
-            }
+            pad_box(ch.box, lo[c], hi[c]);
             if (ch.leaf()) {
                 w[c] = leaf_ref(tri_base + ch.start, ch.count);
                 ts.leaves++;
@@ -591,7 +635,8 @@ int32_t append_tree(const detmesh_mesh *m, const std::vector<int32_t> &ids, cons
                 w[c] = dev_of[kids[c]];
             }
         }
-        std::memcpy(&f[24], w, 32);
+        float f[kNodeFloats];
+        quantise_node(n, lo, hi, w, f);
         out->nodes.insert(out->nodes.end(), f, f + kNodeFloats);
     }
     return node_base;
@@ -697,6 +742,31 @@ gadep_status build_bvh_host(const detmesh_mesh *m, const gadep_bvh_opts &o, gade
 
 }  // namespace gadep
 
+namespace gadep {
+
+void decode_node(const float *f, WideNode &out)
+{
+    uint32_t u[kNodeFloats];
+    std::memcpy(u, f, sizeof(u));
+    std::memcpy(out.child, &u[4], 16);
+    out.n = 0;
+    for (int c = 0; c < 4; ++c) out.n += out.child[c] != kEmptyChild;
+    for (int k = 0; k < 3; ++k) {
+        float b, S;
+        std::memcpy(&b, &u[k], 4);
+        std::memcpy(&S, &u[kWordS[k]], 4);
+        const double s = (double)S / 128.0, base = (double)b + (double)S;
+        for (int c = 0; c < 4; ++c) {
+            const int ql = (int)((u[kWordLo[k]] >> (8 * c)) & 0xffu) - 128;
+            const int qh = (int)((u[kWordLo[k] + 1] >> (8 * c)) & 0xffu) - 128;
+            out.lo[c][k] = base + ql * s;
+            out.hi[c][k] = base + qh * s;
+        }
+    }
+}
+
+}  // namespace gadep
+
 extern "C" void gadep_bvh_opts_default(gadep_bvh_opts *o)
 {
     if (!o) return;
@@ -721,43 +791,52 @@ namespace {
 
 struct LeafBox { int32_t id, rec; float lo[3], hi[3]; };   // mesh triangle, its record
 
-// Walk one tree: child boxes inside the box the parent stores, every leaf box
-// meeting the bounding box of each triangle it holds, no triangle twice in one
-// leaf; append (mesh triangle id, leaf box) for every triangle record.
+// Walk one tree: every stored child box non-empty, empty slots empty, no
+// triangle twice in one leaf, every leaf's box meeting the bounding box of each
+// triangle it holds; append (mesh triangle id, box) for every triangle record,
+// the box being the intersection of the leaf's box with those of all its
+// ancestors (the region a ray must pass every box test of to reach the leaf).
 gadep_status walk_tree(const gadep_bvh *b, int32_t root, std::vector<LeafBox> &out)
 {
     const int32_t nn = b->stats.n_nodes;
     const int32_t ns = (int32_t)(b->tris.size() / 12);
-    struct Item { int32_t node; float lo[3], hi[3]; };
+    struct Item { int32_t node; double lo[3], hi[3]; };
     std::vector<Item> stack;
     stack.push_back(Item{ root, { -INFINITY, -INFINITY, -INFINITY }, { INFINITY, INFINITY, INFINITY } });
     int64_t visited = 0;
+    gadep::WideNode wn;
     while (!stack.empty()) {
         Item it = stack.back();
         stack.pop_back();
         if (it.node < 0 || it.node >= nn || ++visited > nn)
             return gadep::fail(GADEP_E_MESH, "bvh: bad node index %d", it.node);
-        const float *f = &b->nodes[(size_t)it.node * kNodeFloats];
-        int32_t w[8];
-        std::memcpy(w, &f[24], 32);
-        if (w[4] < 1 || w[4] > 4) return gadep::fail(GADEP_E_MESH, "bvh: node %d has %d children", it.node, w[4]);
+        gadep::decode_node(&b->nodes[(size_t)it.node * kNodeFloats], wn);
+        if (wn.n < 1) return gadep::fail(GADEP_E_MESH, "bvh: node %d has no children", it.node);
         for (int c = 0; c < 4; ++c) {
-            const float lo[3] = { f[c], f[8 + c], f[16 + c] };
-            const float hi[3] = { f[4 + c], f[12 + c], f[20 + c] };
-            if (c >= w[4]) {
-                if (w[c] >= 0 || ((~w[c]) & 7) != 0 || lo[0] != INFINITY || hi[0] != INFINITY || lo[1] != INFINITY ||
-                    hi[1] != INFINITY || lo[2] != INFINITY || hi[2] != INFINITY)
+            const int32_t wc = wn.child[c];
+            if (c >= wn.n) {
+                bool inverted = true;
+                for (int k = 0; k < 3; ++k) inverted = inverted && wn.lo[c][k] > wn.hi[c][k];
+                if (wc != kEmptyChild || !inverted)
                     return gadep::fail(GADEP_E_MESH, "bvh: empty slot of node %d is not empty", it.node);
                 continue;
             }
-            for (int k = 0; k < 3; ++k)
-                if (lo[k] < it.lo[k] || hi[k] > it.hi[k] || lo[k] > hi[k])
-                    return gadep::fail(GADEP_E_MESH, "bvh: child box of node %d not inside its parent", it.node);
-            if (w[c] >= 0) {
-                stack.push_back(Item{ w[c], { lo[0], lo[1], lo[2] }, { hi[0], hi[1], hi[2] } });
+            double lo[3], hi[3];
+            for (int k = 0; k < 3; ++k) {
+                if (wn.lo[c][k] > wn.hi[c][k])
+                    return gadep::fail(GADEP_E_MESH, "bvh: child box of node %d is empty", it.node);
+                lo[k] = std::max(wn.lo[c][k], it.lo[k]);
+                hi[k] = std::min(wn.hi[c][k], it.hi[k]);
+                if (lo[k] > hi[k])
+                    return gadep::fail(GADEP_E_MESH, "bvh: child box of node %d outside its parent", it.node);
+            }
+            if (wc >= 0) {
+                stack.push_back(Item{ wc, { lo[0], lo[1], lo[2] }, { hi[0], hi[1], hi[2] } });
                 continue;
             }
-            const int32_t first = (~w[c]) >> 3, cnt = (~w[c]) & 7;
+            float flo[3], fhi[3];
+            for (int k = 0; k < 3; ++k) { flo[k] = round_down(lo[k]); fhi[k] = round_up(hi[k]); }
+            const int32_t first = (~wc) >> 3, cnt = (~wc) & 7;
             if (first < 0 || cnt < 1 || first + cnt > ns) return gadep::fail(GADEP_E_MESH, "bvh: bad leaf range");
             for (int32_t t = first; t < first + cnt; ++t) {
                 int32_t id;
@@ -774,7 +853,7 @@ gadep_status walk_tree(const gadep_bvh *b, int32_t root, std::vector<LeafBox> &o
                     }
                     if (vhi < lo[k] || vlo > hi[k]) return gadep::fail(GADEP_E_MESH, "bvh: leaf box misses its triangle");
                 }
-                out.push_back(LeafBox{ id, t, { lo[0], lo[1], lo[2] }, { hi[0], hi[1], hi[2] } });
+                out.push_back(LeafBox{ id, t, { flo[0], flo[1], flo[2] }, { fhi[0], fhi[1], fhi[2] } });
             }
         }
     }

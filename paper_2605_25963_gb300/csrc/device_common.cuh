@@ -9,8 +9,8 @@
 //                   decide the hit; products are never contracted into FMAs so a
 //                   shared edge gives exactly opposite values in its two
 //                   triangles, and exact zeros are re-evaluated in FP64.
-//   node4_keys      the four box tests of a 4-wide BVH node, children hit sorted
-//                   nearest first
+//   node4_keys      the four box tests of a 4-wide BVH node (child boxes on a
+//                   7-bit grid of the node's own), children hit sorted nearest first
 //   traverse        nearest hit in the 4-wide BVH with a per-thread stack
 #pragma once
 #include <cstdint>
@@ -25,7 +25,7 @@ constexpr float kTwoPi = 6.28318530717958647692f;
 constexpr int kStack = 64;
 
 // One 32-byte load through the read-only data path (sm_100 and later); p must be
-// 32-byte aligned.  Halves the load instructions of a 64-byte BVH node.
+// 32-byte aligned.  A 64-byte BVH node takes two.
 __device__ __forceinline__ void ldg256(const float4 *p, float4 &a, float4 &b)
 {
     asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
@@ -229,16 +229,29 @@ struct TravStats { uint32_t nodes, boxes, tris, relocated; };
 // within 4 ulp may swap places, which only changes the visiting order.
 constexpr uint32_t kMiss = 0xffffffffu;
 
-__device__ __forceinline__ uint32_t box_key(float lx, float hx, float ly, float hy, float lz, float hz, float ix,
-                                            float iy, float iz, float oix, float oiy, float oiz, float t_min,
-                                            float t_best, uint32_t slot)
+// Grid position of child c's plane in a plane word (byte c = 128 + q): the
+// float 1 + q / 128, made by placing that byte under the exponent byte 0x3f.
+template <int C>
+__device__ __forceinline__ float qplane(uint32_t w)
 {
-    const float x0 = fmaf(lx, ix, -oix), x1 = fmaf(hx, ix, -oix);
-    const float y0 = fmaf(ly, iy, -oiy), y1 = fmaf(hy, iy, -oiy);
-    const float z0 = fmaf(lz, iz, -oiz), z1 = fmaf(hz, iz, -oiz);
-    const float tn = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), t_min));
-    const float tf = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), t_best));
+    return __uint_as_float(__byte_perm(w, 0x3f000000u, 0x7044u | (C << 8)));
+}
+
+// Key of one child from its near-plane and far-plane distances along each axis.
+__device__ __forceinline__ uint32_t slab_key(float xn, float xf, float yn, float yf, float zn, float zf, float t_min,
+                                             float t_best, uint32_t slot)
+{
+    const float tn = fmaxf(fmaxf(xn, yn), fmaxf(zn, t_min));
+    const float tf = fminf(fminf(xf, yf), fminf(zf, t_best));
     return tn <= tf ? ((__float_as_uint(tn) & 0x7ffffffcu) | slot) : kMiss;
+}
+
+// Distances t = f * (S / d) + (b - o) / d of one axis's planes in plane word w
+// for children (0, 1) and (2, 3), two per packed FMA.
+__device__ __forceinline__ void qplanes(uint32_t w, float2 a, float2 b, float2 &t01, float2 &t23)
+{
+    t01 = __ffma2_rn(make_float2(qplane<0>(w), qplane<1>(w)), a, b);
+    t23 = __ffma2_rn(make_float2(qplane<2>(w), qplane<3>(w)), a, b);
 }
 
 __device__ __forceinline__ void cswap(uint32_t &a, uint32_t &b)
@@ -250,23 +263,43 @@ __device__ __forceinline__ void cswap(uint32_t &a, uint32_t &b)
 
 // The four child boxes of wide node `node` against the ray (o, 1/d) restricted
 // to [t_min, t_best]: keys k[0..3] of the children hit, nearest first (kMiss
-// after the last), the node's child words and its number of children.
+// after the last), the node's child words and its number of children.  Per
+// axis the near plane is the low one for a direction component >= 0 and the
+// high one otherwise, so one comparison per axis replaces a min and a max per
+// child and axis; an empty slot's inverted box (low above high) is never met.
 __device__ __forceinline__ void node4_keys(const float4 *__restrict__ nodes, int node, float ix, float iy,
                                            float iz, float oix, float oiy, float oiz, float t_min, float t_best,
                                            uint32_t &k0, uint32_t &k1, uint32_t &k2, uint32_t &k3, int4 &child,
                                            int &n_child)
 {
-    float4 lx, hx, ly, hy, lz, hz, cw, meta;
-    ldg256(nodes + 8 * node, lx, hx);
-    ldg256(nodes + 8 * node + 2, ly, hy);
-    ldg256(nodes + 8 * node + 4, lz, hz);
-    ldg256(nodes + 8 * node + 6, cw, meta);
+    float4 base, cw, pxy, pz;
+    ldg256(nodes + 4 * node, base, cw);
+    ldg256(nodes + 4 * node + 2, pxy, pz);
     child = make_int4(__float_as_int(cw.x), __float_as_int(cw.y), __float_as_int(cw.z), __float_as_int(cw.w));
-    n_child = __float_as_int(meta.x);
-    k0 = box_key(lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, ix, iy, iz, oix, oiy, oiz, t_min, t_best, 0u);
-    k1 = box_key(lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, ix, iy, iz, oix, oiy, oiz, t_min, t_best, 1u);
-    k2 = box_key(lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, ix, iy, iz, oix, oiy, oiz, t_min, t_best, 2u);
-    k3 = box_key(lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, ix, iy, iz, oix, oiy, oiz, t_min, t_best, 3u);
+    n_child = (child.x != ~0) + (child.y != ~0) + (child.z != ~0) + (child.w != ~0);
+    const float ax = base.w * ix, ay = pz.z * iy, az = pz.w * iz;
+    const float bx = fmaf(base.x, ix, -oix), by = fmaf(base.y, iy, -oiy), bz = fmaf(base.z, iz, -oiz);
+    const uint32_t lx = __float_as_uint(pxy.x), hx = __float_as_uint(pxy.y);
+    const uint32_t ly = __float_as_uint(pxy.z), hy = __float_as_uint(pxy.w);
+    const uint32_t lz = __float_as_uint(pz.x), hz = __float_as_uint(pz.y);
+    const bool sx = ix < 0.0f, sy = iy < 0.0f, sz = iz < 0.0f;
+    const uint32_t nx = sx ? hx : lx, fx = sx ? lx : hx;
+    const uint32_t ny = sy ? hy : ly, fy = sy ? ly : hy;
+    const uint32_t nz = sz ? hz : lz, fz = sz ? lz : hz;
+    float2 xn01, xn23, xf01, xf23, yn01, yn23, yf01, yf23, zn01, zn23, zf01, zf23;
+    const float2 ax2 = make_float2(ax, ax), bx2 = make_float2(bx, bx);
+    const float2 ay2 = make_float2(ay, ay), by2 = make_float2(by, by);
+    const float2 az2 = make_float2(az, az), bz2 = make_float2(bz, bz);
+    qplanes(nx, ax2, bx2, xn01, xn23);
+    qplanes(fx, ax2, bx2, xf01, xf23);
+    qplanes(ny, ay2, by2, yn01, yn23);
+    qplanes(fy, ay2, by2, yf01, yf23);
+    qplanes(nz, az2, bz2, zn01, zn23);
+    qplanes(fz, az2, bz2, zf01, zf23);
+    k0 = slab_key(xn01.x, xf01.x, yn01.x, yf01.x, zn01.x, zf01.x, t_min, t_best, 0u);
+    k1 = slab_key(xn01.y, xf01.y, yn01.y, yf01.y, zn01.y, zf01.y, t_min, t_best, 1u);
+    k2 = slab_key(xn23.x, xf23.x, yn23.x, yf23.x, zn23.x, zf23.x, t_min, t_best, 2u);
+    k3 = slab_key(xn23.y, xf23.y, yn23.y, yf23.y, zn23.y, zf23.y, t_min, t_best, 3u);
     cswap(k0, k1);
     cswap(k2, k3);
     cswap(k0, k2);

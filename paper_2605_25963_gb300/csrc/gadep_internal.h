@@ -46,22 +46,39 @@ struct detmesh_mesh {
     std::vector<float> xyz_f;  // FP32 copy handed to the BVH and to callers
 };
 
-// Device-side compacted BVH of 4-wide nodes.  Node = 8 x 16 bytes (128 B, one
-// L1 line), the boxes of the four children stored in the parent, one axis
-// bound per float4 so that the four box tests run side by side:
-//   f4[0] = lo.x of children 0..3      f4[1] = hi.x of children 0..3
-//   f4[2] = lo.y                       f4[3] = hi.y
-//   f4[4] = lo.z                       f4[5] = hi.z
-//   i4[6] = (child0, child1, child2, child3)
-//   i4[7] = (number of children 1..4, 0, 0, 0)
-// child >= 0: inner node index; child < 0: leaf ~(first << 3 | count) holding
-// triangles [first, first + count).  Slots past the number of children are empty:
-// count 0 and a box at +infinity on every axis, which no ray's slab test meets.
+// Device-side compacted BVH of 4-wide nodes with quantised child boxes (after
+// Ylitie, Karras and Laine, HPG 2017).  Node = 4 x 16 bytes (64 B, half an L1
+// line), the boxes of the four children stored in the parent on a grid of the
+// node's own:
+//   f4[0] = (b.x, b.y, b.z, S.x)        i4[1] = (child0, child1, child2, child3)
+//   u4[2] = (lo.x, hi.x, lo.y, hi.y)    u4[3] = (lo.z, hi.z, S.y, S.z)
+// A plane word holds one byte per child, 128 + q with q in [0, 127]; the plane
+// it stands for is b + S (1 + q / 128) on that axis, where S = 128 s is a power
+// of two and s the grid step.  Low planes are rounded down and high planes up
+// from the padded child box, so the quantised box contains it.  child >= 0:
+// inner node index; child < 0: leaf ~(first << 3 | count) holding triangles
+// [first, first + count).  Slots past the number of children are empty: child
+// ~0 (count 0) and an inverted box (every low plane q = 127, every high plane
+// q = 0), which a slab test with near and far planes chosen by the ray's
+// direction signs never meets.
 // Triangle = 3 x float4: (v0, region id bits), (v1, mesh triangle id bits), (v2, 0)
 // with region id = solid + 1 (0 = world).
 // Trees: one per region (the triangles of the region's own solid and of its child
 // solids) plus one over every triangle; all share the node and triangle arrays.
-constexpr int kNodeFloats = 32;
+constexpr int kNodeFloats = 16;
+constexpr int32_t kEmptyChild = ~0;   // leaf_ref(0, 0)
+
+namespace gadep {
+// One node decoded on the host: the child boxes in FP64 (the planes the device
+// approximates), the child words and the number of children in use.
+struct WideNode {
+    double lo[4][3], hi[4][3];
+    int32_t child[4];
+    int n;
+};
+void decode_node(const float *f, WideNode &out);
+}  // namespace gadep
+
 struct gadep_bvh {
     int device = 0;
     gadep::MeshData geo;                 // for host-side localisation of sources

@@ -695,15 +695,20 @@ void scene_box(const gadep_bvh *b, float lo[3], float hi[3])
 {
     for (int k = 0; k < 3; ++k) { lo[k] = 0.0f; hi[k] = -1.0f; }
     if (b->regions[3] < 0) return;
-    const float *f = b->nodes.data() + (size_t)b->regions[3] * kNodeFloats;
-    int32_t w[8];
-    std::memcpy(w, &f[24], 32);
-    for (int k = 0; k < 3; ++k) { lo[k] = INFINITY; hi[k] = -INFINITY; }
-    for (int c = 0; c < w[4] && c < 4; ++c) {
+    WideNode wn;
+    decode_node(b->nodes.data() + (size_t)b->regions[3] * kNodeFloats, wn);
+    double dlo[3] = { INFINITY, INFINITY, INFINITY }, dhi[3] = { -INFINITY, -INFINITY, -INFINITY };
+    for (int c = 0; c < wn.n; ++c) {
         for (int k = 0; k < 3; ++k) {
-            lo[k] = std::min(lo[k], f[8 * k + c]);
-            hi[k] = std::max(hi[k], f[8 * k + 4 + c]);
+            dlo[k] = std::min(dlo[k], wn.lo[c][k]);
+            dhi[k] = std::max(dhi[k], wn.hi[c][k]);
         }
+    }
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = (float)dlo[k];
+        if ((double)lo[k] > dlo[k]) lo[k] = std::nextafter(lo[k], -INFINITY);
+        hi[k] = (float)dhi[k];
+        if ((double)hi[k] < dhi[k]) hi[k] = std::nextafter(hi[k], INFINITY);
     }
 }
 

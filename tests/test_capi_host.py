@@ -151,7 +151,7 @@ def test_bvh_host_invariants(name, spatial):
     # one tree over every triangle + one per region over its own and its children's
     # triangles: each triangle is in three trees (global, own region, parent region);
     # spatial splits add copies, within the budget of max_dup records per triangle
-    assert st["node_bytes"] == 128 * st["n_nodes"] and st["tri_bytes"] == 48 * st["n_refs"]
+    assert st["node_bytes"] == 64 * st["n_nodes"] and st["tri_bytes"] == 48 * st["n_refs"]
     if spatial:
         assert 3 * st["n_tri"] <= st["n_refs"] <= 2 * 3 * st["n_tri"] + 64
     else:
