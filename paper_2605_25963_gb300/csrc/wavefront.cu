@@ -899,8 +899,11 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
     int inter_inst = 0;
     const unsigned int stride = gridDim.x * blockDim.x;
     for (unsigned int base = blockIdx.x * blockDim.x; base < n; base += stride) {   // block-uniform
-        const unsigned int j = base + threadIdx.x;
-        const bool mine = j < n;
+        // last queue entry first: the trace kernel handed out its queue from the
+        // front, so the records it touched last are the likeliest still in L2
+        const unsigned int jf = base + threadIdx.x;
+        const bool mine = jf < n;
+        const unsigned int j = mine ? n - 1u - jf : 0u;
         const unsigned int slot = mine ? S.qsort[j] : 0u;
         bool alive_slot = false, finished = false;
         uint32_t key = 0;
@@ -914,7 +917,17 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
         Track tr;
         if (mine) {
             const Hit ht = S.hit[j];
-            const SlotA sa = S.slot[slot].a;
+            // the hot half, with the L2 told to fetch the whole 64-byte record: an
+            // interaction then finds the cold half there instead of waiting on DRAM
+            SlotA sa;
+            {
+                const uint4 *pa = reinterpret_cast<const uint4 *>(&S.slot[slot].a);
+                uint4 x, y;
+                asm("ld.global.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(x.x), "=r"(x.y), "=r"(x.z), "=r"(x.w) : "l"(pa));
+                asm("ld.global.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(y.x), "=r"(y.y), "=r"(y.z), "=r"(y.w) : "l"(pa + 1));
+                sa.f = make_float4(__uint_as_float(x.x), __uint_as_float(x.y), __uint_as_float(x.z), __uint_as_float(x.w));
+                sa.u = y;
+            }
             float t_cur = sa.f.x;
             const uint32_t tag = __float_as_uint(sa.f.y);
             float E = sa.f.z, lam = sa.f.w;
