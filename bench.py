@@ -67,7 +67,7 @@ def workload_config(name, n_hist):
         return dict(det=W.STRESS_DET, src=W.STRESS_SOURCE, energies=W.STRESS_ENERGIES,
                     n_hist=n_hist or W.STRESS_HISTORIES,
                     desc="stress: coax at 1024 segments with a 2 x 1 mm contact groove and a Cu flange with 16 "
-                         "bolt holes (1,012,288 triangles), water-prism volume source, 8 energies 59.5-1836 keV")
+                         "bolt holes (1,501,300 triangles), water-prism volume source, 8 energies 59.5-1836 keV")
     if name == "bare":
         return dict(det=W.BARE_CYLINDER, src=W.BARE_POINT_100, energies=(662.0,), n_hist=n_hist or 1_000_000,
                     desc="bare Ge cylinder R 30 L 60, 48 segments (192 triangles), point source 100 mm, 662 keV")

@@ -193,6 +193,69 @@ def test_nearest_hit_matches_bruteforce(orc):
         assert strict >= 0.99 and agree >= 0.998, (strict, agree)
 
 
+def test_axis_parallel_rays_match_bruteforce(orc):
+    """Rays along the coordinate axes and the diagonals of the coordinate planes
+    (one or two direction components exactly zero: reciprocal directions of
+    +-1e30 in the slab tests of the quantised child boxes), from random origins
+    and from points on the detector's symmetry axis (where the end faces' ring
+    triangulations meet), against FP64 brute force on the same binary32
+    vertices: no ray may pass between triangles or miss a surface, and the
+    surface hit and its side agree."""
+    eps32 = 2.0 ** -24
+    for name in ("COAX_P", "BARE_CYLINDER"):
+        m, b, om64 = scene(orc, name)
+        gpu_solid = m.arrays()[2]
+        X, T, S, sol = om64.arrays()
+        X32 = X.astype(np.float32).astype(np.float64)
+        om = orc.Mesh.from_arrays(X32, T, S, sol["material"], sol["active"], sol["group"], sol["parent"])
+        nrm = np.cross(X32[T[:, 1]] - X32[T[:, 0]], X32[T[:, 2]] - X32[T[:, 0]])
+        nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+        dirs = []
+        for a in range(3):
+            for sgn in (1.0, -1.0):
+                e = np.zeros(3)
+                e[a] = sgn
+                dirs.append(e)
+        for a, c in ((0, 1), (0, 2), (1, 2)):
+            for sa in (1.0, -1.0):
+                for sc in (1.0, -1.0):
+                    e = np.zeros(3)
+                    e[a], e[c] = sa, sc
+                    dirs.append(e / np.linalg.norm(e))
+        dirs = np.array(dirs)
+        rng = np.random.default_rng(5)
+        n_rand = 400
+        o = np.column_stack([rng.uniform(-40, 40, n_rand), rng.uniform(-40, 40, n_rand), rng.uniform(-125, 30, n_rand)])
+        d = dirs[rng.integers(0, len(dirs), n_rand)]
+        # on the symmetry axis, along it and across it
+        zs = np.linspace(-120.0, 25.0, 30)
+        o_ax = np.column_stack([np.zeros_like(zs), np.zeros_like(zs), zs])
+        o = np.vstack([o, o_ax, o_ax])
+        d = np.vstack([d, np.tile([0.0, 0.0, 1.0], (30, 1)), np.tile([0.0, 0.0, -1.0], (30, 1))])
+        n = len(o)
+        rays = np.zeros((n, 8), np.float32)
+        rays[:, 0:3] = o
+        rays[:, 4:7] = d
+        rays[:, 7] = np.array([-1] * n, np.int32).view(np.float32)
+        t, tri, ent = (x.cpu().numpy() for x in api.gadep_nearest_hit(b, torch.from_numpy(rays).cuda()))
+        agree = 0
+        for i in range(n):
+            oo = rays[i, 0:3].astype(np.float64)
+            dd = rays[i, 4:7].astype(np.float64)
+            k, tt, ee = om.nearest_hit(oo, dd, 0.0, -1)
+            if k < 0:
+                assert tri[i] == -1 and np.isinf(t[i]), (name, i)
+                agree += 1
+                continue
+            assert tri[i] >= 0, (name, i, "GPU ray missed a surface", tt)
+            cosv = abs(np.dot(dd, nrm[k]))
+            scale = np.abs(oo).max() + np.abs(X32[T[k]]).max()
+            tol = 1e-5 * max(tt, 1.0) + 8 * eps32 * scale / max(cosv, 1e-3)
+            assert abs(t[i] - tt) <= tol, (name, i, t[i], tt, cosv)
+            agree += gpu_solid[tri[i]] == S[k] and ent[i] == ee
+        assert agree >= n - 2, (name, agree, n)
+
+
 def test_philox_device_stream_matches_oracle(orc):
     for seed, hid, inst in ((1, 0, 0), (0xDEADBEEFCAFEF00D, 123456789012, 7), (2 ** 64 - 1, 2 ** 40 + 3, 2 ** 32 - 1)):
         g = api.gadep_philox_words(seed, hid, inst, 4097).cpu().numpy().view(np.uint32)
