@@ -218,11 +218,14 @@ gadep_status gadep_bvh_build(const detmesh_mesh *m, int32_t device, gadep_bvh **
 gadep_status gadep_bvh_build_opts(const detmesh_mesh *m, const gadep_bvh_opts *opts, int32_t device,
                                   gadep_bvh **out);
 gadep_status gadep_bvh_get_stats(const gadep_bvh *b, gadep_bvh_stats *out);
-/* Host-side invariant check of every tree: each of its triangles held by at
- * least one leaf and never twice by one leaf, child boxes inside parents, every
- * leaf box meeting the bounds of the triangles it holds, and the leaf boxes of
- * each triangle covering a grid of points on it (vertices included; the whole
- * triangle when it was not cut).  GADEP_E_MESH if violated. */
+/* Host-side invariant check of every tree, on the decoded (quantised) boxes:
+ * each of its triangles held by at least one leaf and never twice by one leaf,
+ * every child box non-empty and meeting its parent's, empty slots empty, every
+ * leaf box meeting the bounds of the triangles it holds, and, with each leaf's
+ * box intersected with those of all its ancestors (the region a ray passes
+ * every box test of on its way to the leaf), the leaves of each triangle
+ * covering a grid of points on it (vertices included; the whole triangle when
+ * it was not cut).  GADEP_E_MESH if violated. */
 gadep_status gadep_bvh_validate(const gadep_bvh *b);
 void gadep_bvh_destroy(gadep_bvh *b);
 
