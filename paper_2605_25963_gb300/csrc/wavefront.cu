@@ -41,10 +41,11 @@ using namespace gadep::dev;
 
 // Per-slot photon record: 64 bytes, the DRAM fetch unit, in two 32-byte halves
 // (DRAM sectors).  The first holds everything a boundary crossing -- three
-// visits in four -- reads and changes, so such a physics visit moves one sector
-// each way; the second (flight origin, direction, random-number state) is read
-// only at interactions and when a waiting annihilation photon starts, and
-// written then.  The trace query reads both.
+// visits in four -- reads and changes; the second (flight origin, direction,
+// random-number state) is read only at interactions and when a waiting
+// annihilation photon starts, and written then.  The trace query reads both and
+// leaves a copy of the first in queue order (State::hot), so a physics visit
+// reads it in a coalesced stream and writes it back to the slot, one sector.
 struct __align__(32) SlotA {
     float4 f;                   // t_cur (distance travelled from the flight origin), tag bits
                                 // (last mesh triangle + 1) << 8 | region, E, lam (mean free paths left)
@@ -56,7 +57,7 @@ struct __align__(32) SlotB {
     float4 d;                   // direction, w = history index within the instance (bits)
 };
 struct __align__(64) Slot {
-    SlotA a;                    // read and written by every physics visit, read by trace
+    SlotA a;                    // read by trace (copied to State::hot), written by every physics visit
     SlotB b;                    // read by trace; read and written by physics at interactions
 };
 // info word: instance (10 bits; a run has at most 1024), error bits (6), flags (2),
@@ -330,6 +331,7 @@ struct State {
     float *esc;
     float4 *score;                 // GRAD only
     Hit *hit;                      // by queue position
+    SlotA *hot;                    // by queue position: the slot's first half, copied by trace, read by physics
     unsigned int *queue[2];
     unsigned int *qkey[2];         // sort key of each queue entry
     unsigned int *hist[2];         // key histogram of queue[parity]
@@ -760,8 +762,10 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const Params P, State S, 
             if (!has && idx != 0xffffffffu) {
                 qidx = idx;
                 const Slot &sr = S.slot[queue[idx]];
-                const float4 af = sr.a.f;
-                const uint32_t pinst = sr.a.u.x & kInstMask;
+                const SlotA sa = sr.a;
+                S.hot[idx] = sa;        // physics reads it here, in queue order
+                const float4 af = sa.f;
+                const uint32_t pinst = sa.u.x & kInstMask;
                 const float4 bo = sr.b.o, bd = sr.b.d;
                 const float E = af.z, lam = af.w;
                 const uint32_t tag = __float_as_uint(af.y);
@@ -917,17 +921,9 @@ __global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S
         Track tr;
         if (mine) {
             const Hit ht = S.hit[j];
-            // the hot half, with the L2 told to fetch the whole 64-byte record: an
-            // interaction then finds the cold half there instead of waiting on DRAM
-            SlotA sa;
-            {
-                const uint4 *pa = reinterpret_cast<const uint4 *>(&S.slot[slot].a);
-                uint4 x, y;
-                asm("ld.global.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(x.x), "=r"(x.y), "=r"(x.z), "=r"(x.w) : "l"(pa));
-                asm("ld.global.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(y.x), "=r"(y.y), "=r"(y.z), "=r"(y.w) : "l"(pa + 1));
-                sa.f = make_float4(__uint_as_float(x.x), __uint_as_float(x.y), __uint_as_float(x.z), __uint_as_float(x.w));
-                sa.u = y;
-            }
+            // the slot's first half as the trace kernel found it (nothing writes the
+            // slot between the two kernels), in queue order: a coalesced read
+            const SlotA sa = S.hot[j];
             float t_cur = sa.f.x;
             const uint32_t tag = __float_as_uint(sa.f.y);
             float E = sa.f.z, lam = sa.f.w;
@@ -1302,6 +1298,7 @@ gadep_status wavefront_create(int device, int slots, bool grad, WavefrontBuffers
     size_t o_score = off; off = align_up(off + n * sizeof(float4));   // always: buffers serve both forms
     (void)grad;
     size_t o_hit = off; off = align_up(off + n * sizeof(wf::Hit));
+    size_t o_hot = off; off = align_up(off + n * sizeof(wf::SlotA));
     size_t o_q0 = off; off = align_up(off + n * 4);
     size_t o_q1 = off; off = align_up(off + n * 4);
     size_t o_k0 = off; off = align_up(off + n * 4);
@@ -1330,6 +1327,7 @@ gadep_status wavefront_create(int device, int slots, bool grad, WavefrontBuffers
     w->S.esc = (float *)(b + o_esc);
     w->S.score = (float4 *)(b + o_score);
     w->S.hit = (wf::Hit *)(b + o_hit);
+    w->S.hot = (wf::SlotA *)(b + o_hot);
     w->S.queue[0] = (unsigned int *)(b + o_q0);
     w->S.queue[1] = (unsigned int *)(b + o_q1);
     w->S.qkey[0] = (unsigned int *)(b + o_k0);
