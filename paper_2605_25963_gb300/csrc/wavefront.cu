@@ -93,7 +93,7 @@ struct __align__(32) Sec {      // second annihilation photon, waiting for the f
     float4 d;                   // direction, w = region bits
 };
 
-constexpr int kMaxFaceBins = 10;    // direction cells per cube-map face and axis, at most
+constexpr int kMaxFaceBins = 12;    // direction cells per cube-map face and axis, at most
 constexpr int kMaxKeys = 8192;      // regions * 6 * face_bins^2 at most
 
 // Face cells per axis for a mesh of n_region regions: the finest that keeps the
@@ -876,8 +876,13 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const Params P, State S, 
 }
 
 // ---------------------------------------------------------------- physics
+// Bounds on registers: with room for three blocks of 256 per SM, ptxas allocates the
+// photon-only form without spilling in 64 registers (so four blocks still fit; under a
+// four-block bound it spilled a few bytes and ran slower) and the charged-particle form
+// in 80; the gradient form would take 69 and drop to three blocks per SM, slower than
+// its small spill at four, so it keeps the four-block bound.
 template <bool GRAD, bool COUNT, bool EM>
-__global__ void __launch_bounds__(256, 4) physics_kernel(const Params P, State S, int cur,
+__global__ void __launch_bounds__(256, GRAD ? 4 : 3) physics_kernel(const Params P, State S, int cur,
                                                       unsigned long long *counters)
 {
     const uint32_t FULL = 0xffffffffu;
