@@ -315,7 +315,7 @@ typedef struct {
     float    group_scale[GADEP_MAX_GROUPS];  /* density scale per group (default 1) */
     int32_t  wf_slots;        /* wavefront variant: photon slots in device memory, 1024..2^26 (0 = from
                                  the run: the smallest power of two >= the histories expected to
-                                 reach the scene, within [2^20, 2^25]; ~200 B each) */
+                                 reach the scene, within [2^20, 2^25]; ~220 B each) */
     int32_t  e_model;         /* charged particles set in motion by photon interactions:
                                  0 (default) deposit their kinetic energy at the interaction point;
                                  1 run straight ahead in the continuous-slowing-down
