@@ -58,3 +58,28 @@ def test_gpu_arm_fails_loudly_without_a_gpu():
         assert "no CUDA device" in str(e)
     else:
         raise AssertionError("gadep_bvh_build on device 0 succeeded without a GPU")
+
+
+def test_traffic_record_matches_the_kernels():
+    """The DRAM-per-query record in profiles/traffic.json was taken on the transport
+    kernels as they stand: its hash is the hash of their sources (the benchmark
+    reports no traffic otherwise), and the benchmark scales each per-query figure
+    by the queries of a launch."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    argv = sys.argv
+    try:
+        sys.argv = [argv[0]]
+        spec.loader.exec_module(bench)
+    finally:
+        sys.argv = argv
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        rec = json.load(f)
+    h = bench.kernel_hash()
+    for workload, kinds in (("coax", ("trace", "physics", "sort")), ("stress", ("trace",))):
+        assert rec[workload]["kernel_hash"] == h, workload
+        for kind in kinds:
+            per_query = rec[workload]["dram_bytes_per_query"][kind]
+            assert per_query > 0
+            assert bench.recorded_traffic(workload, kind, 1000) == per_query * 1000
